@@ -1,0 +1,318 @@
+"""Throughput benchmark of the scene-flow hot path (SGM at t and t+1 with the
+left-right check, then the combination) on 1242x375 stereo quadruples, D=128.
+
+One step = one whole frame: sf_scene_flow on one synthetic quadruple resident
+in HBM.  Prints ONE JSON line (rank 0).  See --help for the arms."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scene-flow frames/s @1242x375 D=128 (learned vs plain L-R); % of HBM roofline"
+W_IMG, H_IMG, D_MAX = 1242, 375, 128
+WORKLOAD = "automotive 1242x375 D=128 quadruple, plain SGM (8 paths, census 9x7, P1=7, P2=86, L-R tol 1) + combination"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t0 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [v.strip() for v in line.split(",")]))
+
+    def mark(self):
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for t, r in self.rows if self.t0 is None or t >= self.t0 - 0.1]
+        if not rows:
+            rows = [r for _, r in self.rows[-3:]]
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def bytes_model(N, D):
+    """Algorithmic HBM bytes of the dominant stage per launch (one stereo pass).
+    Aggregation of a stored cost volume: read the uint8 cost once and write the
+    uint16 aggregated cost once -> 3*N*D bytes."""
+    return 3 * N * D
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1801_04720_gb300 import _lib, build, synth
+
+    torch.cuda.set_device(local)
+    build.build()
+    _lib.load()
+    dev = torch.device("cuda", local)
+    q = synth.automotive(seed=args.seed + rank)
+    H, W = q.shape
+    N = W * H
+    p = _lib.params(D=D_MAX)
+    cam = _lib.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
+    imgs = [torch.from_numpy(im).to(dev) for im in q.images()]
+    flow = torch.from_numpy(q.flow).to(dev)
+    ws = _lib.workspace(W, H, p, dev)
+    out = _lib.alloc_scene_flow_outputs(W, H, dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        _lib.sf_scene_flow(imgs, flow, p, cam, ws=ws, out=out, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # keep the GPU loaded for >= ~1.5 s before and during the timed region so
+    # the clock samples describe the timed work
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_end = time.time() + 1.5
+    while time.time() < t_end:
+        step()
+        torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    tracer = _lib.StageTracer(n_records=64 * args.steps)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.mark()
+    launches0 = _lib.kernel_launches()
+    with tracer:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)            # L2 flush between timed steps (untimed)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.kernel_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    stages = tracer.durations()
+    stage_tot = {k: sum(v) for k, v in stages.items()}
+    dominant = max(stage_tot, key=stage_tot.get)
+    dom_ms = statistics.mean(stages[dominant])
+    hbm_peak, peak_kind = peaks()
+    algo_bytes = bytes_model(N, D_MAX)
+    achieved = algo_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get(dominant)
+        except Exception:
+            traffic = None
+
+    e2e = None
+    if not args.no_e2e:
+        ws_h = torch.empty(_lib.sf_scene_flow_host_workspace_size(W, H, p), dtype=torch.uint8,
+                           device=dev)
+        h_imgs = [torch.from_numpy(im).pin_memory() for im in q.images()]
+        h_flow = torch.from_numpy(q.flow).pin_memory()
+        h_out = {"s4": torch.empty((H, W, 4)).pin_memory(),
+                 "motion": torch.empty((H, W, 3)).pin_memory(),
+                 "point": torch.empty((H, W, 3)).pin_memory(),
+                 "valid": torch.empty((H, W), dtype=torch.uint8).pin_memory()}
+        for _ in range(3):
+            _lib.sf_scene_flow_host(h_imgs, h_flow, p, cam, ws_h, h_out, stream=stream)
+        e_ms = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _lib.sf_scene_flow_host(h_imgs, h_flow, p, cam, ws_h, h_out, stream=stream)
+            e_ms.append((time.perf_counter() - t0) * 1e3)
+        e_mean = statistics.mean(e_ms)
+        if world > 1:
+            t = torch.tensor([e_mean], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_mean = float(t.item())
+        e2e = {"value": round(world * 1000.0 / e_mean, 2), "unit": "frames/s",
+               "h2d_bytes_per_step": 4 * N + 8 * N, "d2h_bytes_per_step": 16 * N + 12 * N + 12 * N + N,
+               "ms_per_step": round(e_mean, 4)}
+
+    result = {
+        "metric": METRIC, "value": round(world * 1000.0 / ms, 2), "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/u16 integer SGM, f32 subpixel + scene flow",
+        "data": "synthetic (seeded automotive-shaped scenes; KITTI is not available)",
+        "config": {"workload": WORKLOAD, "W": W, "H": H, "D": D_MAX, "frames_per_step": 1,
+                   "path": "plain L-R", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB write, untimed)"},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(achieved, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "avg_launch_ms": round(dom_ms, 5)},
+        "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_tot.items()},
+        "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+    }
+    return result, q
+
+
+def cpu_baseline(q):
+    """The oracle as it stands on one full frame (single thread)."""
+    from oracle import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.scene_flow(q.images(), q.flow, q.camera.f, q.camera.B, q.camera.cx, q.camera.cy,
+                      D=D_MAX)
+    dt = time.perf_counter() - t0
+    return {"value": round(1.0 / dt, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "one full 1242x375 D=128 frame (4 SGM passes + combination), 1 thread",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle as it stands, each step a 1242x24 band of
+    the frame (all 4 SGM passes + combination), scaled to frames/s by area."""
+    from oracle import oracle
+    from paper_1801_04720_gb300 import synth
+    oracle.build()
+    q = synth.automotive(seed=args.seed)
+    band = 24
+    y0 = 160
+    sl = slice(y0, y0 + band)
+    imgs = [np.ascontiguousarray(im[sl]) for im in q.images()]
+    flow = np.ascontiguousarray(q.flow[sl])
+
+    def step():
+        oracle.scene_flow(imgs, flow, q.camera.f, q.camera.B, q.camera.cx, q.camera.cy - y0,
+                          D=D_MAX)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    frac = band / H_IMG
+    value = frac / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "frames/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int + f64 (CPU oracle)",
+        "data": "synthetic (seeded automotive-shaped scenes; KITTI is not available)",
+        "config": {"workload": WORKLOAD, "W": W_IMG, "H": H_IMG, "D": D_MAX,
+                   "sample": f"1242x{band} band per step, scaled by area"},
+        "cpu_baseline": {"value": round(value, 5), "unit": "frames/s", "cores": 1,
+                         "kind": "oracle", "sample": f"1242x{band} band per step, 1 thread"},
+        "e2e": {"value": round(value, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+import numpy as np  # noqa: E402  (used by the reference arm)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank)), flush=True)
+        return
+    result, q = run_ours(args, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            result["cpu_baseline"] = cpu_baseline(q)
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * libsf - GB300 (sm_103a) scene flow from SGM stereo disparity and a given
+ * optical flow, after Schuster et al., "Combining Stereo Disparity and Optical
+ * Flow for Basic Scene Flow" (arXiv 1801.04720).
+ *
+ * C ABI.  Plain pointers and sizes only.  Unless a function says otherwise:
+ *   - every array pointer is a DEVICE pointer owned by the caller; the library
+ *     never allocates, frees or keeps a pointer after the call returns;
+ *   - parameter structs (sf_sgm_params, sf_camera) live in HOST memory and are
+ *     read during the call only;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); the work
+ *     is enqueued asynchronously on it and the function returns without
+ *     waiting;
+ *   - arguments are validated on the host before anything is launched; a bad
+ *     argument returns SF_ERR_INVALID_ARG or SF_ERR_UNSUPPORTED and enqueues
+ *     nothing;
+ *   - a launch failure returns SF_ERR_CUDA; an error raised while a kernel
+ *     runs surfaces at the next synchronisation of `stream` (or from a later
+ *     call's launch check).
+ * Nothing crosses the ABI as an exception.
+ *
+ * Layouts: images are uint8 rows of `pitch` bytes (pitch >= W); every other
+ * array is dense row-major with pixel index i = y*W + x and, for volumes, the
+ * disparity d fastest: cost / aggregated cost [H][W][D].
+ *
+ * Disparity convention: a left-image pixel (x, y) with disparity d matches the
+ * right-image pixel (x - d, y); d runs over 0 .. D-1.
+ */
+#ifndef SF_H_
+#define SF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SF_OK = 0,
+  SF_ERR_INVALID_ARG = 1,   /* null pointer, size out of range, bad buffer size  */
+  SF_ERR_UNSUPPORTED = 2,   /* valid request outside what this build supports     */
+  SF_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed               */
+  SF_ERR_TIMEOUT = 4        /* a bounded device-side wait gave up (batch kernel)  */
+} sf_status;
+
+#define SF_MAX_DISPARITY 256
+#define SF_NUM_PATHS 8
+
+/* SGM parameters (Sec. 3.1 names SGM with eight paths and the left-right
+ * check; the values are the method's free parameters).
+ *   census_w, census_h : census window, both odd, census_w*census_h - 1 <= 64;
+ *                        the matching cost of a candidate outside the image is
+ *                        cmax = census_w*census_h - 1.
+ *   P1, P2             : path penalties for |delta d| = 1 and >= 2;
+ *                        need P1 <= P2 and cmax + P2 <= 255.
+ *   path_mask          : bit r enables traversal direction r, in the order
+ *                        (+1,0) (-1,0) (0,+1) (0,-1) (+1,+1) (-1,-1) (+1,-1) (-1,+1)
+ *                        where (rx, ry) is the step from p - r to p.
+ *   D                  : number of disparities, 1..256 (values 0..D-1).
+ *   subpixel           : 1 = parabolic refinement of the winner, 0 = off.
+ *   lr_tol             : left-right tolerance in pixels, >= 0 (inclusive). */
+typedef struct {
+  int32_t census_w, census_h;
+  uint16_t P1, P2;
+  uint32_t path_mask;
+  int32_t D;
+  int32_t subpixel;
+  int32_t lr_tol;
+} sf_sgm_params;
+
+/* Pinhole stereo camera: focal length f (px), baseline B (m), principal point
+ * (cx, cy) in pixels.  Used by the back-projection Z = f*B/d. */
+typedef struct {
+  float f, B, cx, cy;
+} sf_camera;
+
+/* Fills p with census 9x7, P1 = 7, P2 = 86, all 8 paths, D = 128, subpixel on,
+ * lr_tol = 1. */
+void sf_default_params(sf_sgm_params* p);
+
+/* Human-readable name of a status code (static storage). */
+const char* sf_status_string(sf_status s);
+
+/* Census transform (the matching cost of SGM, Sec. 3.1).  Bit k of
+ * census_out[y*W+x] (k = 0 least significant) is 1 iff the k-th window
+ * neighbour, counted row-major with the centre skipped, is strictly darker
+ * than the centre; neighbours outside the image take the nearest edge pixel.
+ * img: uint8 [H][pitch]; census_out: uint64 [H][W]. */
+sf_status sf_census(const uint8_t* img, int32_t W, int32_t H, int32_t pitch, int32_t census_w,
+                    int32_t census_h, uint64_t* census_out, void* stream);
+
+/* Matching cost volume (Sec. 3.1): Hamming distance of census strings.
+ * ref_is_right = 0: cost(x,y,d) = H(cL(x,y), cR(x-d,y)), ref = left image;
+ * ref_is_right = 1: cost(x,y,d) = H(cR(x,y), cL(x+d,y)), ref = right image.
+ * Candidates outside the image cost cmax.  ref / other: uint8 [H][pitch];
+ * cost_out: uint8 [H][W][D].  Census strings are computed inside the call. */
+sf_status sf_cost_volume(const uint8_t* ref, const uint8_t* other, int32_t W, int32_t H,
+                         int32_t pitch, const sf_sgm_params* p, int32_t ref_is_right,
+                         uint8_t* cost_out, void* stream);
+
+/* Workspace bytes that sf_sgm_aggregate needs (0 today; kept for the ABI). */
+size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p);
+
+/* Semi-global aggregation over the enabled paths (Sec. 3.1, "eight different
+ * paths"): S(p,d) = sum_r L_r(p,d) with
+ *   L_r(p,d) = C(p,d) + min(L_r(p-r,d), L_r(p-r,d+-1) + P1, min_k L_r(p-r,k) + P2)
+ *              - min_k L_r(p-r,k),
+ * and L_r(p,d) = C(p,d) where p - r is outside the image.  Exact integers.
+ * cost: uint8 [H][W][D]; agg_out: uint16 [H][W][D]. */
+sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
+                           uint16_t* agg_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Winner-take-all and parabolic subpixel refinement (Sec. 3.1).  d* is the
+ * smallest d reaching min_d S; for subpixel = 1 and 0 < d* < D-1 the output is
+ * d* + (a-b)/(2(a+b)) with a = S(d*-1)-S(d*), b = S(d*+1)-S(d*), else d*.
+ * agg: uint16 [H][W][D]; disp_int_out: int16 [H][W]; disp_sub_out: float
+ * [H][W] or NULL. */
+sf_status sf_disparity_select(const uint16_t* agg, int32_t W, int32_t H, int32_t D,
+                              int32_t subpixel, int16_t* disp_int_out, float* disp_sub_out,
+                              void* stream);
+
+/* Left-right consistency check (Sec. 3.1; it makes the disparity map
+ * non-dense): valid(x,y) = [x - dL >= 0 and |dL(x,y) - dR(x-dL,y)| <= tol] on
+ * the integer winners; disp_out = dL_sub where valid, NaN elsewhere.
+ * dL, dR: int16 [H][W]; dL_sub: float [H][W]; valid_out: uint8 [H][W]
+ * (1 / 0); disp_out: float [H][W]. */
+sf_status sf_lr_check(const int16_t* dL, const int16_t* dR, const float* dL_sub, int32_t W,
+                      int32_t H, int32_t tol, uint8_t* valid_out, float* disp_out, void* stream);
+
+/* Scene-flow combination (Sec. 3.3, Eq. 3-5).  For each pixel x the target is
+ * x' = x + F(x), computed as a float32 round-to-nearest sum.  S(x) is defined
+ * iff x' lies in [0, W-1] x [0, H-1], D0(x) is a usable disparity, and every
+ * tap of the bilinear interpolation of D1 at x' (Eq. 5) whose weight is not
+ * zero is usable; usable = not NaN and > 0.  Then
+ *   s4     = (u, v, d0, d1)                        with d1 = D1(x') by Eq. 5,
+ *   point  = P0 = ((x-cx)B/d0, (y-cy)B/d0, fB/d0),
+ *   motion = P1 - P0, P1 = ((x'-cx)B/d1, (y'-cy)B/d1, fB/d1);
+ * otherwise every float output is NaN and valid_out = 0.
+ * D0, D1: float [H][W] (NaN = removed by the check); flow: float [H][W][2];
+ * s4_out: float [H][W][4]; motion_out, point_out: float [H][W][3] or NULL;
+ * valid_out: uint8 [H][W]. */
+sf_status sf_combine_sceneflow(const float* D0, const float* D1, const float* flow, int32_t W,
+                               int32_t H, const sf_camera* cam, float* s4_out, float* motion_out,
+                               float* point_out, uint8_t* valid_out, void* stream);
+
+/* Workspace bytes for sf_sgm_full and sf_scene_flow at this size. */
+size_t sf_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p);
+
+/* Whole SGM for one rectified stereo pair (Sec. 3.1): census, cost,
+ * aggregation and selection with the left image as reference and again with
+ * the right image as reference, then the left-right check.
+ * left, right: uint8 [H][pitch].  Outputs (each may be NULL except disp_out):
+ * dL_out, dR_out: int16 [H][W] integer winners; valid_out: uint8 [H][W];
+ * disp_out: float [H][W] (subpixel left disparity, NaN where invalid).
+ * workspace: device buffer of at least sf_workspace_size() bytes, 256-byte
+ * aligned, owned by the caller, contents undefined on return. */
+sf_status sf_sgm_full(const uint8_t* left, const uint8_t* right, int32_t W, int32_t H,
+                      int32_t pitch, const sf_sgm_params* p, int16_t* dL_out, int16_t* dR_out,
+                      uint8_t* valid_out, float* disp_out, void* workspace, size_t ws_bytes,
+                      void* stream);
+
+/* The whole hot path for one stereo quadruple (Sec. 3): SGM disparity D0 on
+ * (left_t, right_t) and D1 on (left_t1, right_t1), each with its left-right
+ * check, then the combination with the given flow.  Images: uint8 [H][pitch];
+ * flow: float [H][W][2]; outputs as in sf_combine_sceneflow; D0_out, D1_out:
+ * float [H][W] or NULL (the checked subpixel disparities).  workspace: at least
+ * sf_workspace_size() bytes. */
+sf_status sf_scene_flow(const uint8_t* left_t, const uint8_t* right_t, const uint8_t* left_t1,
+                        const uint8_t* right_t1, int32_t pitch, const float* flow, int32_t W,
+                        int32_t H, const sf_sgm_params* p, const sf_camera* cam, float* s4_out,
+                        float* motion_out, float* point_out, uint8_t* valid_out, float* D0_out,
+                        float* D1_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Device workspace bytes for sf_scene_flow_host: sf_workspace_size() plus
+ * device staging for the inputs and outputs. */
+size_t sf_scene_flow_host_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p);
+
+/* sf_scene_flow with HOST inputs and outputs: the four images (uint8 [H][W],
+ * dense), flow and the outputs are host pointers (pinned memory gives
+ * asynchronous copies; pageable memory works but copies synchronously).  The
+ * call copies the inputs to the device workspace, runs the path, copies the
+ * outputs back and waits for `stream`.  motion_out / point_out may be NULL. */
+sf_status sf_scene_flow_host(const uint8_t* left_t, const uint8_t* right_t,
+                             const uint8_t* left_t1, const uint8_t* right_t1, const float* flow,
+                             int32_t W, int32_t H, const sf_sgm_params* p, const sf_camera* cam,
+                             float* s4_out, float* motion_out, float* point_out,
+                             uint8_t* valid_out, void* dev_workspace, size_t ws_bytes,
+                             void* stream);
+
+/* ---- tracing and counters (host-side bookkeeping; no paper counterpart) --- */
+
+/* Stage ids written by the tracer. */
+typedef enum {
+  SF_STAGE_CENSUS = 0,      /* census transform                              */
+  SF_STAGE_COST = 1,        /* stored cost volume                            */
+  SF_STAGE_AGGREGATE = 2,   /* path aggregation (one stereo pass)            */
+  SF_STAGE_SELECT = 3,      /* winner-take-all + subpixel                    */
+  SF_STAGE_LRCHECK = 4,     /* left-right check                              */
+  SF_STAGE_COMBINE = 5,     /* scene-flow combination                        */
+  SF_STAGE_SGM_SWEEP = 6,   /* fused cost + aggregation sweep                */
+  SF_NUM_STAGES = 7
+} sf_stage;
+
+/* Arms the tracer: from now on every stage the library enqueues is bracketed
+ * by cudaEventRecord() of the next two events of `events` (cudaEvent_t
+ * handles created by the caller) on the stage's stream, and the stage id is
+ * appended to stage_out.  Recording stops silently when events run out.  The
+ * arrays must stay valid until sf_trace_disarm().  Not thread-safe: arm and
+ * disarm from the thread that enqueues the work. */
+sf_status sf_trace_arm(void* const* events, int32_t n_events, int32_t* stage_out);
+
+/* Disarms the tracer; returns the number of stage records made (each used
+ * two events). */
+int32_t sf_trace_disarm(void);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all threads), for launch accounting. */
+uint64_t sf_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_H_ */

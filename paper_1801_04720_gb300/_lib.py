@@ -1,0 +1,321 @@
+"""Thin ctypes binding of libsf (include/sf.h).
+
+Argument marshalling only: every step of the path runs in libsf's CUDA
+kernels.  Functions take torch tensors that already live on the GPU (device
+memory and streams are PyTorch's), pass their data pointers and the current
+CUDA stream, and raise ``SFError`` on a non-OK status.  If libsf.so is missing
+the first call raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libsf.so")
+
+SF_OK = 0
+STATUS_NAMES = {0: "SF_OK", 1: "SF_ERR_INVALID_ARG", 2: "SF_ERR_UNSUPPORTED", 3: "SF_ERR_CUDA",
+                4: "SF_ERR_TIMEOUT"}
+
+# The functions include/sf.h declares (checked by the CPU export test).
+EXPORTED = [
+    "sf_default_params", "sf_status_string", "sf_census", "sf_cost_volume",
+    "sf_aggregate_workspace_size", "sf_sgm_aggregate", "sf_disparity_select", "sf_lr_check",
+    "sf_combine_sceneflow", "sf_workspace_size", "sf_sgm_full", "sf_scene_flow",
+    "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
+    "sf_trace_disarm", "sf_kernel_launches",
+]
+
+STAGE_NAMES = ["census", "cost", "aggregate", "select", "lrcheck", "combine", "sgm_sweep"]
+
+
+class SFError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} returned {STATUS_NAMES.get(status, status)}")
+
+
+class SgmParams(ctypes.Structure):
+    _fields_ = [("census_w", ctypes.c_int32), ("census_h", ctypes.c_int32),
+                ("P1", ctypes.c_uint16), ("P2", ctypes.c_uint16), ("path_mask", ctypes.c_uint32),
+                ("D", ctypes.c_int32), ("subpixel", ctypes.c_int32), ("lr_tol", ctypes.c_int32)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_float), ("B", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float)]
+
+
+def params(D=128, P1=7, P2=86, census_w=9, census_h=7, path_mask=0xFF, subpixel=True, lr_tol=1):
+    return SgmParams(census_w, census_h, P1, P2, path_mask, D, int(subpixel), lr_tol)
+
+
+def camera(f, B, cx, cy):
+    return Camera(f, B, cx, cy)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsf.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsf.so not found at {path}: run __graft_entry__.build() "
+                               "(the CUDA library is required; there is no fallback)")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i32 = ctypes.c_int32
+        sz = ctypes.c_size_t
+        PP = ctypes.POINTER(SgmParams)
+        PC = ctypes.POINTER(Camera)
+        sig = {
+            "sf_default_params": (None, [PP]),
+            "sf_status_string": (ctypes.c_char_p, [i32]),
+            "sf_census": (i32, [P, i32, i32, i32, i32, i32, P, P]),
+            "sf_cost_volume": (i32, [P, P, i32, i32, i32, PP, i32, P, P]),
+            "sf_aggregate_workspace_size": (sz, [i32, i32, PP]),
+            "sf_sgm_aggregate": (i32, [P, i32, i32, PP, P, P, sz, P]),
+            "sf_disparity_select": (i32, [P, i32, i32, i32, i32, P, P, P]),
+            "sf_lr_check": (i32, [P, P, P, i32, i32, i32, P, P, P]),
+            "sf_combine_sceneflow": (i32, [P, P, P, i32, i32, PC, P, P, P, P, P]),
+            "sf_workspace_size": (sz, [i32, i32, PP]),
+            "sf_sgm_full": (i32, [P, P, i32, i32, i32, PP, P, P, P, P, P, sz, P]),
+            "sf_scene_flow": (i32, [P, P, P, P, i32, P, i32, i32, PP, PC, P, P, P, P, P, P, P, sz, P]),
+            "sf_scene_flow_host_workspace_size": (sz, [i32, i32, PP]),
+            "sf_scene_flow_host": (i32, [P, P, P, P, P, i32, i32, PP, PC, P, P, P, P, P, sz, P]),
+            "sf_trace_arm": (i32, [P, i32, P]),
+            "sf_trace_disarm": (i32, []),
+            "sf_kernel_launches": (ctypes.c_uint64, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(fn, st):
+    if st != SF_OK:
+        raise SFError(fn, st)
+
+
+def _dev(t, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{name} must be a CUDA tensor of dtype {dtype}")
+    return t
+
+
+# ---- calls with the ABI's names ------------------------------------------
+
+def sf_census(img, cw=9, ch=7, out=None, stream=None):
+    _dev(img, torch.uint8, "img")
+    H, W = img.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.int64, device=img.device)
+    _check("sf_census", load().sf_census(_ptr(img), W, H, img.stride(0), cw, ch, _ptr(out),
+                                         _stream(stream)))
+    return out
+
+
+def sf_cost_volume(ref, other, p: SgmParams, ref_is_right=False, out=None, stream=None):
+    _dev(ref, torch.uint8, "ref")
+    _dev(other, torch.uint8, "other")
+    H, W = ref.shape
+    if out is None:
+        out = torch.empty((H, W, p.D), dtype=torch.uint8, device=ref.device)
+    _check("sf_cost_volume", load().sf_cost_volume(_ptr(ref), _ptr(other), W, H, ref.stride(0),
+                                                   ctypes.byref(p), int(ref_is_right), _ptr(out),
+                                                   _stream(stream)))
+    return out
+
+
+def sf_sgm_aggregate(cost, p: SgmParams, out=None, stream=None):
+    _dev(cost, torch.uint8, "cost")
+    H, W, D = cost.shape
+    if D != p.D:
+        raise ValueError("cost volume depth must equal p.D")
+    if out is None:
+        out = torch.empty((H, W, D), dtype=torch.int16, device=cost.device)
+    _check("sf_sgm_aggregate", load().sf_sgm_aggregate(_ptr(cost), W, H, ctypes.byref(p), _ptr(out),
+                                                       None, 0, _stream(stream)))
+    return out
+
+
+def sf_disparity_select(agg, subpixel=True, dint=None, dsub=None, stream=None):
+    _dev(agg, torch.int16, "agg")
+    H, W, D = agg.shape
+    if dint is None:
+        dint = torch.empty((H, W), dtype=torch.int16, device=agg.device)
+    if dsub is None:
+        dsub = torch.empty((H, W), dtype=torch.float32, device=agg.device)
+    _check("sf_disparity_select", load().sf_disparity_select(_ptr(agg), W, H, D, int(subpixel),
+                                                             _ptr(dint), _ptr(dsub), _stream(stream)))
+    return dint, dsub
+
+
+def sf_lr_check(dL, dR, dL_sub, tol=1, valid=None, disp=None, stream=None):
+    H, W = dL.shape
+    if valid is None:
+        valid = torch.empty((H, W), dtype=torch.uint8, device=dL.device)
+    if disp is None:
+        disp = torch.empty((H, W), dtype=torch.float32, device=dL.device)
+    _check("sf_lr_check", load().sf_lr_check(_ptr(dL), _ptr(dR), _ptr(dL_sub), W, H, tol,
+                                             _ptr(valid), _ptr(disp), _stream(stream)))
+    return valid, disp
+
+
+def sf_combine_sceneflow(D0, D1, flow, cam: Camera, want_motion=True, want_point=True, out=None,
+                         stream=None):
+    H, W = D0.shape
+    dev = D0.device
+    if out is None:
+        out = {
+            "s4": torch.empty((H, W, 4), dtype=torch.float32, device=dev),
+            "motion": torch.empty((H, W, 3), dtype=torch.float32, device=dev) if want_motion else None,
+            "point": torch.empty((H, W, 3), dtype=torch.float32, device=dev) if want_point else None,
+            "valid": torch.empty((H, W), dtype=torch.uint8, device=dev),
+        }
+    _check("sf_combine_sceneflow",
+           load().sf_combine_sceneflow(_ptr(D0), _ptr(D1), _ptr(flow), W, H, ctypes.byref(cam),
+                                       _ptr(out["s4"]), _ptr(out["motion"]), _ptr(out["point"]),
+                                       _ptr(out["valid"]), _stream(stream)))
+    return out
+
+
+def sf_workspace_size(W, H, p: SgmParams):
+    return int(load().sf_workspace_size(W, H, ctypes.byref(p)))
+
+
+def workspace(W, H, p: SgmParams, device="cuda"):
+    n = sf_workspace_size(W, H, p)
+    if n == 0:
+        raise ValueError("invalid size or parameters")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def sf_sgm_full(left, right, p: SgmParams, ws=None, out=None, stream=None):
+    _dev(left, torch.uint8, "left")
+    _dev(right, torch.uint8, "right")
+    H, W = left.shape
+    dev = left.device
+    if ws is None:
+        ws = workspace(W, H, p, dev)
+    if out is None:
+        out = {"dL": torch.empty((H, W), dtype=torch.int16, device=dev),
+               "dR": torch.empty((H, W), dtype=torch.int16, device=dev),
+               "valid": torch.empty((H, W), dtype=torch.uint8, device=dev),
+               "disp": torch.empty((H, W), dtype=torch.float32, device=dev)}
+    _check("sf_sgm_full", load().sf_sgm_full(_ptr(left), _ptr(right), W, H, left.stride(0),
+                                             ctypes.byref(p), _ptr(out["dL"]), _ptr(out["dR"]),
+                                             _ptr(out["valid"]), _ptr(out["disp"]), _ptr(ws),
+                                             ws.numel(), _stream(stream)))
+    return out
+
+
+def alloc_scene_flow_outputs(W, H, device="cuda", motion=True, point=True, disparities=True):
+    f32 = torch.float32
+    return {"s4": torch.empty((H, W, 4), dtype=f32, device=device),
+            "motion": torch.empty((H, W, 3), dtype=f32, device=device) if motion else None,
+            "point": torch.empty((H, W, 3), dtype=f32, device=device) if point else None,
+            "valid": torch.empty((H, W), dtype=torch.uint8, device=device),
+            "D0": torch.empty((H, W), dtype=f32, device=device) if disparities else None,
+            "D1": torch.empty((H, W), dtype=f32, device=device) if disparities else None}
+
+
+def sf_scene_flow(imgs, flow, p: SgmParams, cam: Camera, ws=None, out=None, stream=None):
+    """imgs = (left_t, right_t, left_t1, right_t1), uint8 [H][W] CUDA tensors."""
+    for k, im in enumerate(imgs):
+        _dev(im, torch.uint8, f"imgs[{k}]")
+    _dev(flow, torch.float32, "flow")
+    H, W = imgs[0].shape
+    dev = imgs[0].device
+    if ws is None:
+        ws = workspace(W, H, p, dev)
+    if out is None:
+        out = alloc_scene_flow_outputs(W, H, dev)
+    _check("sf_scene_flow",
+           load().sf_scene_flow(_ptr(imgs[0]), _ptr(imgs[1]), _ptr(imgs[2]), _ptr(imgs[3]),
+                                imgs[0].stride(0), _ptr(flow), W, H, ctypes.byref(p),
+                                ctypes.byref(cam), _ptr(out["s4"]), _ptr(out["motion"]),
+                                _ptr(out["point"]), _ptr(out["valid"]), _ptr(out["D0"]),
+                                _ptr(out["D1"]), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def sf_scene_flow_host_workspace_size(W, H, p: SgmParams):
+    return int(load().sf_scene_flow_host_workspace_size(W, H, ctypes.byref(p)))
+
+
+def sf_scene_flow_host(imgs, flow, p: SgmParams, cam: Camera, dev_ws, out, stream=None):
+    """Host-buffer variant: imgs / flow / out are CPU tensors (pinned for async
+    copies); dev_ws is a CUDA uint8 tensor of sf_scene_flow_host_workspace_size."""
+    H, W = imgs[0].shape
+    _check("sf_scene_flow_host",
+           load().sf_scene_flow_host(_ptr(imgs[0]), _ptr(imgs[1]), _ptr(imgs[2]), _ptr(imgs[3]),
+                                     _ptr(flow), W, H, ctypes.byref(p), ctypes.byref(cam),
+                                     _ptr(out["s4"]), _ptr(out.get("motion")),
+                                     _ptr(out.get("point")), _ptr(out["valid"]), _ptr(dev_ws),
+                                     dev_ws.numel(), _stream(stream)))
+    return out
+
+
+class StageTracer:
+    """Arms libsf's tracer with a pool of CUDA events; after the traced work
+    has finished, ``durations()`` returns {stage name: [ms, ...]}."""
+
+    def __init__(self, n_records=4096):
+        self.events = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_records)]
+        for e in self.events:
+            e.record()            # materialise the handles
+        torch.cuda.synchronize()
+        self._handles = (ctypes.c_void_p * len(self.events))(
+            *[ctypes.c_void_p(e.cuda_event) for e in self.events])
+        self._stages = (ctypes.c_int32 * n_records)()
+        self.records = 0
+
+    def __enter__(self):
+        _check("sf_trace_arm", load().sf_trace_arm(self._handles, len(self.events), self._stages))
+        return self
+
+    def __exit__(self, *exc):
+        self.records = load().sf_trace_disarm()
+        return False
+
+    def durations(self):
+        torch.cuda.synchronize()
+        out = {}
+        for k in range(self.records):
+            name = STAGE_NAMES[self._stages[k]]
+            ms = self.events[2 * k].elapsed_time(self.events[2 * k + 1])
+            out.setdefault(name, []).append(ms)
+        return out
+
+
+def kernel_launches():
+    return int(load().sf_kernel_launches())

@@ -1,0 +1,126 @@
+// Census transform and Hamming matching-cost volume (SGM matching cost,
+// Sec. 3.1 of arXiv 1801.04720).
+#include "sf_internal.cuh"
+
+namespace sf {
+
+namespace {
+
+constexpr int kCensusTX = 32, kCensusTY = 8;
+
+// One thread per pixel; the block stages its (TY + 2ry) x (TX + 2rx) window
+// of edge-clamped pixels in shared memory.
+template <int RX, int RY>
+__global__ void __launch_bounds__(kCensusTX* kCensusTY)
+    census_kernel(const uint8_t* __restrict__ img, int W, int H, int pitch, int rx, int ry,
+                  uint64_t* __restrict__ out) {
+  extern __shared__ uint8_t tile[];
+  const int RXv = RX > 0 ? RX : rx, RYv = RY > 0 ? RY : ry;
+  const int tw = kCensusTX + 2 * RXv, th = kCensusTY + 2 * RYv;
+  const int x0 = blockIdx.x * kCensusTX - RXv, y0 = blockIdx.y * kCensusTY - RYv;
+  for (int i = threadIdx.y * kCensusTX + threadIdx.x; i < tw * th; i += kCensusTX * kCensusTY) {
+    const int ty = i / tw, tx = i - ty * tw;
+    const int gx = clampi(x0 + tx, 0, W - 1), gy = clampi(y0 + ty, 0, H - 1);
+    tile[i] = img[(size_t)gy * pitch + gx];
+  }
+  __syncthreads();
+  const int x = blockIdx.x * kCensusTX + threadIdx.x, y = blockIdx.y * kCensusTY + threadIdx.y;
+  if (x >= W || y >= H) return;
+  uint64_t bits;
+  if (RX > 0)
+    bits = census_window<RX, RY>(tile, tw, threadIdx.x + RX, threadIdx.y + RY);
+  else
+    bits = census_window_rt(tile, tw, threadIdx.x + rx, threadIdx.y + ry, rx, ry);
+  out[(size_t)y * W + x] = bits;
+}
+
+// Cost volume of one image row segment [xs, xs + kCostTX): the block computes
+// the census strings it needs from the raw images, then writes
+// cost[y][x][d] with consecutive threads on consecutive d (coalesced).
+constexpr int kCostTX = 32, kCostThreads = 256;
+
+__global__ void __launch_bounds__(kCostThreads)
+    cost_kernel(const uint8_t* __restrict__ ref, const uint8_t* __restrict__ other, int W, int H,
+                int pitch, int rx, int ry, int D, int ref_is_right, int cmax,
+                uint8_t* __restrict__ cost) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int y = blockIdx.y;
+  const int xs = blockIdx.x * kCostTX;
+  const int nref = min(kCostTX, W - xs);
+  // candidate range in the other image
+  const int o_lo = ref_is_right ? xs : max(0, xs - (D - 1));
+  const int o_hi = ref_is_right ? min(W, xs + nref + D - 1) : xs + nref;  // exclusive
+  const int nother = o_hi - o_lo;
+  uint64_t* c_ref = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* c_oth = c_ref + kCostTX;
+  uint8_t* tile = reinterpret_cast<uint8_t*>(c_oth + (kCostTX + SF_MAX_DISPARITY));
+  const int th = 2 * ry + 1;
+  // ref tile
+  {
+    const int tw = nref + 2 * rx;
+    for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+      const int ty = i / tw, tx = i - ty * tw;
+      tile[i] = ref[(size_t)clampi(y - ry + ty, 0, H - 1) * pitch + clampi(xs - rx + tx, 0, W - 1)];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nref; i += blockDim.x)
+      c_ref[i] = census_window_rt(tile, tw, i + rx, ry, rx, ry);
+    __syncthreads();
+  }
+  // other tile
+  {
+    const int tw = nother + 2 * rx;
+    for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+      const int ty = i / tw, tx = i - ty * tw;
+      tile[i] =
+          other[(size_t)clampi(y - ry + ty, 0, H - 1) * pitch + clampi(o_lo - rx + tx, 0, W - 1)];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nother; i += blockDim.x)
+      c_oth[i] = census_window_rt(tile, tw, i + rx, ry, rx, ry);
+    __syncthreads();
+  }
+  const int total = nref * D;
+  uint8_t* row = cost + ((size_t)y * W + xs) * D;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int px = i / D, d = i - px * D;
+    const int x = xs + px;
+    const int xo = ref_is_right ? x + d : x - d;
+    int c = cmax;
+    if (xo >= 0 && xo < W) c = __popcll(c_ref[px] ^ c_oth[xo - o_lo]);
+    row[i] = (uint8_t)c;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_census(const uint8_t* img, int W, int H, int pitch, int cw, int ch, uint64_t* out,
+                          cudaStream_t s) {
+  StageTrace trace(SF_STAGE_CENSUS, s);
+  count_launches(1);
+  const int rx = cw / 2, ry = ch / 2;
+  dim3 block(kCensusTX, kCensusTY);
+  dim3 grid((W + kCensusTX - 1) / kCensusTX, (H + kCensusTY - 1) / kCensusTY);
+  const size_t smem = (size_t)(kCensusTX + 2 * rx) * (kCensusTY + 2 * ry);
+  if (cw == 9 && ch == 7)
+    census_kernel<4, 3><<<grid, block, smem, s>>>(img, W, H, pitch, rx, ry, out);
+  else
+    census_kernel<0, 0><<<grid, block, smem, s>>>(img, W, H, pitch, rx, ry, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cost_volume(const uint8_t* ref, const uint8_t* other, int W, int H, int pitch,
+                               int cw, int ch, int D, int ref_is_right, uint8_t* cost,
+                               cudaStream_t s) {
+  StageTrace trace(SF_STAGE_COST, s);
+  count_launches(1);
+  const int rx = cw / 2, ry = ch / 2;
+  dim3 grid((W + kCostTX - 1) / kCostTX, H);
+  const size_t smem = sizeof(uint64_t) * (2 * kCostTX + SF_MAX_DISPARITY) +
+                      (size_t)(kCostTX + SF_MAX_DISPARITY + 2 * rx) * (2 * ry + 1);
+  cost_kernel<<<grid, kCostThreads, smem, s>>>(ref, other, W, H, pitch, rx, ry, D, ref_is_right,
+                                               cw * ch - 1, cost);
+  return cudaGetLastError();
+}
+
+}  // namespace sf
