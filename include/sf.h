@@ -99,7 +99,8 @@ sf_status sf_cost_volume(const uint8_t* ref, const uint8_t* other, int32_t W, in
                          int32_t pitch, const sf_sgm_params* p, int32_t ref_is_right,
                          uint8_t* cost_out, void* stream);
 
-/* Workspace bytes that sf_sgm_aggregate needs (0 today; kept for the ABI). */
+/* Workspace bytes with which sf_sgm_aggregate runs the fused band sweeps
+ * (0 when D is not a multiple of 16: the staged kernels need none). */
 size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p);
 
 /* Semi-global aggregation over the enabled paths (Sec. 3.1, "eight different
@@ -107,7 +108,10 @@ size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p)
  *   L_r(p,d) = C(p,d) + min(L_r(p-r,d), L_r(p-r,d+-1) + P1, min_k L_r(p-r,k) + P2)
  *              - min_k L_r(p-r,k),
  * and L_r(p,d) = C(p,d) where p - r is outside the image.  Exact integers.
- * cost: uint8 [H][W][D]; agg_out: uint16 [H][W][D]. */
+ * cost: uint8 [H][W][D]; agg_out: uint16 [H][W][D].  With D % 16 == 0, a
+ * 16-byte aligned cost volume and a workspace of at least
+ * sf_aggregate_workspace_size() bytes the fused band sweeps run; otherwise
+ * (workspace may then be NULL) one kernel per path. */
 sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
                            uint16_t* agg_out, void* workspace, size_t ws_bytes, void* stream);
 
@@ -217,6 +221,21 @@ int32_t sf_trace_disarm(void);
 /* Number of CUDA kernels this library has launched in the calling process
  * (all threads), for launch accounting. */
 uint64_t sf_kernel_launches(void);
+
+/* Process-wide choice between the fused stereo kernels (1, default) and the
+ * staged kernels (0: stored cost volume, one kernel per path, separate
+ * selection).  Both compute the same integers; the staged kernels also serve
+ * requests the fused ones do not take (a row of W*D distances beyond one
+ * CTA's shared memory, D not a multiple of 16 in sf_sgm_aggregate). */
+sf_status sf_set_fused(int32_t enable);
+
+/* Reads the device-side error word of a workspace used by sf_sgm_full
+ * (npairs = 1) or sf_scene_flow (npairs = 2) with these sizes; waits for
+ * `stream`.  Returns SF_ERR_TIMEOUT if a bounded inter-CTA wait of the band
+ * sweeps gave up (the outputs of that call are then invalid), SF_OK
+ * otherwise. */
+sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const sf_sgm_params* p,
+                             int32_t npairs, void* stream);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ EXPORTED = [
     "sf_aggregate_workspace_size", "sf_sgm_aggregate", "sf_disparity_select", "sf_lr_check",
     "sf_combine_sceneflow", "sf_workspace_size", "sf_sgm_full", "sf_scene_flow",
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
-    "sf_trace_disarm", "sf_kernel_launches",
+    "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
 ]
 
 STAGE_NAMES = ["census", "cost", "aggregate", "select", "lrcheck", "combine", "sgm_sweep"]
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
             "sf_trace_arm": (i32, [P, i32, P]),
             "sf_trace_disarm": (i32, []),
             "sf_kernel_launches": (ctypes.c_uint64, []),
+            "sf_set_fused": (i32, [i32]),
+            "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -155,16 +157,36 @@ def sf_cost_volume(ref, other, p: SgmParams, ref_is_right=False, out=None, strea
     return out
 
 
-def sf_sgm_aggregate(cost, p: SgmParams, out=None, stream=None):
+def sf_aggregate_workspace_size(W, H, p: SgmParams):
+    return int(load().sf_aggregate_workspace_size(W, H, ctypes.byref(p)))
+
+
+def sf_sgm_aggregate(cost, p: SgmParams, out=None, ws="auto", stream=None):
+    """ws="auto" allocates the fused-path workspace; ws=None runs the staged
+    kernels (one per path)."""
     _dev(cost, torch.uint8, "cost")
     H, W, D = cost.shape
     if D != p.D:
         raise ValueError("cost volume depth must equal p.D")
     if out is None:
         out = torch.empty((H, W, D), dtype=torch.int16, device=cost.device)
+    if isinstance(ws, str):
+        n = sf_aggregate_workspace_size(W, H, p)
+        ws = torch.empty(n, dtype=torch.uint8, device=cost.device) if n else None
+    nbytes = ws.numel() if ws is not None else 0
     _check("sf_sgm_aggregate", load().sf_sgm_aggregate(_ptr(cost), W, H, ctypes.byref(p), _ptr(out),
-                                                       None, 0, _stream(stream)))
+                                                       _ptr(ws), nbytes, _stream(stream)))
     return out
+
+
+def sf_set_fused(enable: bool):
+    _check("sf_set_fused", load().sf_set_fused(int(bool(enable))))
+
+
+def sf_check_workspace(ws, W, H, p: SgmParams, npairs, stream=None):
+    """Raises SFError(SF_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check("sf_check_workspace", load().sf_check_workspace(_ptr(ws), W, H, ctypes.byref(p), npairs,
+                                                           _stream(stream)))
 
 
 def sf_disparity_select(agg, subpixel=True, dint=None, dsub=None, stream=None):

@@ -4,6 +4,7 @@
 
 #include <atomic>
 
+#include "sf_fused.cuh"
 #include "sf_internal.cuh"
 
 using namespace sf;
@@ -143,6 +144,132 @@ sf_status sgm_full_impl(const uint8_t* left, const uint8_t* right, int W, int H,
   return SF_OK;
 }
 
+bool g_use_fused = true;
+
+// Whether the fused stereo kernels handle this request (otherwise the staged
+// kernels above run): a whole image row of distances must fit one CTA's
+// shared memory.
+bool fused_eligible(int W, int H, const sf_sgm_params* p) {
+  (void)H;
+  if (!g_use_fused) return false;
+  return fused::cost_pair_smem(W, p->D) <= 227u * 1024u;
+}
+
+// Workspace of the fused path for `npairs` stereo pairs (2 passes each).
+struct FusedLayout {
+  size_t census, cost, hvol, sdown, bs, flags, err, dint, dsub, valid, disp, total;
+  FusedLayout(int W, int H, int D, int npairs) {
+    const size_t N = (size_t)W * H;
+    const int Dp = fused::padded_d(D), npass = 2 * npairs;
+    const int J = (W + fused::kTW - 1) / fused::kTW;
+    size_t o = 0;
+    census = o; o = align_up(o + (size_t)npass * N * sizeof(uint64_t), 256);
+    cost = o; o = align_up(o + (size_t)npass * N * Dp, 256);
+    hvol = o; o = align_up(o + (size_t)npass * 2 * N * Dp, 256);
+    sdown = o; o = align_up(o + fused::sdown_bytes(W, H, D, npass), 256);
+    bs = o; o = align_up(o + fused::bs_bytes(W, D, npass), 256);
+    flags = o; o = align_up(o + (size_t)2 * npass * J * sizeof(int), 256);
+    err = o; o = align_up(o + 256, 256);
+    dint = o; o = align_up(o + (size_t)npass * N * sizeof(int16_t), 256);
+    dsub = o; o = align_up(o + (size_t)npairs * N * sizeof(float), 256);
+    valid = o; o = align_up(o + (size_t)npairs * N, 256);
+    disp = o; o = align_up(o + (size_t)npairs * N * sizeof(float), 256);
+    total = o;
+  }
+};
+
+constexpr long long kSpinLimit = 1ll << 24;   // bounded neighbour wait (~1 s)
+
+// Band sweeps + horizontal paths for `npass` cost volumes already in place.
+sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8_t* ws,
+                          const FusedLayout& lay, const fused::PassIO* io_up, cudaStream_t s) {
+  const size_t N = (size_t)W * H;
+  const int Dp = fused::padded_d(p->D);
+  const int J = (W + fused::kTW - 1) / fused::kTW;
+  uint8_t* cost = ws + lay.cost;
+  uint8_t* hvol = ws + lay.hvol;
+  fused::HLineArgs ha{};
+  ha.W = W; ha.H = H; ha.D = p->D; ha.Dp = Dp; ha.npass = npass; ha.P1 = p->P1; ha.P2 = p->P2;
+  ha.path_mask = p->path_mask;
+  for (int k = 0; k < npass; k++) {
+    ha.cost[k] = io_up[k].cost ? io_up[k].cost : cost + (size_t)k * N * Dp;
+    ha.hfwd[k] = hvol + (size_t)(2 * k) * N * Dp;
+    ha.hbwd[k] = hvol + (size_t)(2 * k + 1) * N * Dp;
+  }
+  SF_TRY_CUDA(fused::launch_hline(ha, s));
+  int* flags = reinterpret_cast<int*>(ws + lay.flags);
+  SF_TRY_CUDA(cudaMemsetAsync(flags, 0, (size_t)2 * npass * J * sizeof(int), s));
+  SF_TRY_CUDA(cudaMemsetAsync(ws + lay.err, 0, sizeof(int), s));
+  fused::SweepArgs sa{};
+  sa.W = W; sa.H = H; sa.D = p->D; sa.Dp = Dp; sa.P1 = p->P1; sa.P2 = p->P2; sa.J = J;
+  sa.nb = (H + fused::kTH - 1) / fused::kTH; sa.items = npass * J; sa.subpixel = p->subpixel;
+  sa.path_mask = p->path_mask;
+  sa.en_h0 = (p->path_mask >> 0) & 1u;
+  sa.en_h1 = (p->path_mask >> 1) & 1u;
+  sa.sdown = reinterpret_cast<uint32_t*>(ws + lay.sdown);
+  sa.bs = ws + lay.bs;
+  sa.err = reinterpret_cast<int*>(ws + lay.err);
+  sa.spin_limit = kSpinLimit;
+  for (int k = 0; k < npass; k++) {
+    sa.io[k].cost = ha.cost[k];
+    sa.io[k].hfwd = ha.hfwd[k];
+    sa.io[k].hbwd = ha.hbwd[k];
+  }
+  sa.flags = flags;
+  SF_TRY_CUDA(fused::launch_sweep(sa, false, s));
+  for (int k = 0; k < npass; k++) {
+    sa.io[k].dint = io_up[k].dint;
+    sa.io[k].dsub = io_up[k].dsub;
+    sa.io[k].S = io_up[k].S;
+  }
+  sa.flags = flags + npass * J;
+  SF_TRY_CUDA(fused::launch_sweep(sa, true, s));
+  return SF_OK;
+}
+
+// Fused SGM for `npairs` stereo pairs: census, one distance computation per
+// pair, both reference passes, the left-right check.
+sf_status run_fused_pairs(const uint8_t* const* left, const uint8_t* const* right, int npairs,
+                          int W, int H, int pitch, const sf_sgm_params* p, int16_t* const* dL_out,
+                          int16_t* const* dR_out, uint8_t* const* valid_out, float* const* disp_out,
+                          uint8_t* ws, cudaStream_t s) {
+  FusedLayout lay(W, H, p->D, npairs);
+  const size_t N = (size_t)W * H;
+  const int Dp = fused::padded_d(p->D), npass = 2 * npairs;
+  const int cmax = p->census_w * p->census_h - 1;
+  uint64_t* census = reinterpret_cast<uint64_t*>(ws + lay.census);
+  uint8_t* cost = ws + lay.cost;
+  for (int k = 0; k < npairs; k++) {
+    SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, census + (2 * k) * N, s));
+    SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, census + (2 * k + 1) * N, s));
+  }
+  for (int k = 0; k < npairs; k++)
+    SF_TRY_CUDA(fused::launch_cost_pair(census + (2 * k) * N, census + (2 * k + 1) * N, W, H, p->D, Dp,
+                                        cmax, cost + (size_t)(2 * k) * N * Dp,
+                                        cost + (size_t)(2 * k + 1) * N * Dp, s));
+  int16_t* dint = reinterpret_cast<int16_t*>(ws + lay.dint);
+  float* dsub = reinterpret_cast<float*>(ws + lay.dsub);
+  fused::PassIO io[fused::kMaxPass] = {};
+  for (int k = 0; k < npairs; k++) {
+    io[2 * k].dint = (dL_out && dL_out[k]) ? dL_out[k] : dint + (size_t)(2 * k) * N;
+    io[2 * k].dsub = dsub + (size_t)k * N;
+    io[2 * k + 1].dint = (dR_out && dR_out[k]) ? dR_out[k] : dint + (size_t)(2 * k + 1) * N;
+  }
+  sf_status st = run_aggregation(W, H, p, npass, ws, lay, io, s);
+  if (st != SF_OK) return st;
+  for (int k = 0; k < npairs; k++) {
+    uint8_t* valid = (valid_out && valid_out[k]) ? valid_out[k] : ws + lay.valid + (size_t)k * N;
+    SF_TRY_CUDA(launch_lr_check(io[2 * k].dint, io[2 * k + 1].dint, io[2 * k].dsub, W, H, p->lr_tol,
+                                valid, disp_out[k], s));
+  }
+  return SF_OK;
+}
+
+size_t workspace_bytes(int W, int H, const sf_sgm_params* p, int npairs) {
+  if (fused_eligible(W, H, p)) return std::max(FusedLayout(W, H, p->D, npairs).total, Workspace(W, H, p->D).total);
+  return Workspace(W, H, p->D).total;
+}
+
 }  // namespace
 
 extern "C" {
@@ -195,8 +322,9 @@ sf_status sf_cost_volume(const uint8_t* ref, const uint8_t* other, int32_t W, in
 }
 
 size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p) {
-  (void)W; (void)H; (void)p;
-  return 0;
+  if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
+  if (p->D % 16 != 0) return 0;   // staged kernels, no workspace
+  return FusedLayout(W, H, p->D, 1).total;
 }
 
 sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
@@ -207,8 +335,18 @@ sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_s
   if (!cost || !agg_out) return SF_ERR_INVALID_ARG;
   if ((st = check_params(p, W, H)) != SF_OK) return st;
   if (!aligned(agg_out, 2)) return SF_ERR_INVALID_ARG;
-  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg_out,
-                               (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  // fused sweeps when the volume is 16-disparity aligned and a workspace of
+  // sf_aggregate_workspace_size() bytes is given; staged kernels otherwise
+  if (g_use_fused && p->D % 16 == 0 && aligned(cost, 16) && workspace && aligned(workspace, 256) &&
+      ws_bytes >= FusedLayout(W, H, p->D, 1).total) {
+    FusedLayout lay(W, H, p->D, 1);
+    fused::PassIO io[fused::kMaxPass] = {};
+    io[0].cost = cost;
+    io[0].S = agg_out;
+    return run_aggregation(W, H, p, 1, (uint8_t*)workspace, lay, io, s);
+  }
+  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg_out, s));
   return SF_OK;
 }
 
@@ -253,7 +391,7 @@ sf_status sf_combine_sceneflow(const float* D0, const float* D1, const float* fl
 
 size_t sf_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p) {
   if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
-  return Workspace(W, H, p->D).total;
+  return workspace_bytes(W, H, p, 2);
 }
 
 sf_status sf_sgm_full(const uint8_t* left, const uint8_t* right, int32_t W, int32_t H,
@@ -264,8 +402,11 @@ sf_status sf_sgm_full(const uint8_t* left, const uint8_t* right, int32_t W, int3
   if (st != SF_OK) return st;
   if (!left || !right || !disp_out || !workspace || pitch < W) return SF_ERR_INVALID_ARG;
   if ((st = check_params(p, W, H)) != SF_OK) return st;
-  if (ws_bytes < Workspace(W, H, p->D).total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  if (ws_bytes < workspace_bytes(W, H, p, 1) || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
   if (!aligned(dL_out, 2) || !aligned(dR_out, 2) || !aligned(disp_out, 4)) return SF_ERR_INVALID_ARG;
+  if (fused_eligible(W, H, p))
+    return run_fused_pairs(&left, &right, 1, W, H, pitch, p, &dL_out, &dR_out, &valid_out, &disp_out,
+                           (uint8_t*)workspace, (cudaStream_t)stream);
   return sgm_full_impl(left, right, W, H, pitch, p, dL_out, dR_out, valid_out, disp_out,
                        (uint8_t*)workspace, (cudaStream_t)stream);
 }
@@ -282,19 +423,32 @@ sf_status sf_scene_flow(const uint8_t* left_t, const uint8_t* right_t, const uin
     return SF_ERR_INVALID_ARG;
   if ((st = check_params(p, W, H)) != SF_OK) return st;
   if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
-  Workspace lay(W, H, p->D);
-  if (ws_bytes < lay.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  if (ws_bytes < workspace_bytes(W, H, p, 2) || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
   if (!aligned(flow, 8) || !aligned(s4_out, 16) || !aligned(motion_out, 4) ||
       !aligned(point_out, 4) || !aligned(D0_out, 4) || !aligned(D1_out, 4))
     return SF_ERR_INVALID_ARG;
   uint8_t* ws = (uint8_t*)workspace;
   cudaStream_t s = (cudaStream_t)stream;
-  float* D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + lay.disp0);
-  float* D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + lay.disp1);
-  if ((st = sgm_full_impl(left_t, right_t, W, H, pitch, p, nullptr, nullptr, nullptr, D0, ws, s)) != SF_OK)
-    return st;
-  if ((st = sgm_full_impl(left_t1, right_t1, W, H, pitch, p, nullptr, nullptr, nullptr, D1, ws, s)) != SF_OK)
-    return st;
+  float* D0;
+  float* D1;
+  if (fused_eligible(W, H, p)) {
+    FusedLayout fl(W, H, p->D, 2);
+    D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + fl.disp);
+    D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + fl.disp) + (size_t)W * H;
+    const uint8_t* L[2] = {left_t, left_t1};
+    const uint8_t* R[2] = {right_t, right_t1};
+    float* disp[2] = {D0, D1};
+    if ((st = run_fused_pairs(L, R, 2, W, H, pitch, p, nullptr, nullptr, nullptr, disp, ws, s)) != SF_OK)
+      return st;
+  } else {
+    Workspace lay(W, H, p->D);
+    D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + lay.disp0);
+    D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + lay.disp1);
+    if ((st = sgm_full_impl(left_t, right_t, W, H, pitch, p, nullptr, nullptr, nullptr, D0, ws, s)) != SF_OK)
+      return st;
+    if ((st = sgm_full_impl(left_t1, right_t1, W, H, pitch, p, nullptr, nullptr, nullptr, D1, ws, s)) != SF_OK)
+      return st;
+  }
   SF_TRY_CUDA(launch_combine(D0, D1, flow, W, H, cam->f, cam->B, cam->cx, cam->cy, s4_out,
                              motion_out, point_out, valid_out, s));
   return SF_OK;
@@ -318,7 +472,7 @@ sf_status sf_scene_flow_host(const uint8_t* left_t, const uint8_t* right_t,
       !dev_workspace)
     return SF_ERR_INVALID_ARG;
   if ((st = check_params(p, W, H)) != SF_OK) return st;
-  const size_t base = Workspace(W, H, p->D).total;
+  const size_t base = workspace_bytes(W, H, p, 2);
   HostStaging hs(W, H, base);
   if (ws_bytes < hs.total || !aligned(dev_workspace, 256)) return SF_ERR_INVALID_ARG;
   uint8_t* ws = (uint8_t*)dev_workspace;
@@ -362,5 +516,25 @@ int32_t sf_trace_disarm(void) {
 }
 
 uint64_t sf_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sf_status sf_set_fused(int32_t enable) {
+  if (enable != 0 && enable != 1) return SF_ERR_INVALID_ARG;
+  g_use_fused = enable != 0;
+  return SF_OK;
+}
+
+sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const sf_sgm_params* p,
+                             int32_t npairs, void* stream) {
+  if (!workspace || !p || check_size(W, H) != SF_OK || (npairs != 1 && npairs != 2))
+    return SF_ERR_INVALID_ARG;
+  if (!fused_eligible(W, H, p)) return SF_OK;
+  FusedLayout lay(W, H, p->D, npairs);
+  int err = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  SF_TRY_CUDA(cudaMemcpyAsync(&err, (const uint8_t*)workspace + lay.err, sizeof(int),
+                              cudaMemcpyDeviceToHost, s));
+  SF_TRY_CUDA(cudaStreamSynchronize(s));
+  return err ? SF_ERR_TIMEOUT : SF_OK;
+}
 
 }  // extern "C"

@@ -75,12 +75,13 @@ AGG_CASES = [
 ] + [(37, 29, 40, 7, 86, 1 << r) for r in range(8)]
 
 
+@pytest.mark.parametrize("staged", [False, True])
 @pytest.mark.parametrize("W,H,D,P1,P2,mask", AGG_CASES)
-def test_aggregate_random_cost(sf, oracle_mod, W, H, D, P1, P2, mask):
+def test_aggregate_random_cost(sf, oracle_mod, W, H, D, P1, P2, mask, staged):
     rng = np.random.default_rng(W * 1000 + D)
     C = rng.integers(0, 63, size=(H, W, D), dtype=np.uint8)
     p = sf.params(D=D, P1=P1, P2=P2, path_mask=mask)
-    got = to_np(sf.sf_sgm_aggregate(to_dev(C), p), np.uint16)
+    got = to_np(sf.sf_sgm_aggregate(to_dev(C), p, ws=None if staged else "auto"), np.uint16)
     exp = oracle_mod.aggregate(C, P1, P2, mask)
     assert np.array_equal(got.astype(np.int32), exp)
 
@@ -148,8 +149,15 @@ def test_combine(sf, oracle_mod, W, H):
     assert_sceneflow_close(got, s4, motion, point, valid)
 
 
+@pytest.fixture(params=["fused", "staged"])
+def path(sf, request):
+    sf.sf_set_fused(request.param == "fused")
+    yield request.param
+    sf.sf_set_fused(True)
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
-def test_sgm_full_planes(sf, oracle_mod, seed):
+def test_sgm_full_planes(sf, oracle_mod, seed, path):
     q = synth.fronto_planes(seed=seed)
     p = sf.params(D=q.D)
     out = sf.sf_sgm_full(to_dev(q.left_t), to_dev(q.right_t), p)
@@ -160,8 +168,10 @@ def test_sgm_full_planes(sf, oracle_mod, seed):
     assert_nan_equal_close(to_np(out["disp"]), r["disp"], SUBPIXEL_ATOL, "disp")
 
 
-@pytest.mark.parametrize("W,H,D,seed", [(67, 53, 24, 5), (130, 41, 48, 6), (200, 60, 64, 7)])
-def test_sgm_full_ragged(sf, oracle_mod, W, H, D, seed):
+@pytest.mark.parametrize("W,H,D,seed", [(67, 53, 24, 5), (130, 41, 48, 6), (200, 60, 64, 7),
+                                        (33, 9, 16, 8), (97, 40, 100, 9), (130, 41, 192, 10),
+                                        (300, 25, 256, 11), (31, 13, 16, 12), (95, 19, 128, 13)])
+def test_sgm_full_ragged(sf, oracle_mod, W, H, D, seed, path):
     q = synth.fronto_planes(W=W, H=H, D=D, disparities=(2, D // 3, D - 5), seed=seed)
     p = sf.params(D=D)
     out = sf.sf_sgm_full(to_dev(q.left_t), to_dev(q.right_t), p)
@@ -204,7 +214,7 @@ def _scene_flow_parity(sf, oracle_mod, q, p_kw, oracle_results=None):
 
 
 @pytest.mark.parametrize("seed", [0, 1])
-def test_scene_flow_planes(sf, oracle_mod, seed):
+def test_scene_flow_planes(sf, oracle_mod, seed, path):
     q = synth.fronto_planes(seed=seed)
     got = _scene_flow_parity(sf, oracle_mod, q, dict(D=q.D))
     assert got["valid"].mean() > 0.3
