@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "sf_fused.cuh"
 #include "sf_internal.cuh"
@@ -168,7 +169,7 @@ struct FusedLayout {
     hvol = o; o = align_up(o + (size_t)npass * 2 * N * Dp, 256);
     sdown = o; o = align_up(o + fused::sdown_bytes(W, H, D, npass), 256);
     bs = o; o = align_up(o + fused::bs_bytes(W, D, npass), 256);
-    flags = o; o = align_up(o + (size_t)2 * npass * J * sizeof(int), 256);
+    flags = o; o = align_up(o + (size_t)2 * (npass * J + 1) * sizeof(int), 256);
     err = o; o = align_up(o + 256, 256);
     dint = o; o = align_up(o + (size_t)npass * N * sizeof(int16_t), 256);
     dsub = o; o = align_up(o + (size_t)npairs * N * sizeof(float), 256);
@@ -179,6 +180,31 @@ struct FusedLayout {
 };
 
 constexpr long long kSpinLimit = 1ll << 24;   // bounded neighbour wait (~1 s)
+
+// Side stream on which the horizontal-path kernel overlaps the down sweep
+// (one per device, created on first use; fork and join through events so the
+// pattern also works under CUDA graph capture of the caller's stream).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mu;
+SideStream g_side[64];
+
+cudaError_t side_stream(SideStream** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  SideStream& ss = g_side[dev];
+  if (!ss.s) {
+    if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+  }
+  *out = &ss;
+  return cudaSuccess;
+}
 
 // Band sweeps + horizontal paths for `npass` cost volumes already in place.
 sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8_t* ws,
@@ -196,13 +222,20 @@ sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8
     ha.hfwd[k] = hvol + (size_t)(2 * k) * N * Dp;
     ha.hbwd[k] = hvol + (size_t)(2 * k + 1) * N * Dp;
   }
-  SF_TRY_CUDA(fused::launch_hline(ha, s));
+  // the horizontal paths run beside the down sweep; the up sweep joins them
+  std::lock_guard<std::mutex> guard(g_side_mu);
+  SideStream* side = nullptr;
+  SF_TRY_CUDA(side_stream(&side));
+  SF_TRY_CUDA(cudaEventRecord(side->fork, s));
+  SF_TRY_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0));
+  SF_TRY_CUDA(fused::launch_hline(ha, side->s));
+  SF_TRY_CUDA(cudaEventRecord(side->join, side->s));
   int* flags = reinterpret_cast<int*>(ws + lay.flags);
-  SF_TRY_CUDA(cudaMemsetAsync(flags, 0, (size_t)2 * npass * J * sizeof(int), s));
+  SF_TRY_CUDA(cudaMemsetAsync(flags, 0, (size_t)2 * (npass * J + 1) * sizeof(int), s));
   SF_TRY_CUDA(cudaMemsetAsync(ws + lay.err, 0, sizeof(int), s));
   fused::SweepArgs sa{};
   sa.W = W; sa.H = H; sa.D = p->D; sa.Dp = Dp; sa.P1 = p->P1; sa.P2 = p->P2; sa.J = J;
-  sa.nb = (H + fused::kTH - 1) / fused::kTH; sa.items = npass * J; sa.subpixel = p->subpixel;
+  sa.nb = (H + fused::band_rows(p->D) - 1) / fused::band_rows(p->D); sa.items = npass * J; sa.subpixel = p->subpixel;
   sa.path_mask = p->path_mask;
   sa.en_h0 = (p->path_mask >> 0) & 1u;
   sa.en_h1 = (p->path_mask >> 1) & 1u;
@@ -216,6 +249,7 @@ sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8
     sa.io[k].hbwd = ha.hbwd[k];
   }
   sa.flags = flags;
+  sa.task_counter = flags + 2 * npass * J;
   SF_TRY_CUDA(fused::launch_sweep(sa, false, s));
   for (int k = 0; k < npass; k++) {
     sa.io[k].dint = io_up[k].dint;
@@ -223,6 +257,8 @@ sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8
     sa.io[k].S = io_up[k].S;
   }
   sa.flags = flags + npass * J;
+  sa.task_counter = flags + 2 * npass * J + 1;
+  SF_TRY_CUDA(cudaStreamWaitEvent(s, side->join, 0));
   SF_TRY_CUDA(fused::launch_sweep(sa, true, s));
   return SF_OK;
 }

@@ -10,21 +10,21 @@
 //      integer rate, so sharing the distances between both passes halves it.
 //   2. hline_kernel: the two horizontal paths (+1,0) and (-1,0), each row an
 //      independent line; two rows share a register (u16x2 lanes).  Writes
-//      L_r as uint8 volumes.
+//      L_r as uint8 volumes.  Runs beside the down sweep.
 //   3. sweep_kernel<DOWN>: paths (0,+1), (+1,+1), (-1,+1) walking the image
-//      top to bottom in bands of TH rows.  Each CTA owns a strip of 32
-//      columns; the diagonal paths enter a strip from its neighbours, so the
-//      band is computed on a trapezoid with TH-1 halo columns per side from
-//      the neighbours' band-end states (global memory, published with
-//      release/acquire flags; waits are bounded).  Writes the partial sum
-//      S_down in a tile layout.
+//      top to bottom in bands of halo+1 rows.  A task is one band of one
+//      32-column strip of one pass; the diagonal paths enter a strip from its
+//      neighbours, so the band is computed on a trapezoid with `halo` extra
+//      columns per side, started from the neighbours' band-end states (global
+//      memory, published with release/acquire flags; waits are bounded).
+//      Writes the partial sum S_down in a tile layout.
 //   4. sweep_kernel<UP>: paths (0,-1), (-1,-1), (+1,-1) bottom to top, adds
 //      S_down and both horizontal paths, and fuses winner-take-all and the
 //      parabolic subpixel step (or writes the full aggregated cost).
-// All arithmetic is exact integer math in 16-bit lanes (L_r <= cmax + P2,
-// S <= 8 (cmax + P2) < 2^16).
-#include <cooperative_groups.h>
-
+// Tasks come from a band-major queue, so the sweep time is the band chain
+// (bands x per-band latency); each task is spread over many threads to keep
+// that latency short.  All arithmetic is exact integer math in 16-bit lanes
+// (L_r <= cmax + P2, S <= 8 (cmax + P2) < 2^16).
 #include "sf_fused.cuh"
 #include "sgm_common.cuh"
 
@@ -102,9 +102,16 @@ __global__ void __launch_bounds__(512)
 // ---------------------------------------------------------------------------
 // 2. horizontal paths
 // ---------------------------------------------------------------------------
-template <int CHUNKS>
-__global__ void __launch_bounds__(256)
+constexpr int kHlineThreads = 256;
+constexpr int kHlinePrefetch = 8;   // cost columns in flight per thread
+
+template <int DC, int CHUNKS>
+__global__ void __launch_bounds__(kHlineThreads)
     hline_kernel(HLineArgs a) {
+  using V = typename ByteVec<DC>::T;
+  // per-thread ring of prefetched cost columns: [slot][row y0 / y1][thread]
+  extern __shared__ __align__(16) uint8_t hsmem[];
+  V* ring = reinterpret_cast<V*>(hsmem);
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int item = gt / CHUNKS;
   const int q = gt - item * CHUNKS;
@@ -115,54 +122,67 @@ __global__ void __launch_bounds__(256)
   const int rem = item - p * per_pass;
   const int dir = rem / rows2;           // 0: (+1,0), 1: (-1,0)
   const int rp = rem - dir * rows2;
-  const int y0 = 2 * rp, y1 = min(2 * rp + 1, a.H - 1);
+  const int y0 = active ? 2 * rp : 0, y1 = active ? min(2 * rp + 1, a.H - 1) : 0;
   const int W = a.W, Dp = a.Dp;
-  // chunks at or past the padded depth hold no data (D not a power of two)
-  const bool enabled = active && ((a.path_mask >> dir) & 1u) && q * kDC < Dp;
-  const uint8_t* C = a.cost[p];
-  uint8_t* out = dir == 0 ? a.hfwd[p] : a.hbwd[p];
-  const int d0 = q * kDC;
-  const bool pad = d0 + kDC > a.D;
-  const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
-  uint32_t L[kDC], Cr[kDC], N[kDC];
+  const int d0 = q * DC;
+  // chunks at or past the padded depth hold no data
+  const bool enabled = active && ((a.path_mask >> dir) & 1u) && d0 < Dp;
+  const uint8_t* C = a.cost[0];
+  uint8_t* out = dir == 0 ? a.hfwd[0] : a.hbwd[0];
 #pragma unroll
-  for (int i = 0; i < kDC; i++) L[i] = 0;
-  uint32_t m = 0;
-  const int step = dir == 0 ? 1 : -1;
-  int x = dir == 0 ? 0 : W - 1;
-  // prefetch the first column's costs
-  uint4 ca = make_uint4(0, 0, 0, 0), cb = ca;
-  if (enabled) {
-    ca = __ldg(reinterpret_cast<const uint4*>(C + ((size_t)y0 * W + x) * Dp + d0));
-    cb = __ldg(reinterpret_cast<const uint4*>(C + ((size_t)y1 * W + x) * Dp + d0));
+  for (int k = 1; k < kMaxPass; k++) {   // select without indexing the parameter array
+    if (p == k) {
+      C = a.cost[k];
+      out = dir == 0 ? a.hfwd[k] : a.hbwd[k];
+    }
   }
+  const bool pad = d0 + DC > a.D;
+  const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
+  const int step = dir == 0 ? 1 : -1;
+  const int xstart = dir == 0 ? 0 : W - 1;
+  auto issue = [&](int s) {   // prefetch column number s into its ring slot
+    const int xs = xstart + s * step;
+    const bool ok = enabled && s < W;
+    V* dst = ring + (s % kHlinePrefetch) * 2 * kHlineThreads + threadIdx.x;
+    const uint8_t* src0 = ok ? C + ((size_t)y0 * W + xs) * Dp + d0 : C;
+    const uint8_t* src1 = ok ? C + ((size_t)y1 * W + xs) * Dp + d0 : C;
+    cp_async<DC>(dst, src0, ok);
+    cp_async<DC>(dst + kHlineThreads, src1, ok);
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int s = 0; s < kHlinePrefetch - 1; s++) issue(s);
+  uint32_t L[DC], Cr[DC], N[DC];
+#pragma unroll
+  for (int i = 0; i < DC; i++) L[i] = 0;
+  uint32_t m = 0;
+  int x = xstart;
   for (int s = 0; s < W; s++, x += step) {
-    bytes_to_pairs(ca, cb, Cr);
+    issue(s + kHlinePrefetch - 1);
+    cp_async_wait<kHlinePrefetch - 1>();
+    const V* src = ring + (s % kHlinePrefetch) * 2 * kHlineThreads + threadIdx.x;
+    bytes_to_pairs<DC>(src[0], src[kHlineThreads], Cr);
     if (pad) {
 #pragma unroll
-      for (int i = 0; i < kDC; i++)
+      for (int i = 0; i < DC; i++)
         if (d0 + i >= a.D) Cr[i] = kPadCost2;
     }
-    if (enabled && s + 1 < W) {
-      const int xn = x + step;
-      ca = __ldg(reinterpret_cast<const uint4*>(C + ((size_t)y0 * W + xn) * Dp + d0));
-      cb = __ldg(reinterpret_cast<const uint4*>(C + ((size_t)y1 * W + xn) * Dp + d0));
-    }
-    uint32_t left = __shfl_up_sync(0xffffffffu, L[kDC - 1], 1, CHUNKS);
+    uint32_t left = __shfl_up_sync(0xffffffffu, L[DC - 1], 1, CHUNKS);
     uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, CHUNKS);
     if (q == 0) left = (s == 0) ? 0u : kInf2;
     if (q == CHUNKS - 1) right = (s == 0) ? 0u : kInf2;
-    const uint32_t acc = sgm_step16(L, Cr, left, right, m, p1x2, p2x2, N);
-    m = group_min2<CHUNKS>(acc);
+    sgm_update<DC>(L, Cr, left, right, m, p1x2, p2x2, N);
+    m = group_min2<CHUNKS>(tree_min<DC>(N));
 #pragma unroll
-    for (int i = 0; i < kDC; i++) L[i] = N[i];
+    for (int i = 0; i < DC; i++) L[i] = N[i];
     if (enabled) {
-      uint4 oa, ob;
-      pairs_to_bytes(N, oa, ob);
-      *reinterpret_cast<uint4*>(out + ((size_t)y0 * W + x) * Dp + d0) = oa;
-      if (y1 != y0) *reinterpret_cast<uint4*>(out + ((size_t)y1 * W + x) * Dp + d0) = ob;
+      V oa, ob;
+      pairs_to_bytes<DC>(N, oa, ob);
+      __stcs(reinterpret_cast<V*>(out + ((size_t)y0 * W + x) * Dp + d0), oa);
+      if (y1 != y0) __stcs(reinterpret_cast<V*>(out + ((size_t)y1 * W + x) * Dp + d0), ob);
     }
   }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -173,28 +193,66 @@ __global__ void __launch_bounds__(256)
 // (x0 - HALO + h, x1 + h) carrying the diagonal paths into the strip.
 // FL = the diagonal path fed from column x-1 ((+1,+1) down, (+1,-1) up),
 // FR = the one fed from column x+1 ((-1,+1) down, (-1,-1) up).
-template <int CHUNKS, bool UP>
-__global__ void __launch_bounds__((16 + kHalo) * CHUNKS)
+
+template <int N>
+__device__ __forceinline__ void load_u4(uint32_t* r, const uint4* src, int stride) {
+#pragma unroll
+  for (int w = 0; w < N / 4; w++) {
+    const uint4 v = src[w * stride];
+    r[4 * w] = v.x; r[4 * w + 1] = v.y; r[4 * w + 2] = v.z; r[4 * w + 3] = v.w;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_u4(uint4* dst, int stride, const uint32_t* r) {
+#pragma unroll
+  for (int w = 0; w < N / 4; w++) dst[w * stride] = make_uint4(r[4 * w], r[4 * w + 1], r[4 * w + 2], r[4 * w + 3]);
+}
+
+template <int DC, int CHUNKS, int HALO, bool UP>
+struct SweepCfg {
+  static constexpr int NP = 16 + HALO;      // column pairs per task
+  static constexpr int NT = NP * CHUNKS;    // threads
+  static constexpr int NO = 16 * CHUNKS;    // threads of owned pairs
+  static constexpr int TH = HALO + 1;       // band rows
+  static constexpr int RING = UP ? 2 : 3;   // prefetch depth in rows
+  static constexpr int XW = DC / 4 + 4;     // uint4 slots per owned thread per row (UP)
+  static constexpr size_t smem_bytes() {
+    return (size_t)2 * 2 * (DC / 4) * NT * 16     // diagonal hand-over
+           + (size_t)2 * 2 * NP * 4                // pair minima
+           + (size_t)(DC / 4) * NO * 16            // selection row (UP)
+           + (size_t)RING * 2 * NT * DC            // cost ring
+           + (UP ? (size_t)RING * XW * NO * 16 : 0);
+  }
+};
+
+template <int DC, int CHUNKS, int HALO, bool UP>
+__global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     sweep_kernel(SweepArgs a) {
-  constexpr int NP = 16 + kHalo;
-  constexpr int NT = NP * CHUNKS;
-  constexpr int TH = kHalo + 1;
+  using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
+  using V = typename ByteVec<DC>::T;
+  constexpr int NP = Cfg::NP, NT = Cfg::NT, NO = Cfg::NO, TH = Cfg::TH, RING = Cfg::RING;
+  constexpr int XW = Cfg::XW, G = DC / 4;
   extern __shared__ __align__(16) uint8_t smem[];
-  // exchange buffers [parity][pair][chunk][16] for FL and FR, and pair mins
-  uint32_t* xfl = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* xfr = xfl + 2 * NT * kDC;
-  uint32_t* mfl = xfr + 2 * NT * kDC;     // [parity][pair]
+  // diagonal hand-over buffers, [parity][register group][thread] uint4
+  // (consecutive threads hit consecutive 16-byte words: no bank conflicts)
+  uint4* xfl = reinterpret_cast<uint4*>(smem);
+  uint4* xfr = xfl + 2 * G * NT;
+  uint32_t* mfl = reinterpret_cast<uint32_t*>(xfr + 2 * G * NT);   // [parity][pair]
   uint32_t* mfr = mfl + 2 * NP;
-  uint32_t* srow = mfr + 2 * NP;          // [pair 0..15][chunk][16] (UP selection)
+  uint4* srow = reinterpret_cast<uint4*>(mfr + 2 * NP);            // [group][owned thread]
+  V* ringc = reinterpret_cast<V*>(srow + G * NO);                  // [slot][lo/hi][thread]
+  uint4* ringx = reinterpret_cast<uint4*>(ringc + RING * 2 * NT);  // [slot][XW][owned thread]
   __shared__ int s_abort;
+  __shared__ int s_task;
 
   const int t = threadIdx.x;
   const int pr = t / CHUNKS;
   const int q = t - pr * CHUNKS;
   const bool owned = pr < 16;
   const int W = a.W, H = a.H, Dp = a.Dp, J = a.J;
-  const int d0 = q * kDC;
-  const bool pad = d0 + kDC > a.D;
+  const int d0 = q * DC;
+  const bool pad = d0 + DC > a.D;
   const bool live = d0 < Dp;   // chunks past the padded depth hold no data
   const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
   const bool en_v = (a.path_mask >> (UP ? 3 : 2)) & 1u;
@@ -203,429 +261,430 @@ __global__ void __launch_bounds__((16 + kHalo) * CHUNKS)
   // lanes of owned pairs in this warp (owned and halo pairs share a warp
   // only when CHUNKS == 1)
   const unsigned own_mask = __ballot_sync(0xffffffffu, owned);
+  // hand-over sources: FL from column x-1, FR from column x+1.  Whole
+  // registers move between pairs except at the two seams of the layout.
+  int fl_src, fl_src2 = -1, fr_src, fr_src2 = -1;
+  uint32_t fl_sel = 0, fr_sel = 0;
+  if (owned) {
+    if (pr > 0) fl_src = pr - 1;
+    else { fl_src = NP - 1; fl_src2 = 15; fl_sel = 0x5410u; }     // (x0-1, x0+15)
+    if (pr < 15) fr_src = pr + 1;
+    else { fr_src = 0; fr_src2 = 16; fr_sel = 0x7632u; }          // (x0+16, x1)
+  } else {
+    const int h = pr - 16;
+    if (h > 0) fl_src = pr - 1;
+    else { fl_src = pr; fl_src2 = 15; fl_sel = 0x7610u; }         // (-, x1-1)
+    fr_src = (h < HALO - 1) ? pr + 1 : 0;                         // (x0, -) at the seam
+  }
   if (t == 0) s_abort = 0;
   __syncthreads();
 
-  for (int bi = 0; bi < a.nb; bi++) {
+  // Tasks (band, pass, strip) in band-major order from a global counter: any
+  // CTA takes the next one, so a slow SM delays nobody but itself.  A task
+  // waits (bounded) for the previous band of its own strip and of both
+  // neighbour strips; those tasks were handed out earlier to running CTAs.
+  const int ntasks = a.nb * a.items;
+  for (;;) {
+    if (t == 0) s_task = atomicAdd(a.task_counter, 1);
+    __syncthreads();
+    const int task = s_task;
+    if (task >= ntasks) break;
+    const int bi = task / a.items;
+    const int item = task - bi * a.items;
     const int band = UP ? (a.nb - 1 - bi) : bi;
     const int ytop = band * TH;
     const int nrows = min(TH, H - ytop);
-    for (int item = blockIdx.x; item < a.items; item += gridDim.x) {
-      const int p = item / J;
-      const int j = item - p * J;
-      const int x0 = j * kTW;
-      // ---- wait for the neighbour strips to finish the previous band ----
-      if (t == 0 && bi > 0) {
-        long long spins = 0;
-        const int* fl = a.flags + p * J;
-        for (int n = j - 1; n <= j + 1; n += 2) {
-          if (n < 0 || n >= J) continue;
-          while (ld_acquire(fl + n) < bi) {
-            if (++spins > a.spin_limit || *((volatile int*)a.err) != 0) {
-              atomicExch(a.err, 1);
-              s_abort = 1;
-              break;
-            }
-            __nanosleep(64);
+    const int p = item / J;
+    const int j = item - p * J;
+    const int x0 = j * kTW;
+    // ---- columns of this thread's pair ----
+    int xlo, xhi;
+    if (owned) {
+      xlo = x0 + pr;
+      xhi = x0 + 16 + pr;
+    } else {
+      xlo = x0 - HALO + (pr - 16);
+      xhi = x0 + kTW + (pr - 16);
+    }
+    const bool lo_in = live && xlo >= 0 && xlo < W, hi_in = live && xhi >= 0 && xhi < W;
+    const PassIO& io = a.io[p];
+    // ---- prefetch ring: the first rows' inputs are requested before the
+    // neighbour wait (they do not depend on it) ----
+    auto issue_row = [&](int r) {
+      const bool ok = r < nrows;
+      const int yy = UP ? ytop + nrows - 1 - r : ytop + r;
+      V* cs = ringc + (r % RING) * 2 * NT + t;
+      const uint8_t* rowc = io.cost + (size_t)yy * W * Dp + d0;
+      cp_async<DC>(cs, ok && lo_in ? rowc + (size_t)xlo * Dp : io.cost, ok && lo_in);
+      cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : io.cost, ok && hi_in);
+      if (UP && owned) {
+        uint4* xs = ringx + (r % RING) * XW * NO + t;
+        const size_t tile = ((((size_t)p * H + (ok ? yy : 0)) * J + j) * 16 + pr) * CHUNKS + q;
+        const uint4* sd = reinterpret_cast<const uint4*>(a.sdown) + tile * G;
+#pragma unroll
+        for (int w = 0; w < G; w++) cp_async<16>(xs + w * NO, sd + w, ok);
+        const size_t ol = ((size_t)yy * W + xlo) * Dp + d0, oh = ((size_t)yy * W + xhi) * Dp + d0;
+        const bool fl = ok && lo_in, fh = ok && hi_in;
+        cp_async<DC>(xs + (G + 0) * NO, fl && a.en_h0 ? io.hfwd + ol : io.hfwd, fl && a.en_h0);
+        cp_async<DC>(xs + (G + 1) * NO, fh && a.en_h0 ? io.hfwd + oh : io.hfwd, fh && a.en_h0);
+        cp_async<DC>(xs + (G + 2) * NO, fl && a.en_h1 ? io.hbwd + ol : io.hbwd, fl && a.en_h1);
+        cp_async<DC>(xs + (G + 3) * NO, fh && a.en_h1 ? io.hbwd + oh : io.hbwd, fh && a.en_h1);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int r = 0; r < RING - 1; r++) issue_row(r);
+    // ---- wait for the previous band of this strip and its neighbours ----
+    if (t == 0 && bi > 0) {
+      long long spins = 0;
+      const int* fl = a.flags + p * J;
+      for (int n = j - 1; n <= j + 1; n++) {
+        if (n < 0 || n >= J) continue;
+        while (ld_acquire(fl + n) < bi) {
+          if (++spins > a.spin_limit || *((volatile int*)a.err) != 0) {
+            atomicExch(a.err, 1);
+            s_abort = 1;
+            break;
           }
-          if (s_abort) break;
+          if (spins > 64) __nanosleep(32);
         }
-        __threadfence();
+        if (s_abort) break;
       }
-      __syncthreads();
-      if (s_abort) return;
+    }
+    __syncthreads();
+    if (s_abort) {
+      cp_async_wait<0>();
+      return;
+    }
 
-      // ---- columns of this thread's pair ----
-      int xlo, xhi;
-      if (owned) {
-        xlo = x0 + pr;
-        xhi = x0 + 16 + pr;
-      } else {
-        xlo = x0 - kHalo + (pr - 16);
-        xhi = x0 + kTW + (pr - 16);
-      }
-      const bool lo_in = live && xlo >= 0 && xlo < W, hi_in = live && xhi >= 0 && xhi < W;
-      // lanes whose predecessor column lies outside the image start a path
-      const uint32_t fl_keep = ((xlo - 1 >= 0) ? 0x0000ffffu : 0u) | ((xhi - 1 >= 0) ? 0xffff0000u : 0u);
-      const uint32_t fr_keep = ((xlo + 1 < W) ? 0x0000ffffu : 0u) | ((xhi + 1 < W) ? 0xffff0000u : 0u);
+    // lanes whose predecessor column lies outside the image start a path
+    const uint32_t fl_keep = ((xlo - 1 >= 0) ? 0x0000ffffu : 0u) | ((xhi - 1 >= 0) ? 0xffff0000u : 0u);
+    const uint32_t fr_keep = ((xlo + 1 < W) ? 0x0000ffffu : 0u) | ((xhi + 1 < W) ? 0xffff0000u : 0u);
+    const uint8_t* bsv = a.bs + ((size_t)(p * 2 + ((bi + 1) & 1)) * 3 + 0) * W * Dp;
+    const uint8_t* bsl = bsv + (size_t)W * Dp;
+    const uint8_t* bsr = bsl + (size_t)W * Dp;
+    uint8_t* wsv = a.bs + ((size_t)(p * 2 + (bi & 1)) * 3 + 0) * W * Dp;
+    uint8_t* wsl = wsv + (size_t)W * Dp;
+    uint8_t* wsr = wsl + (size_t)W * Dp;
 
-      const PassIO& io = a.io[p];
-      const uint8_t* bsv = a.bs + ((size_t)(p * 2 + ((bi + 1) & 1)) * 3 + 0) * W * Dp;
-      const uint8_t* bsl = bsv + (size_t)W * Dp;
-      const uint8_t* bsr = bsl + (size_t)W * Dp;
-      uint8_t* wsv = a.bs + ((size_t)(p * 2 + (bi & 1)) * 3 + 0) * W * Dp;
-      uint8_t* wsl = wsv + (size_t)W * Dp;
-      uint8_t* wsr = wsl + (size_t)W * Dp;
-
-      uint32_t Lv[kDC], Lf[kDC], Lr[kDC], Cc[kDC];
-      uint32_t mv = 0, mf = 0, mr = 0;
-      // ---- predecessor states at the band boundary ----
-      {
-        const bool have = bi > 0;
-        auto load_pair = [&](const uint8_t* base, int cl, int ch, uint32_t* r, uint32_t keep) {
-          uint4 va = make_uint4(0, 0, 0, 0), vb = va;
-          if (live && have && (keep & 0xffffu) && cl >= 0 && cl < W)
-            va = __ldcg(reinterpret_cast<const uint4*>(base + (size_t)cl * Dp + d0));
-          if (live && have && (keep & 0xffff0000u) && ch >= 0 && ch < W)
-            vb = __ldcg(reinterpret_cast<const uint4*>(base + (size_t)ch * Dp + d0));
-          bytes_to_pairs_u8(va, vb, r);
-          if (pad) {
-#pragma unroll
-            for (int i = 0; i < kDC; i++)
-              if (d0 + i >= a.D) r[i] = (have ? kPadCost2 : 0u) & keep;
-          }
-        };
-        if (owned) load_pair(bsv, xlo, xhi, Lv, 0xffffffffu);
-        else {
-#pragma unroll
-          for (int i = 0; i < kDC; i++) Lv[i] = 0;
-        }
-        load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
-        load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
-        uint32_t av = 0xffffffffu, af = 0xffffffffu, ar = 0xffffffffu;
-#pragma unroll
-        for (int i = 0; i < kDC; i++) {
-          av = vmin2(av, Lv[i]);
-          af = vmin2(af, Lf[i]);
-          ar = vmin2(ar, Lr[i]);
-        }
-        mv = group_min2<CHUNKS>(av);
-        mf = group_min2<CHUNKS>(af);
-        mr = group_min2<CHUNKS>(ar);
-        if (!have) mv = mf = mr = 0;
-        mf &= fl_keep;
-        mr &= fr_keep;
-      }
-
-      // prefetch the first row's costs
-      auto cost_ptr = [&](int x, int y) {
-        return reinterpret_cast<const uint4*>(io.cost + ((size_t)y * W + x) * Dp + d0);
-      };
-      const int yfirst = UP ? ytop + nrows - 1 : ytop;
-      uint4 ca = make_uint4(0, 0, 0, 0), cb = ca;
-      if (lo_in) ca = __ldg(cost_ptr(xlo, yfirst));
-      if (hi_in) cb = __ldg(cost_ptr(xhi, yfirst));
-
-      for (int k = 0; k < nrows; k++) {
-        const int y = UP ? ytop + nrows - 1 - k : ytop + k;
-        bytes_to_pairs(ca, cb, Cc);
+    uint32_t Lv[DC], Lf[DC], Lr[DC], Cc[DC];
+    uint32_t mv = 0, mf = 0, mr = 0;
+    // ---- predecessor states at the band boundary ----
+    {
+      const bool have = bi > 0;
+      auto load_pair = [&](const uint8_t* base, int cl, int ch, uint32_t* r, uint32_t keep) {
+        V va = ByteVec<DC>::zero(), vb = va;
+        if (live && have && (keep & 0xffffu) && cl >= 0 && cl < W)
+          va = __ldcg(reinterpret_cast<const V*>(base + (size_t)cl * Dp + d0));
+        if (live && have && (keep & 0xffff0000u) && ch >= 0 && ch < W)
+          vb = __ldcg(reinterpret_cast<const V*>(base + (size_t)ch * Dp + d0));
+        bytes_to_pairs_u8<DC>(va, vb, r);
         if (pad) {
 #pragma unroll
-          for (int i = 0; i < kDC; i++)
-            if (d0 + i >= a.D) Cc[i] = kPadCost2;
+          for (int i = 0; i < DC; i++)
+            if (d0 + i >= a.D) r[i] = (have ? kPadCost2 : 0u) & keep;
         }
-        if (k + 1 < nrows) {
-          const int yn = UP ? y - 1 : y + 1;
-          if (lo_in) ca = __ldg(cost_ptr(xlo, yn));
-          if (hi_in) cb = __ldg(cost_ptr(xhi, yn));
-        }
-        const int par = k & 1;
-        // ---- vertical path (owned pairs) ----
-        uint32_t Nv[kDC];
-        if (owned) {
-          uint32_t left = __shfl_up_sync(own_mask, Lv[kDC - 1], 1, CHUNKS);
-          uint32_t right = __shfl_down_sync(own_mask, Lv[0], 1, CHUNKS);
-          const bool fresh = (bi == 0 && k == 0);
-          if (q == 0) left = fresh ? 0u : kInf2;
-          if (q == CHUNKS - 1) right = fresh ? 0u : kInf2;
-          const uint32_t acc = sgm_step16(Lv, Cc, left, right, mv, p1x2, p2x2, Nv);
-          mv = group_min2<CHUNKS>(acc, own_mask);
-        }
-        // ---- diagonal paths ----
-        uint32_t Nf[kDC], Nr[kDC];
-        {
-          uint32_t left = __shfl_up_sync(0xffffffffu, Lf[kDC - 1], 1, CHUNKS);
-          uint32_t right = __shfl_down_sync(0xffffffffu, Lf[0], 1, CHUNKS);
-          if (q == 0) left = kInf2 & fl_keep;
-          if (q == CHUNKS - 1) right = kInf2 & fl_keep;
-          if (bi == 0 && k == 0) { if (q == 0) left = 0; if (q == CHUNKS - 1) right = 0; }
-          const uint32_t acc = sgm_step16(Lf, Cc, left, right, mf, p1x2, p2x2, Nf);
-          mf = group_min2<CHUNKS>(acc);
-        }
-        {
-          uint32_t left = __shfl_up_sync(0xffffffffu, Lr[kDC - 1], 1, CHUNKS);
-          uint32_t right = __shfl_down_sync(0xffffffffu, Lr[0], 1, CHUNKS);
-          if (q == 0) left = kInf2 & fr_keep;
-          if (q == CHUNKS - 1) right = kInf2 & fr_keep;
-          if (bi == 0 && k == 0) { if (q == 0) left = 0; if (q == CHUNKS - 1) right = 0; }
-          const uint32_t acc = sgm_step16(Lr, Cc, left, right, mr, p1x2, p2x2, Nr);
-          mr = group_min2<CHUNKS>(acc);
-        }
-        // ---- accumulate and emit (owned pairs) ----
-        if (owned) {
-          uint32_t S[kDC];
+      };
+      if (owned) {
+        load_pair(bsv, xlo, xhi, Lv, 0xffffffffu);
+      } else {
 #pragma unroll
-          for (int i = 0; i < kDC; i++)
-            S[i] = (en_v ? Nv[i] : 0u) + (en_fl ? Nf[i] : 0u) + (en_fr ? Nr[i] : 0u);
-          const size_t tile = ((((size_t)p * H + y) * J + j) * 16 + pr) * CHUNKS + q;
-          uint4* sd = reinterpret_cast<uint4*>(a.sdown) + tile * 4;
-          if (!UP) {
+        for (int i = 0; i < DC; i++) Lv[i] = 0;
+      }
+      load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
+      load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
+      uint32_t av = tree_min<DC>(Lv), af = tree_min<DC>(Lf), ar = tree_min<DC>(Lr);
 #pragma unroll
-            for (int w = 0; w < 4; w++)
-              sd[w] = make_uint4(S[4 * w], S[4 * w + 1], S[4 * w + 2], S[4 * w + 3]);
-          } else {
-            // add the down sweep and the horizontal paths
+      for (int o = 1; o < CHUNKS; o <<= 1) {
+        av = vmin2(av, __shfl_xor_sync(0xffffffffu, av, o, CHUNKS));
+        af = vmin2(af, __shfl_xor_sync(0xffffffffu, af, o, CHUNKS));
+        ar = vmin2(ar, __shfl_xor_sync(0xffffffffu, ar, o, CHUNKS));
+      }
+      mv = have ? av : 0u;
+      mf = have ? (af & fl_keep) : 0u;
+      mr = have ? (ar & fr_keep) : 0u;
+    }
+
+    for (int k = 0; k < nrows; k++) {
+      const int y = UP ? ytop + nrows - 1 - k : ytop + k;
+      issue_row(k + RING - 1);
+      cp_async_wait<RING - 1>();
+      {
+        const V* cs = ringc + (k % RING) * 2 * NT + t;
+        bytes_to_pairs<DC>(cs[0], cs[NT], Cc);
+      }
+      if (pad) {
 #pragma unroll
-            for (int w = 0; w < 4; w++) {
-              const uint4 v = __ldcs(sd + w);
-              S[4 * w] += v.x;
-              S[4 * w + 1] += v.y;
-              S[4 * w + 2] += v.z;
-              S[4 * w + 3] += v.w;
-            }
-            uint32_t hf[kDC], hb[kDC];
-            const uint4 z = make_uint4(0, 0, 0, 0);
-            const size_t ol = ((size_t)y * W + xlo) * Dp + d0, oh = ((size_t)y * W + xhi) * Dp + d0;
-            bytes_to_pairs_u8(lo_in && a.en_h0 ? __ldcs(reinterpret_cast<const uint4*>(io.hfwd + ol)) : z,
-                           hi_in && a.en_h0 ? __ldcs(reinterpret_cast<const uint4*>(io.hfwd + oh)) : z, hf);
-            bytes_to_pairs_u8(lo_in && a.en_h1 ? __ldcs(reinterpret_cast<const uint4*>(io.hbwd + ol)) : z,
-                           hi_in && a.en_h1 ? __ldcs(reinterpret_cast<const uint4*>(io.hbwd + oh)) : z, hb);
+        for (int i = 0; i < DC; i++)
+          if (d0 + i >= a.D) Cc[i] = kPadCost2;
+      }
+      const int par = k & 1;
+      const bool fresh = (bi == 0 && k == 0);
+      // ---- neighbour disparities d0-1 and d0+DC of all three paths ----
+      uint32_t lv = __shfl_up_sync(0xffffffffu, Lv[DC - 1], 1, CHUNKS);
+      uint32_t rv = __shfl_down_sync(0xffffffffu, Lv[0], 1, CHUNKS);
+      uint32_t lf = __shfl_up_sync(0xffffffffu, Lf[DC - 1], 1, CHUNKS);
+      uint32_t rf = __shfl_down_sync(0xffffffffu, Lf[0], 1, CHUNKS);
+      uint32_t lr = __shfl_up_sync(0xffffffffu, Lr[DC - 1], 1, CHUNKS);
+      uint32_t rr = __shfl_down_sync(0xffffffffu, Lr[0], 1, CHUNKS);
+      if (q == 0) {
+        lv = fresh ? 0u : kInf2;
+        lf = fresh ? 0u : (kInf2 & fl_keep);
+        lr = fresh ? 0u : (kInf2 & fr_keep);
+      }
+      if (q == CHUNKS - 1) {
+        rv = fresh ? 0u : kInf2;
+        rf = fresh ? 0u : (kInf2 & fl_keep);
+        rr = fresh ? 0u : (kInf2 & fr_keep);
+      }
+      // ---- all three paths ----
+      uint32_t Nv[DC], Nf[DC], Nr[DC];
+      if (owned) sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2x2, Nv);
+      sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
+      sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+      uint32_t av = owned ? tree_min<DC>(Nv) : 0u;
+      uint32_t af = tree_min<DC>(Nf), ar = tree_min<DC>(Nr);
 #pragma unroll
-            for (int i = 0; i < kDC; i++) S[i] += hf[i] + hb[i];
-            if (pad) {
-#pragma unroll
-              for (int i = 0; i < kDC; i++)
-                if (d0 + i >= a.D) S[i] = 0xffffffffu;
-            }
-            if (io.S) {
-              // full aggregated cost, [H][W][D] uint16
-#pragma unroll
-              for (int i = 0; i < kDC; i++) {
-                if (d0 + i < a.D) {
-                  if (lo_in) io.S[((size_t)y * W + xlo) * a.D + d0 + i] = (uint16_t)(S[i] & 0xffffu);
-                  if (hi_in) io.S[((size_t)y * W + xhi) * a.D + d0 + i] = (uint16_t)(S[i] >> 16);
-                }
-              }
-            }
-            if (io.dint) {
-              // winner-take-all: smallest d with the minimal S, per lane
-              uint32_t mn = 0xffffffffu;
-#pragma unroll
-              for (int i = 0; i < kDC; i++) mn = vmin2(mn, S[i]);
-              const uint32_t gmin = group_min2<CHUNKS>(mn, own_mask);
-              uint32_t first = 0xffffffffu;
-#pragma unroll
-              for (int i = kDC - 1; i >= 0; i--) {
-                const uint32_t d2 = (uint32_t)(d0 + i) * 0x10001u;
-                const uint32_t lo_eq = ((S[i] ^ gmin) & 0xffffu) == 0 ? 0x0000ffffu : 0u;
-                const uint32_t hi_eq = ((S[i] ^ gmin) & 0xffff0000u) == 0 ? 0xffff0000u : 0u;
-                const uint32_t eq = lo_eq | hi_eq;
-                first = (first & ~eq) | (d2 & eq);
-              }
-              const uint32_t dstar2 = group_min2<CHUNKS>(first, own_mask);
-              // neighbours S(d*-1), S(d*+1) through shared memory
-              uint32_t* row = srow + (pr * CHUNKS + q) * kDC;
-#pragma unroll
-              for (int i = 0; i < kDC; i++) row[i] = S[i];
-              __syncwarp(own_mask);
-              if (q == 0) {
-                const uint32_t* prow = srow + pr * CHUNKS * kDC;
-#pragma unroll
-                for (int lane = 0; lane < 2; lane++) {
-                  const int x = lane ? xhi : xlo;
-                  if (x < 0 || x >= W) continue;
-                  const int sh = 16 * lane;
-                  const int ds = (dstar2 >> sh) & 0xffff;
-                  const int sv = (prow[ds] >> sh) & 0xffff;
-                  float v = (float)ds;
-                  if (a.subpixel && ds > 0 && ds < a.D - 1) {
-                    const int am = (int)((prow[ds - 1] >> sh) & 0xffff) - sv;
-                    const int bp = (int)((prow[ds + 1] >> sh) & 0xffff) - sv;
-                    v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
-                  }
-                  io.dint[(size_t)y * W + x] = (int16_t)ds;
-                  if (io.dsub) io.dsub[(size_t)y * W + x] = v;
-                }
-              }
-              __syncwarp(own_mask);
-            }
-          }
-        }
-        // ---- diagonal hand-over to the next row ----
-        uint32_t* bfl = xfl + (par * NT + t) * kDC;
-        uint32_t* bfr = xfr + (par * NT + t) * kDC;
-#pragma unroll
-        for (int w = 0; w < 4; w++) {
-          reinterpret_cast<uint4*>(bfl)[w] = make_uint4(Nf[4 * w], Nf[4 * w + 1], Nf[4 * w + 2], Nf[4 * w + 3]);
-          reinterpret_cast<uint4*>(bfr)[w] = make_uint4(Nr[4 * w], Nr[4 * w + 1], Nr[4 * w + 2], Nr[4 * w + 3]);
-        }
+      for (int o = 1; o < CHUNKS; o <<= 1) {
+        av = vmin2(av, __shfl_xor_sync(0xffffffffu, av, o, CHUNKS));
+        af = vmin2(af, __shfl_xor_sync(0xffffffffu, af, o, CHUNKS));
+        ar = vmin2(ar, __shfl_xor_sync(0xffffffffu, ar, o, CHUNKS));
+      }
+      mv = av;
+      mf = af;
+      mr = ar;
+      // ---- diagonal hand-over to the next row (written early) ----
+      if (k + 1 < nrows) {
+        store_u4<DC>(xfl + par * G * NT + t, NT, Nf);
+        store_u4<DC>(xfr + par * G * NT + t, NT, Nr);
         if (q == 0) {
           mfl[par * NP + pr] = mf;
           mfr[par * NP + pr] = mr;
         }
+      }
+      // ---- accumulate and emit (owned pairs) ----
+      if (owned) {
+        uint32_t S[DC];
+#pragma unroll
+        for (int i = 0; i < DC; i++)
+          S[i] = (en_v ? Nv[i] : 0u) + (en_fl ? Nf[i] : 0u) + (en_fr ? Nr[i] : 0u);
+        if (!UP) {
+          const size_t tile = ((((size_t)p * H + y) * J + j) * 16 + pr) * CHUNKS + q;
+          store_u4<DC>(reinterpret_cast<uint4*>(a.sdown) + tile * G, 1, S);
+        } else {
+          // add the down sweep and the horizontal paths
+          uint32_t sdv[DC], hf[DC], hb[DC];
+          const uint4* xs = ringx + (k % RING) * XW * NO + t;
+          load_u4<DC>(sdv, xs, NO);
+          bytes_to_pairs_u8<DC>(*reinterpret_cast<const V*>(xs + G * NO),
+                                *reinterpret_cast<const V*>(xs + (G + 1) * NO), hf);
+          bytes_to_pairs_u8<DC>(*reinterpret_cast<const V*>(xs + (G + 2) * NO),
+                                *reinterpret_cast<const V*>(xs + (G + 3) * NO), hb);
+#pragma unroll
+          for (int i = 0; i < DC; i++) S[i] += sdv[i] + hf[i] + hb[i];
+          if (pad) {
+#pragma unroll
+            for (int i = 0; i < DC; i++)
+              if (d0 + i >= a.D) S[i] = 0xffffffffu;
+          }
+          if (io.S) {
+            // full aggregated cost, [H][W][D] uint16
+#pragma unroll
+            for (int i = 0; i < DC; i++) {
+              if (d0 + i < a.D) {
+                if (lo_in) io.S[((size_t)y * W + xlo) * a.D + d0 + i] = (uint16_t)(S[i] & 0xffffu);
+                if (hi_in) io.S[((size_t)y * W + xhi) * a.D + d0 + i] = (uint16_t)(S[i] >> 16);
+              }
+            }
+          }
+          if (io.dint) {
+            // winner-take-all: the smallest d with the minimal S, per lane
+            const uint32_t gmin = group_min2<CHUNKS>(tree_min<DC>(S), own_mask);
+            uint32_t first = 0xffffffffu;
+#pragma unroll
+            for (int i = DC - 1; i >= 0; i--) {
+              const uint32_t d2 = (uint32_t)(d0 + i) * 0x10001u;
+              const uint32_t x2 = S[i] ^ gmin;
+              const uint32_t eq = ((x2 & 0xffffu) ? 0u : 0x0000ffffu) | ((x2 >> 16) ? 0u : 0xffff0000u);
+              first = (first & ~eq) | (d2 & eq);
+            }
+            const uint32_t dstar2 = group_min2<CHUNKS>(first, own_mask);
+            // S(d*-1) and S(d*+1) through shared memory, [group][thread];
+            // chunk 0 finishes the low lane's column, chunk 1 the high one
+            store_u4<DC>(srow + t, NO, S);
+            __syncwarp(own_mask);
+            const int lane = CHUNKS == 1 ? -1 : q;
+            for (int l = 0; l < 2; l++) {
+              if (!(lane == l || (CHUNKS == 1 && q == 0))) continue;
+              const int x = l ? xhi : xlo;
+              if (x < 0 || x >= W) continue;
+              const int sh = 16 * l;
+              const int ds = (dstar2 >> sh) & 0xffff;
+              const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow);
+              auto s_at = [&](int d) {   // S at disparity d of this pair
+                const int qq = d / DC, ii = d - qq * DC;
+                return (sw[((ii >> 2) * NO + pr * CHUNKS + qq) * 4 + (ii & 3)] >> sh) & 0xffffu;
+              };
+              float v = (float)ds;
+              if (a.subpixel && ds > 0 && ds < a.D - 1) {
+                const int sv = (int)s_at(ds);
+                const int am = (int)s_at(ds - 1) - sv;
+                const int bp = (int)s_at(ds + 1) - sv;
+                v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+              }
+              io.dint[(size_t)y * W + x] = (int16_t)ds;
+              if (io.dsub) io.dsub[(size_t)y * W + x] = v;
+            }
+            __syncwarp(own_mask);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < DC; i++) Lv[i] = Nv[i];
+      }
+      if (k + 1 == nrows) {
+        // band end: publish the states of the owned columns
         if (owned) {
-#pragma unroll
-          for (int i = 0; i < kDC; i++) Lv[i] = Nv[i];
+          V va, vb;
+          pairs_to_bytes<DC>(Nv, va, vb);
+          if (lo_in) *reinterpret_cast<V*>(wsv + (size_t)xlo * Dp + d0) = va;
+          if (hi_in) *reinterpret_cast<V*>(wsv + (size_t)xhi * Dp + d0) = vb;
+          pairs_to_bytes<DC>(Nf, va, vb);
+          if (lo_in) *reinterpret_cast<V*>(wsl + (size_t)xlo * Dp + d0) = va;
+          if (hi_in) *reinterpret_cast<V*>(wsl + (size_t)xhi * Dp + d0) = vb;
+          pairs_to_bytes<DC>(Nr, va, vb);
+          if (lo_in) *reinterpret_cast<V*>(wsr + (size_t)xlo * Dp + d0) = va;
+          if (hi_in) *reinterpret_cast<V*>(wsr + (size_t)xhi * Dp + d0) = vb;
         }
-        if (k + 1 == nrows) {
-          // band end: publish the states of the owned columns
-          if (owned) {
-            uint4 va, vb;
-            pairs_to_bytes(Nv, va, vb);
-            if (lo_in) *reinterpret_cast<uint4*>(wsv + (size_t)xlo * Dp + d0) = va;
-            if (hi_in) *reinterpret_cast<uint4*>(wsv + (size_t)xhi * Dp + d0) = vb;
-            pairs_to_bytes(Nf, va, vb);
-            if (lo_in) *reinterpret_cast<uint4*>(wsl + (size_t)xlo * Dp + d0) = va;
-            if (hi_in) *reinterpret_cast<uint4*>(wsl + (size_t)xhi * Dp + d0) = vb;
-            pairs_to_bytes(Nr, va, vb);
-            if (lo_in) *reinterpret_cast<uint4*>(wsr + (size_t)xlo * Dp + d0) = va;
-            if (hi_in) *reinterpret_cast<uint4*>(wsr + (size_t)xhi * Dp + d0) = vb;
-          }
-          __syncthreads();   // exchange buffers are reused by the next item
-          break;
-        }
-        __syncthreads();
-        // FL from column x-1, FR from column x+1 (whole registers except at
-        // the two seams of the pair layout)
-        {
-          int src;
-          uint32_t sel = 0;
-          int src2 = -1;
-          if (owned) {
-            if (pr > 0) src = pr - 1;
-            else { src = 16 + kHalo - 1; src2 = 15; sel = 0x5410u; }   // (x0-1, x0+15)
-          } else {
-            const int h = pr - 16;
-            if (h > 0) src = pr - 1;
-            else { src = pr; src2 = 15; sel = 0x7610u; }             // (-, x1-1)
-          }
-          const uint32_t* s1 = xfl + (par * NT + src * CHUNKS + q) * kDC;
-          uint32_t m1 = mfl[par * NP + src];
-          if (src2 < 0) {
+        break;
+      }
+      __syncthreads();
+      {
+        const uint4* b = xfl + par * G * NT;
+        if (fl_src2 < 0) {
+          load_u4<DC>(Lf, b + fl_src * CHUNKS + q, NT);
+          mf = mfl[par * NP + fl_src];
+        } else {
+          uint32_t s1[DC], s2[DC];
+          load_u4<DC>(s1, b + fl_src * CHUNKS + q, NT);
+          load_u4<DC>(s2, b + fl_src2 * CHUNKS + q, NT);
 #pragma unroll
-            for (int w = 0; w < 4; w++) {
-              const uint4 v = reinterpret_cast<const uint4*>(s1)[w];
-              Lf[4 * w] = v.x; Lf[4 * w + 1] = v.y; Lf[4 * w + 2] = v.z; Lf[4 * w + 3] = v.w;
-            }
-            mf = m1;
-          } else {
-            const uint32_t* s2 = xfl + (par * NT + src2 * CHUNKS + q) * kDC;
-#pragma unroll
-            for (int i = 0; i < kDC; i++) Lf[i] = prmt(s1[i], s2[i], sel);
-            mf = prmt(m1, mfl[par * NP + src2], sel);
-          }
-        }
-        {
-          int src;
-          uint32_t sel = 0;
-          int src2 = -1;
-          if (owned) {
-            if (pr < 15) src = pr + 1;
-            else { src = 0; src2 = 16; sel = 0x7632u; }               // (x0+16, x1)
-          } else {
-            const int h = pr - 16;
-            if (h < kHalo - 1) src = pr + 1;
-            else src = 0;                                             // (x0, -)
-          }
-          const uint32_t* s1 = xfr + (par * NT + src * CHUNKS + q) * kDC;
-          uint32_t m1 = mfr[par * NP + src];
-          if (src2 < 0) {
-#pragma unroll
-            for (int w = 0; w < 4; w++) {
-              const uint4 v = reinterpret_cast<const uint4*>(s1)[w];
-              Lr[4 * w] = v.x; Lr[4 * w + 1] = v.y; Lr[4 * w + 2] = v.z; Lr[4 * w + 3] = v.w;
-            }
-            mr = m1;
-          } else {
-            const uint32_t* s2 = xfr + (par * NT + src2 * CHUNKS + q) * kDC;
-#pragma unroll
-            for (int i = 0; i < kDC; i++) Lr[i] = prmt(s1[i], s2[i], sel);
-            mr = prmt(m1, mfr[par * NP + src2], sel);
-          }
-        }
-        // a lane whose predecessor column is outside the image restarts
-        if (fl_keep != 0xffffffffu) {
-#pragma unroll
-          for (int i = 0; i < kDC; i++) Lf[i] &= fl_keep;
-          mf &= fl_keep;
-        }
-        if (fr_keep != 0xffffffffu) {
-#pragma unroll
-          for (int i = 0; i < kDC; i++) Lr[i] &= fr_keep;
-          mr &= fr_keep;
+          for (int i = 0; i < DC; i++) Lf[i] = prmt(s1[i], s2[i], fl_sel);
+          mf = prmt(mfl[par * NP + fl_src], mfl[par * NP + fl_src2], fl_sel);
         }
       }
-      // ---- publish progress ----
-      __threadfence();
-      __syncthreads();
-      if (t == 0) st_release(a.flags + p * J + j, bi + 1);
+      {
+        const uint4* b = xfr + par * G * NT;
+        if (fr_src2 < 0) {
+          load_u4<DC>(Lr, b + fr_src * CHUNKS + q, NT);
+          mr = mfr[par * NP + fr_src];
+        } else {
+          uint32_t s1[DC], s2[DC];
+          load_u4<DC>(s1, b + fr_src * CHUNKS + q, NT);
+          load_u4<DC>(s2, b + fr_src2 * CHUNKS + q, NT);
+#pragma unroll
+          for (int i = 0; i < DC; i++) Lr[i] = prmt(s1[i], s2[i], fr_sel);
+          mr = prmt(mfr[par * NP + fr_src], mfr[par * NP + fr_src2], fr_sel);
+        }
+      }
+      // a lane whose predecessor column is outside the image restarts
+      if (fl_keep != 0xffffffffu) {
+#pragma unroll
+        for (int i = 0; i < DC; i++) Lf[i] &= fl_keep;
+        mf &= fl_keep;
+      }
+      if (fr_keep != 0xffffffffu) {
+#pragma unroll
+        for (int i = 0; i < DC; i++) Lr[i] &= fr_keep;
+        mr &= fr_keep;
+      }
     }
+    // ---- publish progress: the barrier orders every thread's band-end
+    // stores before thread 0's release (cumulativity); the exchange buffers
+    // and prefetch ring are free for the next task afterwards ----
+    cp_async_wait<0>();
+    __syncthreads();
+    if (t == 0) st_release(a.flags + p * J + j, bi + 1);
   }
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int chunks) {
-  const int NP = 16 + kHalo, NT = NP * chunks;
-  return (size_t)(2 * 2 * NT * kDC + 2 * 2 * NP + 16 * chunks * kDC) * sizeof(uint32_t);
-}
-
 cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
                              int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
   const size_t smem = (size_t)W * 16 + (size_t)W * Dp;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(cost_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    attr = true;
-  }
+  cudaError_t e = cudaFuncSetAttribute(cost_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   cost_pair_kernel<<<H, 512, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, CR);
   return cudaGetLastError();
 }
 
-template <int CHUNKS>
+template <int DC, int CHUNKS>
 static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
   const int rows2 = (a.H + 1) / 2;
   const long long threads = (long long)a.npass * rows2 * 2 * CHUNKS;
-  hline_kernel<CHUNKS><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  const size_t smem = (size_t)kHlinePrefetch * kHlineThreads * 2 * DC;
+  cudaError_t e = cudaFuncSetAttribute(hline_kernel<DC, CHUNKS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  hline_kernel<DC, CHUNKS><<<(unsigned)((threads + kHlineThreads - 1) / kHlineThreads),
+                             kHlineThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   count_launches(1);
-  switch (chunks_for(a.D)) {
-    case 1: return hline_dispatch<1>(a, s);
-    case 2: return hline_dispatch<2>(a, s);
-    case 4: return hline_dispatch<4>(a, s);
-    case 8: return hline_dispatch<8>(a, s);
-    default: return hline_dispatch<16>(a, s);
+  const Shape sh = shape_for(a.D);
+  if (sh.dc == 16) return sh.chunks <= 8 ? hline_dispatch<16, 8>(a, s) : hline_dispatch<16, 16>(a, s);
+  switch (sh.chunks) {
+    case 1: return hline_dispatch<8, 1>(a, s);
+    case 2: return hline_dispatch<8, 2>(a, s);
+    case 4: return hline_dispatch<8, 4>(a, s);
+    case 8: return hline_dispatch<8, 8>(a, s);
+    default: return hline_dispatch<8, 16>(a, s);
   }
 }
 
-template <int CHUNKS, bool UP>
-static cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s, int* grid_out) {
-  auto kern = sweep_kernel<CHUNKS, UP>;
-  const size_t smem = sweep_smem_bytes(CHUNKS);
+template <int DC, int CHUNKS, int HALO, bool UP>
+static cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
+  using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
+  auto kern = sweep_kernel<DC, CHUNKS, HALO, UP>;
+  const size_t smem = Cfg::smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int threads = (16 + kHalo) * CHUNKS;
   int per_sm = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  const int grid = std::min(a.items, per_sm * sms);
-  if (grid_out) *grid_out = grid;
-  SweepArgs args = a;
-  void* params[] = {&args};
-  // cooperative launch: every CTA is resident at once, so the bounded
-  // neighbour waits always have a running producer
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), params, smem, s);
+  // one wave of CTAs; tasks come from a queue, and a task is only waited on
+  // after a running CTA has taken it, so no co-residency guarantee is needed
+  const int grid = std::max(1, std::min(a.items * a.nb, per_sm * sms));
+  kern<<<grid, Cfg::NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool UP>
+static cudaError_t sweep_select(const SweepArgs& a, cudaStream_t s) {
+  const Shape sh = shape_for(a.D);
+  if (sh.dc == 16) return sweep_dispatch<16, 16, 8, UP>(a, s);   // 128 < D <= 256
+  switch (sh.chunks) {
+    case 1: return sweep_dispatch<8, 1, 16, UP>(a, s);
+    case 2: return sweep_dispatch<8, 2, 16, UP>(a, s);
+    case 4: return sweep_dispatch<8, 4, 16, UP>(a, s);
+    case 8: return sweep_dispatch<8, 8, 16, UP>(a, s);
+    default: return sweep_dispatch<8, 16, 16, UP>(a, s);
+  }
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, bool up, cudaStream_t s) {
   StageTrace trace(SF_STAGE_SGM_SWEEP, s);
   count_launches(1);
-  switch (chunks_for(a.D)) {
-    case 1: return up ? sweep_dispatch<1, true>(a, s, nullptr) : sweep_dispatch<1, false>(a, s, nullptr);
-    case 2: return up ? sweep_dispatch<2, true>(a, s, nullptr) : sweep_dispatch<2, false>(a, s, nullptr);
-    case 4: return up ? sweep_dispatch<4, true>(a, s, nullptr) : sweep_dispatch<4, false>(a, s, nullptr);
-    case 8: return up ? sweep_dispatch<8, true>(a, s, nullptr) : sweep_dispatch<8, false>(a, s, nullptr);
-    default: return up ? sweep_dispatch<16, true>(a, s, nullptr) : sweep_dispatch<16, false>(a, s, nullptr);
-  }
+  return up ? sweep_select<true>(a, s) : sweep_select<false>(a, s);
 }
 
 }  // namespace fused
