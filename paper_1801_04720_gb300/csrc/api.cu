@@ -217,11 +217,13 @@ sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8
   fused::HLineArgs ha{};
   ha.W = W; ha.H = H; ha.D = p->D; ha.Dp = Dp; ha.npass = npass; ha.P1 = p->P1; ha.P2 = p->P2;
   ha.path_mask = p->path_mask;
+  ha.err = reinterpret_cast<int*>(ws + lay.err);
   for (int k = 0; k < npass; k++) {
     ha.cost[k] = io_up[k].cost ? io_up[k].cost : cost + (size_t)k * N * Dp;
     ha.hfwd[k] = hvol + (size_t)(2 * k) * N * Dp;
     ha.hbwd[k] = hvol + (size_t)(2 * k + 1) * N * Dp;
   }
+  SF_TRY_CUDA(cudaMemsetAsync(ws + lay.err, 0, sizeof(int), s));
   // the horizontal paths run beside the down sweep; the up sweep joins them
   std::lock_guard<std::mutex> guard(g_side_mu);
   SideStream* side = nullptr;
@@ -232,7 +234,6 @@ sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8
   SF_TRY_CUDA(cudaEventRecord(side->join, side->s));
   int* flags = reinterpret_cast<int*>(ws + lay.flags);
   SF_TRY_CUDA(cudaMemsetAsync(flags, 0, (size_t)2 * (npass * J + 1) * sizeof(int), s));
-  SF_TRY_CUDA(cudaMemsetAsync(ws + lay.err, 0, sizeof(int), s));
   fused::SweepArgs sa{};
   sa.W = W; sa.H = H; sa.D = p->D; sa.Dp = Dp; sa.P1 = p->P1; sa.P2 = p->P2; sa.J = J;
   sa.nb = (H + fused::band_rows(p->D) - 1) / fused::band_rows(p->D); sa.items = npass * J; sa.subpixel = p->subpixel;

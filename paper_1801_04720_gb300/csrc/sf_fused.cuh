@@ -41,6 +41,7 @@ struct PassIO {
 struct HLineArgs {
   int W, H, D, Dp, npass, P1, P2;
   uint32_t path_mask;
+  int* err;              // set to 1 when a bounded copy wait gives up
   const uint8_t* cost[kMaxPass];
   uint8_t* hfwd[kMaxPass];
   uint8_t* hbwd[kMaxPass];

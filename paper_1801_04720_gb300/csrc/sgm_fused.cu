@@ -102,87 +102,167 @@ __global__ void __launch_bounds__(512)
 // ---------------------------------------------------------------------------
 // 2. horizontal paths
 // ---------------------------------------------------------------------------
-constexpr int kHlineThreads = 256;
-constexpr int kHlinePrefetch = 8;   // cost columns in flight per thread
+// A CTA walks 16 consecutive rows (8 line pairs, two rows per register) of
+// one pass in one direction.  Column chunks of the cost volume (16 rows x CW
+// columns x Dp bytes, contiguous per row) arrive by bulk asynchronous copy
+// (the TMA engine) into a double-buffered shared tile, completion tracked by
+// an mbarrier, so the serial walk along x reads its costs from shared memory.
+constexpr int kHlinePairs = 8;                 // line pairs per CTA
+constexpr int kHlineRows = 2 * kHlinePairs;
+constexpr int kHlineTileBytes = 32 * 1024;     // one buffer
+constexpr long long kMbarSpin = 1ll << 22;     // bounded mbarrier wait
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(bar)),
+               "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared.b64 _, [%0], %1;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"((unsigned)__cvta_generic_to_shared(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          (unsigned)__cvta_generic_to_shared(dst)),
+      "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 template <int DC, int CHUNKS>
-__global__ void __launch_bounds__(kHlineThreads)
+__global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     hline_kernel(HLineArgs a) {
   using V = typename ByteVec<DC>::T;
-  // per-thread ring of prefetched cost columns: [slot][row y0 / y1][thread]
-  extern __shared__ __align__(16) uint8_t hsmem[];
-  V* ring = reinterpret_cast<V*>(hsmem);
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int item = gt / CHUNKS;
-  const int q = gt - item * CHUNKS;
-  const int rows2 = (a.H + 1) / 2;
-  const int per_pass = rows2 * 2;
-  const bool active = item < a.npass * per_pass;
-  const int p = active ? item / per_pass : 0;
-  const int rem = item - p * per_pass;
-  const int dir = rem / rows2;           // 0: (+1,0), 1: (-1,0)
-  const int rp = rem - dir * rows2;
-  const int y0 = active ? 2 * rp : 0, y1 = active ? min(2 * rp + 1, a.H - 1) : 0;
-  const int W = a.W, Dp = a.Dp;
-  const int d0 = q * DC;
-  // chunks at or past the padded depth hold no data
-  const bool enabled = active && ((a.path_mask >> dir) & 1u) && d0 < Dp;
+  extern __shared__ __align__(128) uint8_t hsmem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int s_fail;
+  const int W = a.W, H = a.H, Dp = a.Dp;
+  const int nrb = (H + kHlineRows - 1) / kHlineRows;
+  const int blk = blockIdx.x;
+  const int p = blk / (2 * nrb);
+  const int rem = blk - p * 2 * nrb;
+  const int dir = rem / nrb;                 // 0: (+1,0), 1: (-1,0)
+  const int rb = rem - dir * nrb;
+  if (!((a.path_mask >> dir) & 1u)) return;  // whole CTA: direction disabled
   const uint8_t* C = a.cost[0];
   uint8_t* out = dir == 0 ? a.hfwd[0] : a.hbwd[0];
 #pragma unroll
-  for (int k = 1; k < kMaxPass; k++) {   // select without indexing the parameter array
+  for (int k = 1; k < kMaxPass; k++) {       // select without indexing the parameter array
     if (p == k) {
       C = a.cost[k];
       out = dir == 0 ? a.hfwd[k] : a.hbwd[k];
     }
   }
+  const int t = threadIdx.x;
+  const int lp = t / CHUNKS;
+  const int q = t - lp * CHUNKS;
+  const int ybase = rb * kHlineRows;
+  const int nrows = min(kHlineRows, H - ybase);
+  const int r0 = 2 * lp, r1 = min(2 * lp + 1, nrows - 1);
+  const bool row_ok = r0 < nrows;
+  const int d0 = q * DC;
+  const bool live = d0 < Dp;                 // chunks past the padded depth hold no data
   const bool pad = d0 + DC > a.D;
   const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
-  const int step = dir == 0 ? 1 : -1;
-  const int xstart = dir == 0 ? 0 : W - 1;
-  auto issue = [&](int s) {   // prefetch column number s into its ring slot
-    const int xs = xstart + s * step;
-    const bool ok = enabled && s < W;
-    V* dst = ring + (s % kHlinePrefetch) * 2 * kHlineThreads + threadIdx.x;
-    const uint8_t* src0 = ok ? C + ((size_t)y0 * W + xs) * Dp + d0 : C;
-    const uint8_t* src1 = ok ? C + ((size_t)y1 * W + xs) * Dp + d0 : C;
-    cp_async<DC>(dst, src0, ok);
-    cp_async<DC>(dst + kHlineThreads, src1, ok);
-    cp_async_commit();
+  const int CW = max(1, kHlineTileBytes / (kHlineRows * Dp));   // columns per chunk
+  const int nchunks = (W + CW - 1) / CW;
+  uint8_t* buf[2] = {hsmem, hsmem + kHlineTileBytes};
+  auto chunk_x0 = [&](int c) { return dir == 0 ? c * CW : max(0, W - (c + 1) * CW); };
+  auto chunk_w = [&](int c) { return dir == 0 ? min(CW, W - c * CW) : (W - c * CW) - chunk_x0(c); };
+  auto issue = [&](int c) {                  // one thread: all rows of chunk c
+    uint8_t* dst = buf[c & 1];
+    const int xs = chunk_x0(c), cw = chunk_w(c);
+    const unsigned bytes = (unsigned)(cw * Dp);
+    fence_proxy_async();
+    mbar_arrive_tx(&bars[c & 1], bytes * (unsigned)nrows);
+    for (int r = 0; r < nrows; r++)
+      bulk_g2s(dst + (size_t)r * CW * Dp, C + ((size_t)(ybase + r) * W + xs) * Dp, bytes, &bars[c & 1]);
   };
-#pragma unroll
-  for (int s = 0; s < kHlinePrefetch - 1; s++) issue(s);
+  if (t == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) issue(0);
   uint32_t L[DC], Cr[DC], N[DC];
 #pragma unroll
   for (int i = 0; i < DC; i++) L[i] = 0;
   uint32_t m = 0;
-  int x = xstart;
-  for (int s = 0; s < W; s++, x += step) {
-    issue(s + kHlinePrefetch - 1);
-    cp_async_wait<kHlinePrefetch - 1>();
-    const V* src = ring + (s % kHlinePrefetch) * 2 * kHlineThreads + threadIdx.x;
-    bytes_to_pairs<DC>(src[0], src[kHlineThreads], Cr);
-    if (pad) {
-#pragma unroll
-      for (int i = 0; i < DC; i++)
-        if (d0 + i >= a.D) Cr[i] = kPadCost2;
+  int s = 0;                                 // step along the line
+  for (int c = 0; c < nchunks; c++) {
+    if (t == 0 && c + 1 < nchunks) issue(c + 1);
+    // bounded wait for chunk c
+    {
+      long long spins = 0;
+      while (!mbar_try_wait(&bars[c & 1], (unsigned)((c >> 1) & 1))) {
+        if (++spins > kMbarSpin) {
+          s_fail = 1;
+          break;
+        }
+      }
     }
-    uint32_t left = __shfl_up_sync(0xffffffffu, L[DC - 1], 1, CHUNKS);
-    uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, CHUNKS);
-    if (q == 0) left = (s == 0) ? 0u : kInf2;
-    if (q == CHUNKS - 1) right = (s == 0) ? 0u : kInf2;
-    sgm_update<DC>(L, Cr, left, right, m, p1x2, p2x2, N);
-    m = group_min2<CHUNKS>(tree_min<DC>(N));
+    if (s_fail) break;
+    const uint8_t* tile = buf[c & 1];
+    const int xs = chunk_x0(c), cw = chunk_w(c);
+    for (int u = 0; u < cw; u++, s++) {
+      const int cx = dir == 0 ? u : cw - 1 - u;
+      const int x = xs + cx;
+      V va = ByteVec<DC>::zero(), vb = va;
+      if (live && row_ok) {
+        va = *reinterpret_cast<const V*>(tile + ((size_t)r0 * CW + cx) * Dp + d0);
+        vb = *reinterpret_cast<const V*>(tile + ((size_t)r1 * CW + cx) * Dp + d0);
+      }
+      bytes_to_pairs<DC>(va, vb, Cr);
+      if (pad) {
 #pragma unroll
-    for (int i = 0; i < DC; i++) L[i] = N[i];
-    if (enabled) {
-      V oa, ob;
-      pairs_to_bytes<DC>(N, oa, ob);
-      __stcs(reinterpret_cast<V*>(out + ((size_t)y0 * W + x) * Dp + d0), oa);
-      if (y1 != y0) __stcs(reinterpret_cast<V*>(out + ((size_t)y1 * W + x) * Dp + d0), ob);
+        for (int i = 0; i < DC; i++)
+          if (d0 + i >= a.D) Cr[i] = kPadCost2;
+      }
+      uint32_t left = __shfl_up_sync(0xffffffffu, L[DC - 1], 1, CHUNKS);
+      uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, CHUNKS);
+      if (q == 0) left = (s == 0) ? 0u : kInf2;
+      if (q == CHUNKS - 1) right = (s == 0) ? 0u : kInf2;
+      sgm_update<DC>(L, Cr, left, right, m, p1x2, p2x2, N);
+      m = group_min2<CHUNKS>(tree_min<DC>(N));
+#pragma unroll
+      for (int i = 0; i < DC; i++) L[i] = N[i];
+      if (live && row_ok) {
+        V oa, ob;
+        pairs_to_bytes<DC>(N, oa, ob);
+        __stcs(reinterpret_cast<V*>(out + ((size_t)(ybase + r0) * W + x) * Dp + d0), oa);
+        if (r1 != r0) __stcs(reinterpret_cast<V*>(out + ((size_t)(ybase + r1) * W + x) * Dp + d0), ob);
+      }
     }
+    __syncthreads();   // buffer c&1 is free for chunk c+2
   }
-  cp_async_wait<0>();
+  if (s_fail) {
+    // a copy never completed: record it, let in-flight copies land (bounded)
+    if (t == 0) {
+      atomicExch(a.err, 1);
+      for (int b = 0; b < 2; b++) {
+        long long spins = 0;
+        while (!mbar_try_wait(&bars[b], 0) && !mbar_try_wait(&bars[b], 1) && ++spins < kMbarSpin) {
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -226,8 +306,10 @@ struct SweepCfg {
   }
 };
 
+// Registers are capped so that a 512-thread sweep CTA leaves room on its SM
+// for the horizontal-path blocks that run beside it.
 template <int DC, int CHUNKS, int HALO, bool UP>
-__global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
+__global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ? 96 : 168)
     sweep_kernel(SweepArgs a) {
   using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
   using V = typename ByteVec<DC>::T;
@@ -623,14 +705,12 @@ cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int 
 
 template <int DC, int CHUNKS>
 static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
-  const int rows2 = (a.H + 1) / 2;
-  const long long threads = (long long)a.npass * rows2 * 2 * CHUNKS;
-  const size_t smem = (size_t)kHlinePrefetch * kHlineThreads * 2 * DC;
+  const int nrb = (a.H + kHlineRows - 1) / kHlineRows;
+  const size_t smem = 2 * (size_t)kHlineTileBytes;
   cudaError_t e = cudaFuncSetAttribute(hline_kernel<DC, CHUNKS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  hline_kernel<DC, CHUNKS><<<(unsigned)((threads + kHlineThreads - 1) / kHlineThreads),
-                             kHlineThreads, smem, s>>>(a);
+  hline_kernel<DC, CHUNKS><<<a.npass * 2 * nrb, kHlinePairs * CHUNKS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
