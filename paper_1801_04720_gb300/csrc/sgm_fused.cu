@@ -300,7 +300,7 @@ struct SweepCfg {
   static constexpr size_t smem_bytes() {
     return (size_t)2 * 2 * (DC / 4) * NT * 16     // diagonal hand-over
            + (size_t)2 * 2 * NP * 4                // pair minima
-           + (size_t)(DC / 4) * NO * 16            // selection row (UP)
+           + (size_t)2 * (DC / 4) * NO * 16        // aggregated-cost rows for selection (UP)
            + (size_t)RING * 2 * NT * DC            // cost ring
            + (UP ? (size_t)RING * XW * NO * 16 : 0);
   }
@@ -315,6 +315,10 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
   using V = typename ByteVec<DC>::T;
   constexpr int NP = Cfg::NP, NT = Cfg::NT, NO = Cfg::NO, TH = Cfg::TH, RING = Cfg::RING;
   constexpr int XW = Cfg::XW, G = DC / 4;
+  // winner selection by the halo warps (they carry two paths, the owned
+  // warps three plus the sums): SEL_T threads per output column
+  constexpr int SEL_T = (HALO * CHUNKS) / kTW;
+  constexpr bool HALO_SELECT = UP && CHUNKS >= 2 && SEL_T >= 1 && (CHUNKS % SEL_T) == 0;
   extern __shared__ __align__(16) uint8_t smem[];
   // diagonal hand-over buffers, [parity][register group][thread] uint4
   // (consecutive threads hit consecutive 16-byte words: no bank conflicts)
@@ -322,8 +326,8 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
   uint4* xfr = xfl + 2 * G * NT;
   uint32_t* mfl = reinterpret_cast<uint32_t*>(xfr + 2 * G * NT);   // [parity][pair]
   uint32_t* mfr = mfl + 2 * NP;
-  uint4* srow = reinterpret_cast<uint4*>(mfr + 2 * NP);            // [group][owned thread]
-  V* ringc = reinterpret_cast<V*>(srow + G * NO);                  // [slot][lo/hi][thread]
+  uint4* srow = reinterpret_cast<uint4*>(mfr + 2 * NP);            // [parity][group][owned thread]
+  V* ringc = reinterpret_cast<V*>(srow + 2 * G * NO);              // [slot][lo/hi][thread]
   uint4* ringx = reinterpret_cast<uint4*>(ringc + RING * 2 * NT);  // [slot][XW][owned thread]
   __shared__ int s_abort;
   __shared__ int s_task;
@@ -487,6 +491,53 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       mr = have ? (ar & fr_keep) : 0u;
     }
 
+    // winner-take-all + parabolic subpixel of row kk, done by halo threads
+    // from the aggregated costs the owned threads left in shared memory
+    auto select_row = [&](int kk) {
+      if (!HALO_SELECT || owned || !io.dint) return;
+      const int yk = UP ? ytop + nrows - 1 - kk : ytop + kk;
+      const int ht = t - NO;
+      const int c = ht / SEL_T, sub = ht - c * SEL_T;
+      const int cpr = c & 15, cl = c >> 4;
+      const int x = x0 + c;
+      const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow + (kk & 1) * G * NO);
+      auto s_at = [&](int d) {
+        const int qq = d / DC, ii = d - qq * DC;
+        return (sw[((ii >> 2) * NO + cpr * CHUNKS + qq) * 4 + (ii & 3)] >> (16 * cl)) & 0xffffu;
+      };
+      constexpr int CPT = CHUNKS / (SEL_T > 0 ? SEL_T : 1);
+      uint32_t key = 0xffffffffu;   // S * 256 + d: the minimum is the smallest d with minimal S
+#pragma unroll
+      for (int j = 0; j < CPT; j++) {
+        const int qq = sub * CPT + j;
+#pragma unroll
+        for (int w = 0; w < G; w++) {
+          const uint4 v4 = srow[(kk & 1) * G * NO + w * NO + cpr * CHUNKS + qq];
+          const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int e = 0; e < 4; e++) {
+            const int d = qq * DC + 4 * w + e;
+            const uint32_t sv = (vv[e] >> (16 * cl)) & 0xffffu;
+            if (d < a.D) key = min(key, sv * 256u + (uint32_t)d);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < SEL_T; o <<= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o, SEL_T > 0 ? SEL_T : 1));
+      if (sub == 0 && x < W) {
+        const int ds = (int)(key & 255u);
+        const int sv = (int)(key >> 8);
+        float v = (float)ds;
+        if (a.subpixel && ds > 0 && ds < a.D - 1) {
+          const int am = (int)s_at(ds - 1) - sv;
+          const int bp = (int)s_at(ds + 1) - sv;
+          v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+        }
+        io.dint[(size_t)yk * W + x] = (int16_t)ds;
+        if (io.dsub) io.dsub[(size_t)yk * W + x] = v;
+      }
+    };
+
     for (int k = 0; k < nrows; k++) {
       const int y = UP ? ytop + nrows - 1 - k : ytop + k;
       issue_row(k + RING - 1);
@@ -579,7 +630,10 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
               }
             }
           }
-          if (io.dint) {
+          if (io.dint && HALO_SELECT) {
+            // the halo warps select the winners of this row after the barrier
+            store_u4<DC>(srow + (k & 1) * G * NO + t, NO, S);
+          } else if (io.dint) {
             // winner-take-all: the smallest d with the minimal S, per lane
             const uint32_t gmin = group_min2<CHUNKS>(tree_min<DC>(S), own_mask);
             uint32_t first = 0xffffffffu;
@@ -679,6 +733,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         for (int i = 0; i < DC; i++) Lr[i] &= fr_keep;
         mr &= fr_keep;
       }
+      select_row(k);   // halo threads; row k's costs are complete after the barrier
     }
     // ---- publish progress: the barrier orders every thread's band-end
     // stores before thread 0's release (cumulativity); the exchange buffers
@@ -686,6 +741,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     cp_async_wait<0>();
     __syncthreads();
     if (t == 0) st_release(a.flags + p * J + j, bi + 1);
+    select_row(nrows - 1);   // the last row of the band (its costs are in place)
   }
 }
 
