@@ -269,10 +269,12 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
 // 3./4. band sweeps
 // ---------------------------------------------------------------------------
 // Thread layout: t = pair * CHUNKS + q.  Pairs 0..15 own columns
-// (x0 + c, x0 + 16 + c); pairs 16 .. 16+HALO-1 are halo pairs
-// (x0 - HALO + h, x1 + h) carrying the diagonal paths into the strip.
-// FL = the diagonal path fed from column x-1 ((+1,+1) down, (+1,-1) up),
-// FR = the one fed from column x+1 ((-1,+1) down, (-1,-1) up).
+// (x0 + c, x0 + 16 + c) and carry all three paths.  FL = the diagonal path fed
+// from column x-1 ((+1,+1) down, (+1,-1) up), FR = the one fed from column
+// x+1 ((-1,+1) down, (-1,-1) up).  FL enters the strip from the left, so the
+// left halo pairs (x0 - HALO + h, x0 - HALO/2 + h) carry FL only; the right
+// halo pairs (x1 + h, x1 + HALO/2 + h) carry FR only.  Halo pairs whose
+// columns can no longer reach the strip before the band ends skip the update.
 
 template <int N>
 __device__ __forceinline__ void load_u4(uint32_t* r, const uint4* src, int stride) {
@@ -347,20 +349,26 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
   // lanes of owned pairs in this warp (owned and halo pairs share a warp
   // only when CHUNKS == 1)
   const unsigned own_mask = __ballot_sync(0xffffffffu, owned);
+  constexpr int HH = HALO / 2;             // pairs per halo side
+  constexpr int LH0 = 16, RH0 = 16 + HH;    // first left / right halo pair
+  const int role = owned ? 0 : (pr < RH0 ? 1 : 2);   // 0 owned, 1 left halo, 2 right halo
+  const int hh = role == 1 ? pr - LH0 : pr - RH0;
   // hand-over sources: FL from column x-1, FR from column x+1.  Whole
-  // registers move between pairs except at the two seams of the layout.
-  int fl_src, fl_src2 = -1, fr_src, fr_src2 = -1;
+  // registers move between pairs except at the seams of the layout, where
+  // prmt joins one lane of each of two pairs.
+  int fl_src = pr, fl_src2 = -1, fr_src = pr, fr_src2 = -1;
   uint32_t fl_sel = 0, fr_sel = 0;
-  if (owned) {
+  if (role == 0) {
     if (pr > 0) fl_src = pr - 1;
-    else { fl_src = NP - 1; fl_src2 = 15; fl_sel = 0x5410u; }     // (x0-1, x0+15)
+    else { fl_src = RH0 - 1; fl_src2 = 15; fl_sel = 0x5432u; }    // (x0-1, x0+15)
     if (pr < 15) fr_src = pr + 1;
-    else { fr_src = 0; fr_src2 = 16; fr_sel = 0x7632u; }          // (x0+16, x1)
+    else { fr_src = 0; fr_src2 = RH0; fr_sel = 0x5432u; }         // (x0+16, x1)
+  } else if (role == 1) {
+    if (hh > 0) fl_src = pr - 1;
+    else { fl_src = pr; fl_src2 = RH0 - 1; fl_sel = 0x5410u; }    // (-, x0-HALO/2-1)
   } else {
-    const int h = pr - 16;
-    if (h > 0) fl_src = pr - 1;
-    else { fl_src = pr; fl_src2 = 15; fl_sel = 0x7610u; }         // (-, x1-1)
-    fr_src = (h < HALO - 1) ? pr + 1 : 0;                         // (x0, -) at the seam
+    if (hh < HH - 1) fr_src = pr + 1;
+    else { fr_src = RH0; fr_src2 = pr; fr_sel = 0x7632u; }        // (x1+HALO/2, -)
   }
   if (t == 0) s_abort = 0;
   __syncthreads();
@@ -385,12 +393,15 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     const int x0 = j * kTW;
     // ---- columns of this thread's pair ----
     int xlo, xhi;
-    if (owned) {
+    if (role == 0) {
       xlo = x0 + pr;
       xhi = x0 + 16 + pr;
+    } else if (role == 1) {
+      xlo = x0 - HALO + hh;
+      xhi = x0 - HH + hh;
     } else {
-      xlo = x0 - HALO + (pr - 16);
-      xhi = x0 + kTW + (pr - 16);
+      xlo = x0 + kTW + hh;
+      xhi = x0 + kTW + HH + hh;
     }
     const bool lo_in = live && xlo >= 0 && xlo < W, hi_in = live && xhi >= 0 && xhi < W;
     const PassIO& io = a.io[p];
@@ -477,8 +488,16 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
 #pragma unroll
         for (int i = 0; i < DC; i++) Lv[i] = 0;
       }
-      load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
-      load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
+      if (role != 2) load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
+      else {
+#pragma unroll
+        for (int i = 0; i < DC; i++) Lf[i] = 0;
+      }
+      if (role != 1) load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
+      else {
+#pragma unroll
+        for (int i = 0; i < DC; i++) Lr[i] = 0;
+      }
       uint32_t av = tree_min<DC>(Lv), af = tree_min<DC>(Lf), ar = tree_min<DC>(Lr);
 #pragma unroll
       for (int o = 1; o < CHUNKS; o <<= 1) {
@@ -572,11 +591,22 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       }
       // ---- all three paths ----
       uint32_t Nv[DC], Nf[DC], Nr[DC];
+      // a halo pair works while one of its columns can still reach the strip
+      const bool act_fl = role == 0 || (role == 1 && hh + HH >= k);
+      const bool act_fr = role == 0 || (role == 2 && hh <= HALO - 1 - k);
       if (owned) sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2x2, Nv);
-      sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
-      sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+      if (act_fl) sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
+      else {
+#pragma unroll
+        for (int i = 0; i < DC; i++) Nf[i] = Lf[i];
+      }
+      if (act_fr) sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+      else {
+#pragma unroll
+        for (int i = 0; i < DC; i++) Nr[i] = Lr[i];
+      }
       uint32_t av = owned ? tree_min<DC>(Nv) : 0u;
-      uint32_t af = tree_min<DC>(Nf), ar = tree_min<DC>(Nr);
+      uint32_t af = act_fl ? tree_min<DC>(Nf) : 0u, ar = act_fr ? tree_min<DC>(Nr) : 0u;
 #pragma unroll
       for (int o = 1; o < CHUNKS; o <<= 1) {
         av = vmin2(av, __shfl_xor_sync(0xffffffffu, av, o, CHUNKS));
@@ -588,8 +618,8 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       mr = ar;
       // ---- diagonal hand-over to the next row (written early) ----
       if (k + 1 < nrows) {
-        store_u4<DC>(xfl + par * G * NT + t, NT, Nf);
-        store_u4<DC>(xfr + par * G * NT + t, NT, Nr);
+        if (role != 2) store_u4<DC>(xfl + par * G * NT + t, NT, Nf);
+        if (role != 1) store_u4<DC>(xfr + par * G * NT + t, NT, Nr);
         if (q == 0) {
           mfl[par * NP + pr] = mf;
           mfr[par * NP + pr] = mr;
@@ -694,7 +724,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         break;
       }
       __syncthreads();
-      {
+      if (role != 2) {
         const uint4* b = xfl + par * G * NT;
         if (fl_src2 < 0) {
           load_u4<DC>(Lf, b + fl_src * CHUNKS + q, NT);
@@ -708,7 +738,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
           mf = prmt(mfl[par * NP + fl_src], mfl[par * NP + fl_src2], fl_sel);
         }
       }
-      {
+      if (role != 1) {
         const uint4* b = xfr + par * G * NT;
         if (fr_src2 < 0) {
           load_u4<DC>(Lr, b + fr_src * CHUNKS + q, NT);
