@@ -192,6 +192,59 @@ sf_status sf_scene_flow_host(const uint8_t* left_t, const uint8_t* right_t,
                              uint8_t* valid_out, void* dev_workspace, size_t ws_bytes,
                              void* stream);
 
+/* ---- batches of quadruples with uneven sizes ------------------------------ */
+
+/* One quadruple of a batch: device pointers as in sf_scene_flow, its own size
+ * W x H, row pitch and number of disparities D (1..256), its own camera. */
+typedef struct {
+  const uint8_t* left_t;
+  const uint8_t* right_t;
+  const uint8_t* left_t1;
+  const uint8_t* right_t1;
+  int32_t pitch;
+  const float* flow;        /* [H][W][2] */
+  int32_t W, H, D;
+  sf_camera cam;
+  float* s4_out;            /* [H][W][4], 16-byte aligned */
+  float* motion_out;        /* [H][W][3] or NULL */
+  float* point_out;         /* [H][W][3] or NULL */
+  uint8_t* valid_out;       /* [H][W] */
+  float* D0_out;            /* [H][W] or NULL */
+  float* D1_out;            /* [H][W] or NULL */
+} sf_batch_item;
+
+#define SF_BATCH_GRAPH 1u   /* capture the batch into a CUDA graph once per
+                               signature (items, params, workspace, stream)
+                               and replay it on later calls */
+
+/* Workspace bytes for sf_batch_run over these items (0 if an item is
+ * invalid or too wide for the fused kernels). */
+size_t sf_batch_workspace_size(const sf_batch_item* items, int32_t n, const sf_sgm_params* p);
+
+/* The whole hot path for n quadruples at once (Sec. 3; the batch is this
+ * library's addition).  The stereo passes of all items share persistent
+ * sweep launches, one per kernel shape (items are grouped by D): a band-major
+ * task queue walks every (item, pass, band, strip).  p->D is ignored (each
+ * item has its own D); the other parameters apply to every item.  With
+ * SF_BATCH_GRAPH the first call for a signature records a CUDA graph
+ * (its set-up copies the batch's descriptor tables synchronously, so that
+ * first call must not itself be under stream capture) and later calls replay
+ * it; graph mode needs a created stream (not NULL: the legacy default
+ * stream cannot be captured).  Outputs as in sf_scene_flow, per item. */
+sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_params* p,
+                       uint32_t flags, void* workspace, size_t ws_bytes, void* stream);
+
+/* Destroys the CUDA graphs cached by sf_batch_run (host-side resources). */
+void sf_batch_release_graphs(void);
+
+/* Kernel shape of the band sweeps for a class of disparity counts, as chosen
+ * by an autotuner: every D in [d_lo, d_hi] then runs with `dc` disparities
+ * per thread (8 or 16) and `halo` halo columns (8 or 16; the band height is
+ * halo + 1).  Combinations the build does not provide, or too few threads
+ * for D, return SF_ERR_UNSUPPORTED; dc = 0 restores the built-in choice for
+ * the class.  Process-wide; results are identical for every shape. */
+sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo);
+
 /* ---- tracing and counters (host-side bookkeeping; no paper counterpart) --- */
 
 /* Stage ids written by the tracer. */

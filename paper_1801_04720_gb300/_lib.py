@@ -28,7 +28,10 @@ EXPORTED = [
     "sf_combine_sceneflow", "sf_workspace_size", "sf_sgm_full", "sf_scene_flow",
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
     "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
+    "sf_batch_workspace_size", "sf_batch_run", "sf_batch_release_graphs", "sf_set_sweep_shape",
 ]
+
+SF_BATCH_GRAPH = 1
 
 STAGE_NAMES = ["census", "cost", "aggregate", "select", "lrcheck", "combine", "sgm_sweep"]
 
@@ -48,6 +51,16 @@ class SgmParams(ctypes.Structure):
 class Camera(ctypes.Structure):
     _fields_ = [("f", ctypes.c_float), ("B", ctypes.c_float), ("cx", ctypes.c_float),
                 ("cy", ctypes.c_float)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("left_t", ctypes.c_void_p), ("right_t", ctypes.c_void_p),
+                ("left_t1", ctypes.c_void_p), ("right_t1", ctypes.c_void_p),
+                ("pitch", ctypes.c_int32), ("flow", ctypes.c_void_p), ("W", ctypes.c_int32),
+                ("H", ctypes.c_int32), ("D", ctypes.c_int32), ("cam", Camera),
+                ("s4_out", ctypes.c_void_p), ("motion_out", ctypes.c_void_p),
+                ("point_out", ctypes.c_void_p), ("valid_out", ctypes.c_void_p),
+                ("D0_out", ctypes.c_void_p), ("D1_out", ctypes.c_void_p)]
 
 
 def params(D=128, P1=7, P2=86, census_w=9, census_h=7, path_mask=0xFF, subpixel=True, lr_tol=1):
@@ -96,6 +109,10 @@ def load(path: str = LIB_PATH):
             "sf_trace_disarm": (i32, []),
             "sf_kernel_launches": (ctypes.c_uint64, []),
             "sf_set_fused": (i32, [i32]),
+            "sf_batch_workspace_size": (sz, [P, i32, PP]),
+            "sf_batch_run": (i32, [P, i32, PP, ctypes.c_uint32, P, sz, P]),
+            "sf_batch_release_graphs": (None, []),
+            "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
             "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
         }
         for name, (res, args) in sig.items():
@@ -341,3 +358,41 @@ class StageTracer:
 
 def kernel_launches():
     return int(load().sf_kernel_launches())
+
+
+# ---- batches ----------------------------------------------------------------
+
+def _vp(t):
+    return t.data_ptr() if t is not None else None
+
+
+def make_batch(scenes, outs):
+    """scenes: list of dicts with CUDA tensors left_t, right_t, left_t1, right_t1,
+    flow and ints D plus a Camera cam; outs: matching dicts from
+    alloc_scene_flow_outputs.  Returns a ctypes array of BatchItem."""
+    arr = (BatchItem * len(scenes))()
+    for i, (sc, o) in enumerate(zip(scenes, outs)):
+        H, W = sc["left_t"].shape
+        arr[i] = BatchItem(_vp(sc["left_t"]), _vp(sc["right_t"]), _vp(sc["left_t1"]),
+                           _vp(sc["right_t1"]), sc["left_t"].stride(0), _vp(sc["flow"]), W, H,
+                           sc["D"], sc["cam"], _vp(o["s4"]), _vp(o.get("motion")),
+                           _vp(o.get("point")), _vp(o["valid"]), _vp(o.get("D0")), _vp(o.get("D1")))
+    return arr
+
+
+def sf_batch_workspace_size(items, p: SgmParams):
+    return int(load().sf_batch_workspace_size(items, len(items), ctypes.byref(p)))
+
+
+def sf_batch_run(items, p: SgmParams, ws, graph=False, stream=None):
+    _check("sf_batch_run", load().sf_batch_run(items, len(items), ctypes.byref(p),
+                                               SF_BATCH_GRAPH if graph else 0, _ptr(ws), ws.numel(),
+                                               _stream(stream)))
+
+
+def sf_batch_release_graphs():
+    load().sf_batch_release_graphs()
+
+
+def sf_set_sweep_shape(d_lo, d_hi, dc, halo):
+    _check("sf_set_sweep_shape", load().sf_set_sweep_shape(d_lo, d_hi, dc, halo))

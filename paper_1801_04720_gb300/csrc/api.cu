@@ -4,6 +4,8 @@
 
 #include <atomic>
 #include <mutex>
+#include <vector>
+#include <algorithm>
 
 #include "sf_fused.cuh"
 #include "sf_internal.cuh"
@@ -156,28 +158,76 @@ bool fused_eligible(int W, int H, const sf_sgm_params* p) {
   return fused::cost_pair_smem(W, p->D) <= 227u * 1024u;
 }
 
-// Workspace of the fused path for `npairs` stereo pairs (2 passes each).
-struct FusedLayout {
-  size_t census, cost, hvol, sdown, bs, flags, err, dint, dsub, valid, disp, total;
-  FusedLayout(int W, int H, int D, int npairs) {
-    const size_t N = (size_t)W * H;
-    const int Dp = fused::padded_d(D), npass = 2 * npairs;
-    const int J = (W + fused::kTW - 1) / fused::kTW;
-    size_t o = 0;
-    census = o; o = align_up(o + (size_t)npass * N * sizeof(uint64_t), 256);
-    cost = o; o = align_up(o + (size_t)npass * N * Dp, 256);
-    hvol = o; o = align_up(o + (size_t)npass * 2 * N * Dp, 256);
-    sdown = o; o = align_up(o + fused::sdown_bytes(W, H, D, npass), 256);
-    bs = o; o = align_up(o + fused::bs_bytes(W, D, npass), 256);
-    flags = o; o = align_up(o + (size_t)2 * (npass * J + 1) * sizeof(int), 256);
-    err = o; o = align_up(o + 256, 256);
-    dint = o; o = align_up(o + (size_t)npass * N * sizeof(int16_t), 256);
-    dsub = o; o = align_up(o + (size_t)npairs * N * sizeof(float), 256);
-    valid = o; o = align_up(o + (size_t)npairs * N, 256);
-    disp = o; o = align_up(o + (size_t)npairs * N * sizeof(float), 256);
+// ---- fused-path workspace --------------------------------------------------
+// A control block (error word, task counters, per-pass band flags: zeroed by
+// one memset per call) followed by the buffers of each stereo pair.
+struct PassBuffers {
+  size_t cost, hf, hb, sdown, bs, dint, flags;   // flags: offset in the control block
+};
+struct PairBuffers {
+  size_t census_l, census_r, dsub, valid, disp;
+  PassBuffers pass[2];
+};
+struct PairShape {
+  int W, H, D;
+};
+
+size_t carve(size_t& o, size_t bytes) {
+  const size_t at = o;
+  o = align_up(o + bytes, 256);
+  return at;
+}
+
+struct FusedPlan {
+  std::vector<PairBuffers> pairs;
+  size_t err = 0, counters = 0, control_bytes = 0, tables = 0, total = 0;
+  int ncounters = 0;
+  // Dshape(i): the D that fixes the kernel shape of pair i's sweeps
+  FusedPlan(const PairShape* ps, int n, const int* dshape, int ncounters_, size_t table_bytes) {
+    pairs.resize(n);
+    ncounters = ncounters_;
+    size_t c = 0;
+    err = c; c += sizeof(int);
+    counters = c; c += (size_t)ncounters * sizeof(int);
+    for (int i = 0; i < n; i++) {
+      const int J = (ps[i].W + fused::kTW - 1) / fused::kTW;
+      for (int k = 0; k < 2; k++) {
+        pairs[i].pass[k].flags = c;
+        c += (size_t)2 * J * sizeof(int);
+      }
+    }
+    control_bytes = align_up(c, 256);
+    size_t o = control_bytes;
+    tables = carve(o, table_bytes);
+    for (int i = 0; i < n; i++) {
+      const int W = ps[i].W, H = ps[i].H, D = ps[i].D;
+      const size_t N = (size_t)W * H;
+      const int Dp = fused::padded_d(D);
+      PairBuffers& b = pairs[i];
+      b.census_l = carve(o, N * sizeof(uint64_t));
+      b.census_r = carve(o, N * sizeof(uint64_t));
+      for (int k = 0; k < 2; k++) {
+        PassBuffers& pb = b.pass[k];
+        pb.cost = carve(o, N * Dp);
+        pb.hf = carve(o, N * Dp);
+        pb.hb = carve(o, N * Dp);
+        pb.sdown = carve(o, fused::sdown_bytes(W, H, dshape[i]));
+        pb.bs = carve(o, fused::bs_bytes(W, D));
+        pb.dint = carve(o, N * sizeof(int16_t));
+      }
+      b.dsub = carve(o, N * sizeof(float));
+      b.valid = carve(o, N);
+      b.disp = carve(o, N * sizeof(float));
+    }
     total = o;
   }
 };
+
+FusedPlan single_plan(int W, int H, int D, int npairs) {
+  PairShape ps[2] = {{W, H, D}, {W, H, D}};
+  int dshape[2] = {D, D};
+  return FusedPlan(ps, npairs, dshape, 2, 0);
+}
 
 constexpr long long kSpinLimit = 1ll << 24;   // bounded neighbour wait (~1 s)
 
@@ -206,24 +256,101 @@ cudaError_t side_stream(SideStream** out) {
   return cudaSuccess;
 }
 
-// Band sweeps + horizontal paths for `npass` cost volumes already in place.
-sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8_t* ws,
-                          const FusedLayout& lay, const fused::PassIO* io_up, cudaStream_t s) {
-  const size_t N = (size_t)W * H;
-  const int Dp = fused::padded_d(p->D);
-  const int J = (W + fused::kTW - 1) / fused::kTW;
-  uint8_t* cost = ws + lay.cost;
-  uint8_t* hvol = ws + lay.hvol;
-  fused::HLineArgs ha{};
-  ha.W = W; ha.H = H; ha.D = p->D; ha.Dp = Dp; ha.npass = npass; ha.P1 = p->P1; ha.P2 = p->P2;
-  ha.path_mask = p->path_mask;
-  ha.err = reinterpret_cast<int*>(ws + lay.err);
-  for (int k = 0; k < npass; k++) {
-    ha.cost[k] = io_up[k].cost ? io_up[k].cost : cost + (size_t)k * N * Dp;
-    ha.hfwd[k] = hvol + (size_t)(2 * k) * N * Dp;
-    ha.hbwd[k] = hvol + (size_t)(2 * k + 1) * N * Dp;
+// Pass descriptor of pass k of a pair laid out at `b` in workspace ws.
+fused::PassDesc pass_desc(uint8_t* ws, const FusedPlan& plan, const PairBuffers& b, int k, int W,
+                          int H, int D, int Dshape, const uint8_t* cost_override) {
+  fused::PassDesc d{};
+  d.W = W; d.H = H; d.D = D; d.Dp = fused::padded_d(D);
+  d.J = (W + fused::kTW - 1) / fused::kTW;
+  const int th = fused::band_rows(Dshape);
+  d.nb = (H + th - 1) / th;
+  const PassBuffers& pb = b.pass[k];
+  d.cost = cost_override ? cost_override : ws + pb.cost;
+  d.hfwd = ws + pb.hf;
+  d.hbwd = ws + pb.hb;
+  d.sdown = reinterpret_cast<uint32_t*>(ws + pb.sdown);
+  d.bs = ws + pb.bs;
+  d.flags_down = reinterpret_cast<int*>(ws + pb.flags);
+  d.flags_up = d.flags_down + d.J;
+  d.dint = reinterpret_cast<int16_t*>(ws + pb.dint);
+  d.dsub = nullptr;
+  d.S = nullptr;
+  (void)plan;
+  return d;
+}
+
+// Task tables of a set of passes with one kernel shape: passes sorted by band
+// count (descending); band-major task order.  Written to `tab` (host ints):
+// [band_start (nb+1)] [band_npass (nb)] [prefixJ (npass+1)] [hline block prefix (npass+1)].
+struct TaskTables {
+  std::vector<int> ints;
+  int nbands = 0, ntasks = 0, nblocks = 0, off_band_start = 0, off_band_npass = 0, off_prefixJ = 0,
+      off_hblocks = 0;
+};
+TaskTables build_tables(const fused::PassDesc* d, int npass) {
+  TaskTables t;
+  int nb_max = 0;
+  for (int k = 0; k < npass; k++) nb_max = std::max(nb_max, d[k].nb);
+  t.nbands = nb_max;
+  t.off_band_start = 0;
+  t.off_band_npass = nb_max + 1;
+  t.off_prefixJ = t.off_band_npass + nb_max;
+  t.off_hblocks = t.off_prefixJ + npass + 1;
+  t.ints.assign(t.off_hblocks + npass + 1, 0);
+  int* prefixJ = &t.ints[t.off_prefixJ];
+  for (int k = 0; k < npass; k++) prefixJ[k + 1] = prefixJ[k] + d[k].J;
+  int task = 0;
+  for (int b = 0; b < nb_max; b++) {
+    int active = 0;
+    while (active < npass && d[active].nb > b) active++;
+    t.ints[t.off_band_start + b] = task;
+    t.ints[t.off_band_npass + b] = active;
+    task += prefixJ[active];
   }
-  SF_TRY_CUDA(cudaMemsetAsync(ws + lay.err, 0, sizeof(int), s));
+  t.ints[t.off_band_start + nb_max] = task;
+  t.ntasks = task;
+  int* hb = &t.ints[t.off_hblocks];
+  for (int k = 0; k < npass; k++) hb[k + 1] = hb[k] + 2 * ((d[k].H + 15) / 16);
+  t.nblocks = hb[npass];
+  return t;
+}
+
+// Horizontal paths beside the down sweep, then the up sweep, for passes that
+// share one kernel shape.  Descriptors are passed inline when they fit the
+// parameter block (<= kMaxPass, all alike) and from device memory otherwise.
+sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass, int Dshape,
+                     const fused::PassDesc* d_dev_down, const fused::PassDesc* d_dev_up,
+                     const int* tab_dev, const TaskTables* tt, int* counters, int* err,
+                     cudaStream_t s) {
+  const bool inl = d_dev_down == nullptr;
+  fused::HLineArgs ha{};
+  ha.P1 = p->P1; ha.P2 = p->P2; ha.Dmax = Dshape; ha.npass = npass; ha.path_mask = p->path_mask;
+  ha.err = err;
+  fused::SweepArgs sa{};
+  sa.P1 = p->P1; sa.P2 = p->P2; sa.subpixel = p->subpixel; sa.Dmax = Dshape; sa.npass = npass;
+  sa.path_mask = p->path_mask;
+  sa.en_h0 = (p->path_mask >> 0) & 1u;
+  sa.en_h1 = (p->path_mask >> 1) & 1u;
+  sa.err = err;
+  sa.spin_limit = kSpinLimit;
+  if (inl) {
+    for (int k = 0; k < npass; k++) ha.inl[k] = sa.inl[k] = d[k];
+    ha.uniform_blocks = 2 * ((d[0].H + 15) / 16);
+    ha.nblocks = npass * ha.uniform_blocks;
+    sa.uniform_items = npass * d[0].J;
+    sa.ntasks = d[0].nb * sa.uniform_items;
+    sa.nbands = d[0].nb;
+  } else {
+    ha.pass_ptr = d_dev_down;
+    ha.block_prefix = tab_dev + tt->off_hblocks;
+    ha.nblocks = tt->nblocks;
+    sa.pass_ptr = d_dev_down;
+    sa.band_start = tab_dev + tt->off_band_start;
+    sa.band_npass = tab_dev + tt->off_band_npass;
+    sa.prefixJ = tab_dev + tt->off_prefixJ;
+    sa.nbands = tt->nbands;
+    sa.ntasks = tt->ntasks;
+  }
   // the horizontal paths run beside the down sweep; the up sweep joins them
   std::lock_guard<std::mutex> guard(g_side_mu);
   SideStream* side = nullptr;
@@ -232,78 +359,257 @@ sf_status run_aggregation(int W, int H, const sf_sgm_params* p, int npass, uint8
   SF_TRY_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0));
   SF_TRY_CUDA(fused::launch_hline(ha, side->s));
   SF_TRY_CUDA(cudaEventRecord(side->join, side->s));
-  int* flags = reinterpret_cast<int*>(ws + lay.flags);
-  SF_TRY_CUDA(cudaMemsetAsync(flags, 0, (size_t)2 * (npass * J + 1) * sizeof(int), s));
-  fused::SweepArgs sa{};
-  sa.W = W; sa.H = H; sa.D = p->D; sa.Dp = Dp; sa.P1 = p->P1; sa.P2 = p->P2; sa.J = J;
-  sa.nb = (H + fused::band_rows(p->D) - 1) / fused::band_rows(p->D); sa.items = npass * J; sa.subpixel = p->subpixel;
-  sa.path_mask = p->path_mask;
-  sa.en_h0 = (p->path_mask >> 0) & 1u;
-  sa.en_h1 = (p->path_mask >> 1) & 1u;
-  sa.sdown = reinterpret_cast<uint32_t*>(ws + lay.sdown);
-  sa.bs = ws + lay.bs;
-  sa.err = reinterpret_cast<int*>(ws + lay.err);
-  sa.spin_limit = kSpinLimit;
-  for (int k = 0; k < npass; k++) {
-    sa.io[k].cost = ha.cost[k];
-    sa.io[k].hfwd = ha.hfwd[k];
-    sa.io[k].hbwd = ha.hbwd[k];
-  }
-  sa.flags = flags;
-  sa.task_counter = flags + 2 * npass * J;
+  sa.task_counter = counters;
   SF_TRY_CUDA(fused::launch_sweep(sa, false, s));
-  for (int k = 0; k < npass; k++) {
-    sa.io[k].dint = io_up[k].dint;
-    sa.io[k].dsub = io_up[k].dsub;
-    sa.io[k].S = io_up[k].S;
+  if (inl) {
+    for (int k = 0; k < npass; k++) sa.inl[k] = d[k];   // with outputs of the up sweep
+  } else {
+    sa.pass_ptr = d_dev_up;
   }
-  sa.flags = flags + npass * J;
-  sa.task_counter = flags + 2 * npass * J + 1;
+  sa.task_counter = counters + 1;
   SF_TRY_CUDA(cudaStreamWaitEvent(s, side->join, 0));
   SF_TRY_CUDA(fused::launch_sweep(sa, true, s));
   return SF_OK;
 }
 
-// Fused SGM for `npairs` stereo pairs: census, one distance computation per
-// pair, both reference passes, the left-right check.
+// Census and the shared distance computation of one stereo pair.
+sf_status run_pair_costs(const uint8_t* left, const uint8_t* right, int W, int H, int pitch, int D,
+                         const sf_sgm_params* p, uint8_t* ws, const PairBuffers& b, cudaStream_t s) {
+  const size_t N = (size_t)W * H;
+  (void)N;
+  uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b.census_l);
+  uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b.census_r);
+  SF_TRY_CUDA(launch_census(left, W, H, pitch, p->census_w, p->census_h, cl, s));
+  SF_TRY_CUDA(launch_census(right, W, H, pitch, p->census_w, p->census_h, cr, s));
+  SF_TRY_CUDA(fused::launch_cost_pair(cl, cr, W, H, D, fused::padded_d(D), p->census_w * p->census_h - 1,
+                                      ws + b.pass[0].cost, ws + b.pass[1].cost, s));
+  return SF_OK;
+}
+
+// Fused SGM for `npairs` stereo pairs of one size: census, one distance
+// computation per pair, both reference passes, the left-right check.
 sf_status run_fused_pairs(const uint8_t* const* left, const uint8_t* const* right, int npairs,
                           int W, int H, int pitch, const sf_sgm_params* p, int16_t* const* dL_out,
                           int16_t* const* dR_out, uint8_t* const* valid_out, float* const* disp_out,
                           uint8_t* ws, cudaStream_t s) {
-  FusedLayout lay(W, H, p->D, npairs);
+  FusedPlan plan = single_plan(W, H, p->D, npairs);
   const size_t N = (size_t)W * H;
-  const int Dp = fused::padded_d(p->D), npass = 2 * npairs;
-  const int cmax = p->census_w * p->census_h - 1;
-  uint64_t* census = reinterpret_cast<uint64_t*>(ws + lay.census);
-  uint8_t* cost = ws + lay.cost;
+  SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
   for (int k = 0; k < npairs; k++) {
-    SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, census + (2 * k) * N, s));
-    SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, census + (2 * k + 1) * N, s));
+    sf_status st = run_pair_costs(left[k], right[k], W, H, pitch, p->D, p, ws, plan.pairs[k], s);
+    if (st != SF_OK) return st;
   }
-  for (int k = 0; k < npairs; k++)
-    SF_TRY_CUDA(fused::launch_cost_pair(census + (2 * k) * N, census + (2 * k + 1) * N, W, H, p->D, Dp,
-                                        cmax, cost + (size_t)(2 * k) * N * Dp,
-                                        cost + (size_t)(2 * k + 1) * N * Dp, s));
-  int16_t* dint = reinterpret_cast<int16_t*>(ws + lay.dint);
-  float* dsub = reinterpret_cast<float*>(ws + lay.dsub);
-  fused::PassIO io[fused::kMaxPass] = {};
+  fused::PassDesc d[fused::kMaxPass];
   for (int k = 0; k < npairs; k++) {
-    io[2 * k].dint = (dL_out && dL_out[k]) ? dL_out[k] : dint + (size_t)(2 * k) * N;
-    io[2 * k].dsub = dsub + (size_t)k * N;
-    io[2 * k + 1].dint = (dR_out && dR_out[k]) ? dR_out[k] : dint + (size_t)(2 * k + 1) * N;
+    for (int r = 0; r < 2; r++) {
+      fused::PassDesc& pd = d[2 * k + r];
+      pd = pass_desc(ws, plan, plan.pairs[k], r, W, H, p->D, p->D, nullptr);
+      int16_t* const* user = r == 0 ? dL_out : dR_out;
+      if (user && user[k]) pd.dint = user[k];
+      if (r == 0) pd.dsub = reinterpret_cast<float*>(ws + plan.pairs[k].dsub);
+    }
   }
-  sf_status st = run_aggregation(W, H, p, npass, ws, lay, io, s);
+  sf_status st = run_sweeps(p, d, 2 * npairs, p->D, nullptr, nullptr, nullptr, nullptr,
+                            reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s);
   if (st != SF_OK) return st;
   for (int k = 0; k < npairs; k++) {
-    uint8_t* valid = (valid_out && valid_out[k]) ? valid_out[k] : ws + lay.valid + (size_t)k * N;
-    SF_TRY_CUDA(launch_lr_check(io[2 * k].dint, io[2 * k + 1].dint, io[2 * k].dsub, W, H, p->lr_tol,
-                                valid, disp_out[k], s));
+    uint8_t* valid = (valid_out && valid_out[k]) ? valid_out[k] : ws + plan.pairs[k].valid;
+    SF_TRY_CUDA(launch_lr_check(d[2 * k].dint, d[2 * k + 1].dint, d[2 * k].dsub, W, H, p->lr_tol, valid,
+                                disp_out[k], s));
+  }
+  (void)N;
+  return SF_OK;
+}
+
+std::vector<int> b_shape_keys() {
+  std::vector<int> v;
+  for (int D = 16; D <= SF_MAX_DISPARITY; D += 16) {
+    const fused::Shape sh = fused::shape_for(D);
+    v.push_back(sh.dc * 10000 + sh.chunks * 100 + sh.halo);
+  }
+  return v;
+}
+
+// ---- batches ----------------------------------------------------------------
+// Every item contributes two stereo pairs (t, t+1) = four passes.  Passes are
+// grouped by kernel shape; each group shares one persistent down sweep and one
+// up sweep whose descriptors and task tables live in the workspace.
+struct BatchClass {
+  fused::Shape sh;
+  int Dshape = 0;
+  std::vector<int> pass_ids;   // sorted by band count, descending
+  TaskTables tt;
+  size_t off_down = 0, off_up = 0, off_tab = 0;   // within the tables region
+};
+
+struct BatchSetup {
+  std::vector<PairShape> pairs;
+  std::vector<int> dshape;
+  std::vector<BatchClass> classes;
+  size_t table_bytes = 0;
+  sf_status status = SF_OK;
+};
+
+sf_status check_item(const sf_batch_item& it, const sf_sgm_params* p) {
+  sf_status st = check_size(it.W, it.H);
+  if (st != SF_OK) return st;
+  if (!it.left_t || !it.right_t || !it.left_t1 || !it.right_t1 || !it.flow || !it.s4_out ||
+      !it.valid_out || it.pitch < it.W)
+    return SF_ERR_INVALID_ARG;
+  if (it.D < 1 || it.D > SF_MAX_DISPARITY) return SF_ERR_INVALID_ARG;
+  if (!(it.cam.f > 0.0f) || !(it.cam.B > 0.0f)) return SF_ERR_INVALID_ARG;
+  if (!aligned(it.flow, 8) || !aligned(it.s4_out, 16) || !aligned(it.motion_out, 4) ||
+      !aligned(it.point_out, 4) || !aligned(it.D0_out, 4) || !aligned(it.D1_out, 4))
+    return SF_ERR_INVALID_ARG;
+  sf_sgm_params q = *p;
+  q.D = it.D;
+  if ((st = check_params(&q, it.W, it.H)) != SF_OK) return st;
+  if (fused::cost_pair_smem(it.W, it.D) > 227u * 1024u) return SF_ERR_UNSUPPORTED;
+  return SF_OK;
+}
+
+BatchSetup batch_setup(const sf_batch_item* items, int n, const sf_sgm_params* p) {
+  BatchSetup b;
+  if (!items || n < 1 || !p) {
+    b.status = SF_ERR_INVALID_ARG;
+    return b;
+  }
+  for (int i = 0; i < n; i++) {
+    if ((b.status = check_item(items[i], p)) != SF_OK) return b;
+    for (int f = 0; f < 2; f++) {
+      b.pairs.push_back({items[i].W, items[i].H, items[i].D});
+      b.dshape.push_back(items[i].D);
+    }
+  }
+  const int npass = 2 * (int)b.pairs.size();
+  for (int id = 0; id < npass; id++) {
+    const PairShape& ps = b.pairs[id / 2];
+    const fused::Shape sh = fused::shape_for(ps.D);
+    int c = 0;
+    for (; c < (int)b.classes.size(); c++) {
+      const fused::Shape& o = b.classes[c].sh;
+      if (o.dc == sh.dc && o.chunks == sh.chunks && o.halo == sh.halo) break;
+    }
+    if (c == (int)b.classes.size()) {
+      b.classes.push_back(BatchClass());
+      b.classes[c].sh = sh;
+      b.classes[c].Dshape = ps.D;
+    }
+    b.classes[c].Dshape = std::max(b.classes[c].Dshape, ps.D);
+    b.classes[c].pass_ids.push_back(id);
+  }
+  size_t o = 0;
+  for (BatchClass& c : b.classes) {
+    const int th = c.sh.halo + 1;
+    auto nb_of = [&](int id) { return (b.pairs[id / 2].H + th - 1) / th; };
+    std::stable_sort(c.pass_ids.begin(), c.pass_ids.end(),
+                     [&](int x, int y) { return nb_of(x) > nb_of(y); });
+    std::vector<fused::PassDesc> tmp(c.pass_ids.size());
+    for (size_t k = 0; k < c.pass_ids.size(); k++) {
+      const PairShape& ps = b.pairs[c.pass_ids[k] / 2];
+      tmp[k] = fused::PassDesc{};
+      tmp[k].W = ps.W;
+      tmp[k].H = ps.H;
+      tmp[k].J = (ps.W + fused::kTW - 1) / fused::kTW;
+      tmp[k].nb = nb_of(c.pass_ids[k]);
+    }
+    c.tt = build_tables(tmp.data(), (int)tmp.size());
+    c.off_down = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
+    c.off_up = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
+    c.off_tab = o; o = align_up(o + c.tt.ints.size() * sizeof(int), 256);
+  }
+  b.table_bytes = o;
+  return b;
+}
+
+// Host image of the tables region for a plan placed in workspace ws.
+std::vector<uint8_t> batch_tables(const BatchSetup& b, const FusedPlan& plan, uint8_t* ws,
+                                  const sf_sgm_params* p) {
+  std::vector<uint8_t> blob(b.table_bytes, 0);
+  for (const BatchClass& c : b.classes) {
+    fused::PassDesc* dn = reinterpret_cast<fused::PassDesc*>(blob.data() + c.off_down);
+    fused::PassDesc* up = reinterpret_cast<fused::PassDesc*>(blob.data() + c.off_up);
+    for (size_t k = 0; k < c.pass_ids.size(); k++) {
+      const int id = c.pass_ids[k], pair = id / 2, r = id % 2;
+      const PairShape& ps = b.pairs[pair];
+      dn[k] = pass_desc(ws, plan, plan.pairs[pair], r, ps.W, ps.H, ps.D, ps.D, nullptr);
+      dn[k].dint = nullptr;
+      up[k] = dn[k];
+      up[k].dint = reinterpret_cast<int16_t*>(ws + plan.pairs[pair].pass[r].dint);
+      up[k].dsub = r == 0 ? reinterpret_cast<float*>(ws + plan.pairs[pair].dsub) : nullptr;
+    }
+    memcpy(blob.data() + c.off_tab, c.tt.ints.data(), c.tt.ints.size() * sizeof(int));
+  }
+  (void)p;
+  return blob;
+}
+
+// Everything after the table upload: costs, sweeps, checks, combination.
+sf_status batch_enqueue(const sf_batch_item* items, int n, const sf_sgm_params* p, const BatchSetup& b,
+                        const FusedPlan& plan, uint8_t* ws, cudaStream_t s) {
+  SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
+  for (int i = 0; i < n; i++) {
+    const sf_batch_item& it = items[i];
+    sf_status st = run_pair_costs(it.left_t, it.right_t, it.W, it.H, it.pitch, it.D, p, ws, plan.pairs[2 * i], s);
+    if (st != SF_OK) return st;
+    st = run_pair_costs(it.left_t1, it.right_t1, it.W, it.H, it.pitch, it.D, p, ws, plan.pairs[2 * i + 1], s);
+    if (st != SF_OK) return st;
+  }
+  uint8_t* tab = ws + plan.tables;
+  int* counters = reinterpret_cast<int*>(ws + plan.counters);
+  for (size_t c = 0; c < b.classes.size(); c++) {
+    const BatchClass& bc = b.classes[c];
+    sf_status st = run_sweeps(p, nullptr, (int)bc.pass_ids.size(), bc.Dshape,
+                              reinterpret_cast<const fused::PassDesc*>(tab + bc.off_down),
+                              reinterpret_cast<const fused::PassDesc*>(tab + bc.off_up),
+                              reinterpret_cast<const int*>(tab + bc.off_tab), &bc.tt, counters + 2 * c,
+                              reinterpret_cast<int*>(ws + plan.err), s);
+    if (st != SF_OK) return st;
+  }
+  for (int i = 0; i < n; i++) {
+    const sf_batch_item& it = items[i];
+    float* disp[2];
+    for (int f = 0; f < 2; f++) {
+      const PairBuffers& pb = plan.pairs[2 * i + f];
+      float* user = f == 0 ? it.D0_out : it.D1_out;
+      disp[f] = user ? user : reinterpret_cast<float*>(ws + pb.disp);
+      SF_TRY_CUDA(launch_lr_check(reinterpret_cast<int16_t*>(ws + pb.pass[0].dint),
+                                  reinterpret_cast<int16_t*>(ws + pb.pass[1].dint),
+                                  reinterpret_cast<float*>(ws + pb.dsub), it.W, it.H, p->lr_tol,
+                                  ws + pb.valid, disp[f], s));
+    }
+    SF_TRY_CUDA(launch_combine(disp[0], disp[1], it.flow, it.W, it.H, it.cam.f, it.cam.B, it.cam.cx,
+                               it.cam.cy, it.s4_out, it.motion_out, it.point_out, it.valid_out, s));
   }
   return SF_OK;
 }
 
+struct GraphEntry {
+  std::vector<uint8_t> key;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;
+
+std::vector<uint8_t> batch_key(const sf_batch_item* items, int n, const sf_sgm_params* p, void* ws,
+                               size_t ws_bytes, void* stream) {
+  std::vector<uint8_t> k;
+  auto put = [&](const void* v, size_t nb) {
+    const uint8_t* c = (const uint8_t*)v;
+    k.insert(k.end(), c, c + nb);
+  };
+  put(&n, sizeof(n));
+  put(items, sizeof(sf_batch_item) * (size_t)n);
+  put(p, sizeof(*p));
+  put(&ws, sizeof(ws));
+  put(&ws_bytes, sizeof(ws_bytes));
+  put(&stream, sizeof(stream));
+  for (const auto& pi : b_shape_keys()) put(&pi, sizeof(pi));
+  return k;
+}
+
 size_t workspace_bytes(int W, int H, const sf_sgm_params* p, int npairs) {
-  if (fused_eligible(W, H, p)) return std::max(FusedLayout(W, H, p->D, npairs).total, Workspace(W, H, p->D).total);
+  if (fused_eligible(W, H, p)) return std::max(single_plan(W, H, p->D, npairs).total, Workspace(W, H, p->D).total);
   return Workspace(W, H, p->D).total;
 }
 
@@ -361,7 +667,7 @@ sf_status sf_cost_volume(const uint8_t* ref, const uint8_t* other, int32_t W, in
 size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p) {
   if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
   if (p->D % 16 != 0) return 0;   // staged kernels, no workspace
-  return FusedLayout(W, H, p->D, 1).total;
+  return single_plan(W, H, p->D, 1).total;
 }
 
 sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
@@ -376,12 +682,15 @@ sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_s
   // fused sweeps when the volume is 16-disparity aligned and a workspace of
   // sf_aggregate_workspace_size() bytes is given; staged kernels otherwise
   if (g_use_fused && p->D % 16 == 0 && aligned(cost, 16) && workspace && aligned(workspace, 256) &&
-      ws_bytes >= FusedLayout(W, H, p->D, 1).total) {
-    FusedLayout lay(W, H, p->D, 1);
-    fused::PassIO io[fused::kMaxPass] = {};
-    io[0].cost = cost;
-    io[0].S = agg_out;
-    return run_aggregation(W, H, p, 1, (uint8_t*)workspace, lay, io, s);
+      ws_bytes >= single_plan(W, H, p->D, 1).total) {
+    FusedPlan plan = single_plan(W, H, p->D, 1);
+    uint8_t* ws = (uint8_t*)workspace;
+    SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
+    fused::PassDesc d = pass_desc(ws, plan, plan.pairs[0], 0, W, H, p->D, p->D, cost);
+    d.dint = nullptr;
+    d.S = agg_out;
+    return run_sweeps(p, &d, 1, p->D, nullptr, nullptr, nullptr, nullptr,
+                      reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s);
   }
   SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg_out, s));
   return SF_OK;
@@ -469,9 +778,9 @@ sf_status sf_scene_flow(const uint8_t* left_t, const uint8_t* right_t, const uin
   float* D0;
   float* D1;
   if (fused_eligible(W, H, p)) {
-    FusedLayout fl(W, H, p->D, 2);
-    D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + fl.disp);
-    D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + fl.disp) + (size_t)W * H;
+    FusedPlan fl = single_plan(W, H, p->D, 2);
+    D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + fl.pairs[0].disp);
+    D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + fl.pairs[1].disp);
     const uint8_t* L[2] = {left_t, left_t1};
     const uint8_t* R[2] = {right_t, right_t1};
     float* disp[2] = {D0, D1};
@@ -554,6 +863,79 @@ int32_t sf_trace_disarm(void) {
 
 uint64_t sf_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+size_t sf_batch_workspace_size(const sf_batch_item* items, int32_t n, const sf_sgm_params* p) {
+  BatchSetup b = batch_setup(items, n, p);
+  if (b.status != SF_OK) return 0;
+  std::vector<int> ds = b.dshape;
+  return FusedPlan(b.pairs.data(), (int)b.pairs.size(), ds.data(), 2 * (int)b.classes.size(),
+                   b.table_bytes).total;
+}
+
+sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_params* p, uint32_t flags,
+                       void* workspace, size_t ws_bytes, void* stream) {
+  BatchSetup b = batch_setup(items, n, p);
+  if (b.status != SF_OK) return b.status;
+  if (flags & ~SF_BATCH_GRAPH) return SF_ERR_INVALID_ARG;
+  FusedPlan plan(b.pairs.data(), (int)b.pairs.size(), b.dshape.data(), 2 * (int)b.classes.size(),
+                 b.table_bytes);
+  if (!workspace || ws_bytes < plan.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  uint8_t* ws = (uint8_t*)workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uint8_t> blob = batch_tables(b, plan, ws, p);
+  // descriptor tables travel before the work (pageable source: the copy has
+  // read it when the call returns)
+  SF_TRY_CUDA(cudaMemcpyAsync(ws + plan.tables, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
+  if (!(flags & SF_BATCH_GRAPH)) return batch_enqueue(items, n, p, b, plan, ws, s);
+  if (s == nullptr) return SF_ERR_INVALID_ARG;   // the legacy default stream cannot be captured
+  std::vector<uint8_t> key = batch_key(items, n, p, workspace, ws_bytes, stream);
+  std::lock_guard<std::mutex> guard(g_graph_mu);
+  for (GraphEntry& g : g_graphs) {
+    if (g.key == key) {
+      SF_TRY_CUDA(cudaGraphLaunch(g.exec, s));
+      return SF_OK;
+    }
+  }
+  {
+    SideStream* side = nullptr;   // created outside the capture
+    std::lock_guard<std::mutex> g2(g_side_mu);
+    SF_TRY_CUDA(side_stream(&side));
+  }
+  SF_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  sf_status st = batch_enqueue(items, n, p, b, plan, ws, s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st != SF_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  GraphEntry g;
+  g.key = key;
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return SF_ERR_CUDA;
+  }
+  g_graphs.push_back(g);
+  SF_TRY_CUDA(cudaGraphLaunch(g_graphs.back().exec, s));
+  return SF_OK;
+}
+
+void sf_batch_release_graphs(void) {
+  std::lock_guard<std::mutex> guard(g_graph_mu);
+  for (GraphEntry& g : g_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  g_graphs.clear();
+}
+
+sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo) {
+  return fused::set_shape_override(d_lo, d_hi, dc, halo) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
+}
+
 sf_status sf_set_fused(int32_t enable) {
   if (enable != 0 && enable != 1) return SF_ERR_INVALID_ARG;
   g_use_fused = enable != 0;
@@ -565,7 +947,7 @@ sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const 
   if (!workspace || !p || check_size(W, H) != SF_OK || (npairs != 1 && npairs != 2))
     return SF_ERR_INVALID_ARG;
   if (!fused_eligible(W, H, p)) return SF_OK;
-  FusedLayout lay(W, H, p->D, npairs);
+  FusedPlan lay = single_plan(W, H, p->D, npairs);
   int err = 0;
   cudaStream_t s = (cudaStream_t)stream;
   SF_TRY_CUDA(cudaMemcpyAsync(&err, (const uint8_t*)workspace + lay.err, sizeof(int),

@@ -18,54 +18,61 @@ constexpr int kMaxPass = 4;
 struct Shape {
   int dc, chunks, halo;
 };
-inline Shape shape_for(int D) {
-  Shape s;
-  s.dc = D > 128 ? 16 : 8;
-  s.chunks = 1;
-  while (s.chunks * s.dc < D) s.chunks <<= 1;
-  s.halo = s.dc == 8 ? 16 : 8;
-  return s;
-}
+Shape shape_for(int D);   // built-in rule unless a tuned override covers D
+bool shape_supported(int dc, int chunks, int halo);
+int set_shape_override(int d_lo, int d_hi, int dc, int halo);   // 0 = ok
 inline int padded_d(int D) { return ((D + 15) / 16) * 16; }
 inline int band_rows(int D) { return shape_for(D).halo + 1; }
 
-struct PassIO {
+// One stereo pass (one reference image) of the band sweeps and the
+// horizontal paths: its sizes and buffers.
+struct PassDesc {
+  int W, H, D, Dp, J, nb;
   const uint8_t* cost;   // [H][W][Dp] uint8, this pass's reference image
-  const uint8_t* hfwd;   // [H][W][Dp] uint8, L of path (+1,0)
-  const uint8_t* hbwd;   // [H][W][Dp] uint8, L of path (-1,0)
-  int16_t* dint;         // winner per pixel (UP), or nullptr
-  float* dsub;           // subpixel winner (UP), or nullptr
-  uint16_t* S;           // full aggregated cost [H][W][D] (UP), or nullptr
+  uint8_t* hfwd;         // [H][W][Dp] uint8, L of path (+1,0)
+  uint8_t* hbwd;         // [H][W][Dp] uint8, L of path (-1,0)
+  uint32_t* sdown;       // tile layout [H][J][16][chunks][dc] u32
+  uint8_t* bs;           // band-end states [2][3][W][Dp] u8
+  int* flags_down;       // [J] bands completed by the down sweep
+  int* flags_up;         // [J] bands completed by the up sweep
+  int16_t* dint;         // winner per pixel (up sweep), or nullptr
+  float* dsub;           // subpixel winner (up sweep), or nullptr
+  uint16_t* S;           // full aggregated cost [H][W][D] (up sweep), or nullptr
 };
 
 struct HLineArgs {
-  int W, H, D, Dp, npass, P1, P2;
+  int P1, P2, Dmax, npass, nblocks;
   uint32_t path_mask;
-  int* err;              // set to 1 when a bounded copy wait gives up
-  const uint8_t* cost[kMaxPass];
-  uint8_t* hfwd[kMaxPass];
-  uint8_t* hbwd[kMaxPass];
+  int uniform_blocks;          // > 0: every pass has this many blocks
+  const int* block_prefix;     // otherwise: first block of each pass [npass + 1]
+  int* err;                    // set to 1 when a bounded copy wait gives up
+  PassDesc inl[kMaxPass];      // descriptors in the parameter block (pass_ptr == nullptr)
+  const PassDesc* pass_ptr;    // descriptors in device memory
 };
 
 struct SweepArgs {
-  int W, H, D, Dp, P1, P2, J, nb, items, subpixel;
+  int P1, P2, subpixel, Dmax, npass, ntasks;
   uint32_t path_mask;
   int en_h0, en_h1;
-  uint32_t* sdown;       // tile layout [pass][H][J][16][chunks][dc] u32
-  uint8_t* bs;           // band-end states [pass][2][3][W][Dp] u8
-  int* flags;            // [pass][J] bands completed
-  int* task_counter;     // next task of the queue (zeroed before the launch)
-  int* err;              // set to 1 when a bounded wait gives up
+  int uniform_items;           // > 0: all passes alike, tasks per band
+  const int* band_start;       // otherwise: first task of each band [nbands + 1]
+  const int* band_npass;       // passes (sorted by band count, descending) active in a band
+  const int* prefixJ;          // strip-count prefix over those passes [npass + 1]
+  int nbands;
+  int* task_counter;           // next task of the queue (zeroed before the launch)
+  int* err;                    // set to 1 when a bounded wait gives up
   long long spin_limit;
-  PassIO io[kMaxPass];
+  PassDesc inl[kMaxPass];
+  const PassDesc* pass_ptr;
 };
 
-inline size_t sdown_bytes(int W, int H, int D, int npass) {
+// per-pass buffer sizes (the shape is the launch's, chosen from its largest D)
+inline size_t sdown_bytes(int W, int H, int Dshape) {
   const int J = (W + kTW - 1) / kTW;
-  const Shape s = shape_for(D);
-  return (size_t)npass * H * J * 16 * s.chunks * s.dc * sizeof(uint32_t);
+  const Shape s = shape_for(Dshape);
+  return (size_t)H * J * 16 * s.chunks * s.dc * sizeof(uint32_t);
 }
-inline size_t bs_bytes(int W, int D, int npass) { return (size_t)npass * 2 * 3 * W * padded_d(D); }
+inline size_t bs_bytes(int W, int D) { return (size_t)2 * 3 * W * padded_d(D); }
 inline size_t cost_pair_smem(int W, int D) { return (size_t)W * 16 + (size_t)W * padded_d(D); }
 
 cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,

@@ -28,6 +28,13 @@
 #include "sf_fused.cuh"
 #include "sgm_common.cuh"
 
+// Sweep shapes this build provides: (disparities per thread, chunks, halo).
+#define SF_SWEEP_SHAPES(X)                                                                   \
+  X(8, 1, 16) X(8, 2, 16) X(8, 4, 16) X(8, 8, 16) X(8, 16, 16) X(8, 1, 8) X(8, 2, 8)      \
+  X(8, 4, 8) X(8, 8, 8) X(8, 16, 8) X(16, 4, 8) X(16, 8, 8) X(16, 16, 8) X(16, 4, 16)     \
+  X(16, 8, 16)
+
+
 namespace sf {
 namespace fused {
 
@@ -145,28 +152,33 @@ __device__ __forceinline__ void fence_proxy_async() {
 
 template <int DC, int CHUNKS>
 __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
-    hline_kernel(HLineArgs a) {
+    hline_kernel(const __grid_constant__ HLineArgs a) {
   using V = typename ByteVec<DC>::T;
   extern __shared__ __align__(128) uint8_t hsmem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_fail;
-  const int W = a.W, H = a.H, Dp = a.Dp;
+  // block -> (pass, direction, 16-row block); passes listed by prefix of
+  // their block counts (2 directions x row blocks)
+  int p = 0;
+  {
+    int lo = 0, hi = a.npass - 1;
+    const int blk = blockIdx.x;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      const int start = a.block_prefix ? a.block_prefix[mid] : mid * a.uniform_blocks;
+      if (start <= blk) lo = mid; else hi = mid - 1;
+    }
+    p = lo;
+  }
+  const PassDesc& pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];
+  const int W = pd.W, H = pd.H, Dp = pd.Dp;
   const int nrb = (H + kHlineRows - 1) / kHlineRows;
-  const int blk = blockIdx.x;
-  const int p = blk / (2 * nrb);
-  const int rem = blk - p * 2 * nrb;
+  const int rem = blockIdx.x - (a.block_prefix ? a.block_prefix[p] : p * a.uniform_blocks);
   const int dir = rem / nrb;                 // 0: (+1,0), 1: (-1,0)
   const int rb = rem - dir * nrb;
   if (!((a.path_mask >> dir) & 1u)) return;  // whole CTA: direction disabled
-  const uint8_t* C = a.cost[0];
-  uint8_t* out = dir == 0 ? a.hfwd[0] : a.hbwd[0];
-#pragma unroll
-  for (int k = 1; k < kMaxPass; k++) {       // select without indexing the parameter array
-    if (p == k) {
-      C = a.cost[k];
-      out = dir == 0 ? a.hfwd[k] : a.hbwd[k];
-    }
-  }
+  const uint8_t* C = pd.cost;
+  uint8_t* out = dir == 0 ? pd.hfwd : pd.hbwd;
   const int t = threadIdx.x;
   const int lp = t / CHUNKS;
   const int q = t - lp * CHUNKS;
@@ -176,7 +188,8 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
   const bool row_ok = r0 < nrows;
   const int d0 = q * DC;
   const bool live = d0 < Dp;                 // chunks past the padded depth hold no data
-  const bool pad = d0 + DC > a.D;
+  const int D = pd.D;
+  const bool pad = d0 + DC > D;
   const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
   const int CW = max(1, kHlineTileBytes / (kHlineRows * Dp));   // columns per chunk
   const int nchunks = (W + CW - 1) / CW;
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
       if (pad) {
 #pragma unroll
         for (int i = 0; i < DC; i++)
-          if (d0 + i >= a.D) Cr[i] = kPadCost2;
+          if (d0 + i >= D) Cr[i] = kPadCost2;
       }
       uint32_t left = __shfl_up_sync(0xffffffffu, L[DC - 1], 1, CHUNKS);
       uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, CHUNKS);
@@ -276,6 +289,35 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
 // halo pairs (x1 + h, x1 + HALO/2 + h) carry FR only.  Halo pairs whose
 // columns can no longer reach the strip before the band ends skip the update.
 
+// Task index -> (pass, band in processing order, strip).  Tasks are
+// band-major; with one shape for every pass the split is arithmetic,
+// otherwise passes are sorted by band count (descending) and the tables give
+// each band's first task and the prefix of strip counts.
+__device__ __forceinline__ void decode_task(const SweepArgs& a, int task, int& p, int& bi, int& j) {
+  if (a.uniform_items > 0) {
+    bi = task / a.uniform_items;
+    const int it = task - bi * a.uniform_items;
+    const int J = a.inl[0].J;
+    p = it / J;
+    j = it - p * J;
+    return;
+  }
+  int lo = 0, hi = a.nbands - 1;   // last band whose first task <= task
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.band_start[mid] <= task) lo = mid; else hi = mid - 1;
+  }
+  bi = lo;
+  const int off = task - a.band_start[bi];
+  int plo = 0, phi = a.band_npass[bi] - 1;   // last pass whose strip prefix <= off
+  while (plo < phi) {
+    const int mid = (plo + phi + 1) >> 1;
+    if (a.prefixJ[mid] <= off) plo = mid; else phi = mid - 1;
+  }
+  p = plo;
+  j = off - a.prefixJ[p];
+}
+
 template <int N>
 __device__ __forceinline__ void load_u4(uint32_t* r, const uint4* src, int stride) {
 #pragma unroll
@@ -312,7 +354,7 @@ struct SweepCfg {
 // for the horizontal-path blocks that run beside it.
 template <int DC, int CHUNKS, int HALO, bool UP>
 __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ? 96 : 168)
-    sweep_kernel(SweepArgs a) {
+    sweep_kernel(const __grid_constant__ SweepArgs a) {
   using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
   using V = typename ByteVec<DC>::T;
   constexpr int NP = Cfg::NP, NT = Cfg::NT, NO = Cfg::NO, TH = Cfg::TH, RING = Cfg::RING;
@@ -338,10 +380,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
   const int pr = t / CHUNKS;
   const int q = t - pr * CHUNKS;
   const bool owned = pr < 16;
-  const int W = a.W, H = a.H, Dp = a.Dp, J = a.J;
   const int d0 = q * DC;
-  const bool pad = d0 + DC > a.D;
-  const bool live = d0 < Dp;   // chunks past the padded depth hold no data
   const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
   const bool en_v = (a.path_mask >> (UP ? 3 : 2)) & 1u;
   const bool en_fl = (a.path_mask >> (UP ? 6 : 4)) & 1u;
@@ -377,20 +416,23 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
   // CTA takes the next one, so a slow SM delays nobody but itself.  A task
   // waits (bounded) for the previous band of its own strip and of both
   // neighbour strips; those tasks were handed out earlier to running CTAs.
-  const int ntasks = a.nb * a.items;
+  const int ntasks = a.ntasks;
   for (;;) {
     if (t == 0) s_task = atomicAdd(a.task_counter, 1);
     __syncthreads();
     const int task = s_task;
     if (task >= ntasks) break;
-    const int bi = task / a.items;
-    const int item = task - bi * a.items;
-    const int band = UP ? (a.nb - 1 - bi) : bi;
+    int p, bi, j;
+    decode_task(a, task, p, bi, j);
+    const PassDesc pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];   // by value: fields in registers
+    const int W = pd.W, H = pd.H, Dp = pd.Dp, J = pd.J, D = pd.D;
+    const bool pad = d0 + DC > D;
+    const bool live = d0 < Dp;   // chunks past the padded depth hold no data
+    const int band = UP ? (pd.nb - 1 - bi) : bi;
     const int ytop = band * TH;
     const int nrows = min(TH, H - ytop);
-    const int p = item / J;
-    const int j = item - p * J;
     const int x0 = j * kTW;
+    int* const flags = UP ? pd.flags_up : pd.flags_down;
     // ---- columns of this thread's pair ----
     int xlo, xhi;
     if (role == 0) {
@@ -404,28 +446,27 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       xhi = x0 + kTW + HH + hh;
     }
     const bool lo_in = live && xlo >= 0 && xlo < W, hi_in = live && xhi >= 0 && xhi < W;
-    const PassIO& io = a.io[p];
     // ---- prefetch ring: the first rows' inputs are requested before the
     // neighbour wait (they do not depend on it) ----
     auto issue_row = [&](int r) {
       const bool ok = r < nrows;
       const int yy = UP ? ytop + nrows - 1 - r : ytop + r;
       V* cs = ringc + (r % RING) * 2 * NT + t;
-      const uint8_t* rowc = io.cost + (size_t)yy * W * Dp + d0;
-      cp_async<DC>(cs, ok && lo_in ? rowc + (size_t)xlo * Dp : io.cost, ok && lo_in);
-      cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : io.cost, ok && hi_in);
+      const uint8_t* rowc = pd.cost + (size_t)yy * W * Dp + d0;
+      cp_async<DC>(cs, ok && lo_in ? rowc + (size_t)xlo * Dp : pd.cost, ok && lo_in);
+      cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : pd.cost, ok && hi_in);
       if (UP && owned) {
         uint4* xs = ringx + (r % RING) * XW * NO + t;
-        const size_t tile = ((((size_t)p * H + (ok ? yy : 0)) * J + j) * 16 + pr) * CHUNKS + q;
-        const uint4* sd = reinterpret_cast<const uint4*>(a.sdown) + tile * G;
+        const size_t tile = ((((size_t)(ok ? yy : 0)) * J + j) * 16 + pr) * CHUNKS + q;
+        const uint4* sd = reinterpret_cast<const uint4*>(pd.sdown) + tile * G;
 #pragma unroll
         for (int w = 0; w < G; w++) cp_async<16>(xs + w * NO, sd + w, ok);
         const size_t ol = ((size_t)yy * W + xlo) * Dp + d0, oh = ((size_t)yy * W + xhi) * Dp + d0;
         const bool fl = ok && lo_in, fh = ok && hi_in;
-        cp_async<DC>(xs + (G + 0) * NO, fl && a.en_h0 ? io.hfwd + ol : io.hfwd, fl && a.en_h0);
-        cp_async<DC>(xs + (G + 1) * NO, fh && a.en_h0 ? io.hfwd + oh : io.hfwd, fh && a.en_h0);
-        cp_async<DC>(xs + (G + 2) * NO, fl && a.en_h1 ? io.hbwd + ol : io.hbwd, fl && a.en_h1);
-        cp_async<DC>(xs + (G + 3) * NO, fh && a.en_h1 ? io.hbwd + oh : io.hbwd, fh && a.en_h1);
+        cp_async<DC>(xs + (G + 0) * NO, fl && a.en_h0 ? pd.hfwd + ol : pd.hfwd, fl && a.en_h0);
+        cp_async<DC>(xs + (G + 1) * NO, fh && a.en_h0 ? pd.hfwd + oh : pd.hfwd, fh && a.en_h0);
+        cp_async<DC>(xs + (G + 2) * NO, fl && a.en_h1 ? pd.hbwd + ol : pd.hbwd, fl && a.en_h1);
+        cp_async<DC>(xs + (G + 3) * NO, fh && a.en_h1 ? pd.hbwd + oh : pd.hbwd, fh && a.en_h1);
       }
       cp_async_commit();
     };
@@ -434,7 +475,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     // ---- wait for the previous band of this strip and its neighbours ----
     if (t == 0 && bi > 0) {
       long long spins = 0;
-      const int* fl = a.flags + p * J;
+      const int* fl = flags;
       for (int n = j - 1; n <= j + 1; n++) {
         if (n < 0 || n >= J) continue;
         while (ld_acquire(fl + n) < bi) {
@@ -457,10 +498,10 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     // lanes whose predecessor column lies outside the image start a path
     const uint32_t fl_keep = ((xlo - 1 >= 0) ? 0x0000ffffu : 0u) | ((xhi - 1 >= 0) ? 0xffff0000u : 0u);
     const uint32_t fr_keep = ((xlo + 1 < W) ? 0x0000ffffu : 0u) | ((xhi + 1 < W) ? 0xffff0000u : 0u);
-    const uint8_t* bsv = a.bs + ((size_t)(p * 2 + ((bi + 1) & 1)) * 3 + 0) * W * Dp;
+    const uint8_t* bsv = pd.bs + ((size_t)(((bi + 1) & 1)) * 3 + 0) * W * Dp;
     const uint8_t* bsl = bsv + (size_t)W * Dp;
     const uint8_t* bsr = bsl + (size_t)W * Dp;
-    uint8_t* wsv = a.bs + ((size_t)(p * 2 + (bi & 1)) * 3 + 0) * W * Dp;
+    uint8_t* wsv = pd.bs + ((size_t)((bi & 1)) * 3 + 0) * W * Dp;
     uint8_t* wsl = wsv + (size_t)W * Dp;
     uint8_t* wsr = wsl + (size_t)W * Dp;
 
@@ -479,7 +520,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         if (pad) {
 #pragma unroll
           for (int i = 0; i < DC; i++)
-            if (d0 + i >= a.D) r[i] = (have ? kPadCost2 : 0u) & keep;
+            if (d0 + i >= D) r[i] = (have ? kPadCost2 : 0u) & keep;
         }
       };
       if (owned) {
@@ -513,10 +554,11 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     // winner-take-all + parabolic subpixel of row kk, done by halo threads
     // from the aggregated costs the owned threads left in shared memory
     auto select_row = [&](int kk) {
-      if (!HALO_SELECT || owned || !io.dint) return;
+      if (!HALO_SELECT || owned || !pd.dint) return;
       const int yk = UP ? ytop + nrows - 1 - kk : ytop + kk;
       const int ht = t - NO;
-      const int c = ht / SEL_T, sub = ht - c * SEL_T;
+      constexpr int ST = SEL_T > 0 ? SEL_T : 1;
+      const int c = ht / ST, sub = ht - c * ST;
       const int cpr = c & 15, cl = c >> 4;
       const int x = x0 + c;
       const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow + (kk & 1) * G * NO);
@@ -537,7 +579,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
           for (int e = 0; e < 4; e++) {
             const int d = qq * DC + 4 * w + e;
             const uint32_t sv = (vv[e] >> (16 * cl)) & 0xffffu;
-            if (d < a.D) key = min(key, sv * 256u + (uint32_t)d);
+            if (d < D) key = min(key, sv * 256u + (uint32_t)d);
           }
         }
       }
@@ -547,13 +589,13 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         const int ds = (int)(key & 255u);
         const int sv = (int)(key >> 8);
         float v = (float)ds;
-        if (a.subpixel && ds > 0 && ds < a.D - 1) {
+        if (a.subpixel && ds > 0 && ds < D - 1) {
           const int am = (int)s_at(ds - 1) - sv;
           const int bp = (int)s_at(ds + 1) - sv;
           v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
         }
-        io.dint[(size_t)yk * W + x] = (int16_t)ds;
-        if (io.dsub) io.dsub[(size_t)yk * W + x] = v;
+        pd.dint[(size_t)yk * W + x] = (int16_t)ds;
+        if (pd.dsub) pd.dsub[(size_t)yk * W + x] = v;
       }
     };
 
@@ -568,7 +610,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       if (pad) {
 #pragma unroll
         for (int i = 0; i < DC; i++)
-          if (d0 + i >= a.D) Cc[i] = kPadCost2;
+          if (d0 + i >= D) Cc[i] = kPadCost2;
       }
       const int par = k & 1;
       const bool fresh = (bi == 0 && k == 0);
@@ -632,8 +674,8 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         for (int i = 0; i < DC; i++)
           S[i] = (en_v ? Nv[i] : 0u) + (en_fl ? Nf[i] : 0u) + (en_fr ? Nr[i] : 0u);
         if (!UP) {
-          const size_t tile = ((((size_t)p * H + y) * J + j) * 16 + pr) * CHUNKS + q;
-          store_u4<DC>(reinterpret_cast<uint4*>(a.sdown) + tile * G, 1, S);
+          const size_t tile = ((((size_t)y) * J + j) * 16 + pr) * CHUNKS + q;
+          store_u4<DC>(reinterpret_cast<uint4*>(pd.sdown) + tile * G, 1, S);
         } else {
           // add the down sweep and the horizontal paths
           uint32_t sdv[DC], hf[DC], hb[DC];
@@ -648,22 +690,22 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
           if (pad) {
 #pragma unroll
             for (int i = 0; i < DC; i++)
-              if (d0 + i >= a.D) S[i] = 0xffffffffu;
+              if (d0 + i >= D) S[i] = 0xffffffffu;
           }
-          if (io.S) {
+          if (pd.S) {
             // full aggregated cost, [H][W][D] uint16
 #pragma unroll
             for (int i = 0; i < DC; i++) {
-              if (d0 + i < a.D) {
-                if (lo_in) io.S[((size_t)y * W + xlo) * a.D + d0 + i] = (uint16_t)(S[i] & 0xffffu);
-                if (hi_in) io.S[((size_t)y * W + xhi) * a.D + d0 + i] = (uint16_t)(S[i] >> 16);
+              if (d0 + i < D) {
+                if (lo_in) pd.S[((size_t)y * W + xlo) * D + d0 + i] = (uint16_t)(S[i] & 0xffffu);
+                if (hi_in) pd.S[((size_t)y * W + xhi) * D + d0 + i] = (uint16_t)(S[i] >> 16);
               }
             }
           }
-          if (io.dint && HALO_SELECT) {
+          if (pd.dint && HALO_SELECT) {
             // the halo warps select the winners of this row after the barrier
             store_u4<DC>(srow + (k & 1) * G * NO + t, NO, S);
-          } else if (io.dint) {
+          } else if (pd.dint) {
             // winner-take-all: the smallest d with the minimal S, per lane
             const uint32_t gmin = group_min2<CHUNKS>(tree_min<DC>(S), own_mask);
             uint32_t first = 0xffffffffu;
@@ -692,14 +734,14 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
                 return (sw[((ii >> 2) * NO + pr * CHUNKS + qq) * 4 + (ii & 3)] >> sh) & 0xffffu;
               };
               float v = (float)ds;
-              if (a.subpixel && ds > 0 && ds < a.D - 1) {
+              if (a.subpixel && ds > 0 && ds < D - 1) {
                 const int sv = (int)s_at(ds);
                 const int am = (int)s_at(ds - 1) - sv;
                 const int bp = (int)s_at(ds + 1) - sv;
                 v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
               }
-              io.dint[(size_t)y * W + x] = (int16_t)ds;
-              if (io.dsub) io.dsub[(size_t)y * W + x] = v;
+              pd.dint[(size_t)y * W + x] = (int16_t)ds;
+              if (pd.dsub) pd.dsub[(size_t)y * W + x] = v;
             }
             __syncwarp(own_mask);
           }
@@ -770,7 +812,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     // and prefetch ring are free for the next task afterwards ----
     cp_async_wait<0>();
     __syncthreads();
-    if (t == 0) st_release(a.flags + p * J + j, bi + 1);
+    if (t == 0) st_release(flags + j, bi + 1);
     select_row(nrows - 1);   // the last row of the band (its costs are in place)
   }
 }
@@ -791,20 +833,26 @@ cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int 
 
 template <int DC, int CHUNKS>
 static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
-  const int nrb = (a.H + kHlineRows - 1) / kHlineRows;
   const size_t smem = 2 * (size_t)kHlineTileBytes;
   cudaError_t e = cudaFuncSetAttribute(hline_kernel<DC, CHUNKS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  hline_kernel<DC, CHUNKS><<<a.npass * 2 * nrb, kHlinePairs * CHUNKS, smem, s>>>(a);
+  if (a.nblocks <= 0) return cudaSuccess;
+  hline_kernel<DC, CHUNKS><<<a.nblocks, kHlinePairs * CHUNKS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   count_launches(1);
-  const Shape sh = shape_for(a.D);
-  if (sh.dc == 16) return sh.chunks <= 8 ? hline_dispatch<16, 8>(a, s) : hline_dispatch<16, 16>(a, s);
+  const Shape sh = shape_for(a.Dmax);
+  if (sh.dc == 16) {
+    switch (sh.chunks) {
+      case 4: return hline_dispatch<16, 4>(a, s);
+      case 8: return hline_dispatch<16, 8>(a, s);
+      default: return hline_dispatch<16, 16>(a, s);
+    }
+  }
   switch (sh.chunks) {
     case 1: return hline_dispatch<8, 1>(a, s);
     case 2: return hline_dispatch<8, 2>(a, s);
@@ -812,6 +860,65 @@ cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
     case 8: return hline_dispatch<8, 8>(a, s);
     default: return hline_dispatch<8, 16>(a, s);
   }
+}
+
+// ---- kernel shape choice (built-in rule, or a tuned override per D class) ----
+namespace {
+struct ShapeOverride {
+  int lo, hi, dc, halo;
+};
+ShapeOverride g_over[16];
+int g_nover = 0;
+}  // namespace
+
+static Shape builtin_shape(int D) {
+  Shape s;
+  s.dc = D > 128 ? 16 : 8;
+  s.chunks = 1;
+  while (s.chunks * s.dc < D) s.chunks <<= 1;
+  s.halo = s.dc == 8 ? 16 : 8;
+  return s;
+}
+
+bool shape_supported(int dc, int chunks, int halo) {
+#define SF_SUP(DC_, CH_, HA_) \
+  if (dc == DC_ && chunks == CH_ && halo == HA_) return true;
+  SF_SWEEP_SHAPES(SF_SUP)
+#undef SF_SUP
+  return false;
+}
+
+Shape shape_for(int D) {
+  for (int i = g_nover - 1; i >= 0; i--) {
+    if (D >= g_over[i].lo && D <= g_over[i].hi) {
+      Shape s;
+      s.dc = g_over[i].dc;
+      s.halo = g_over[i].halo;
+      s.chunks = 1;
+      while (s.chunks * s.dc < D) s.chunks <<= 1;
+      return s;
+    }
+  }
+  return builtin_shape(D);
+}
+
+int set_shape_override(int d_lo, int d_hi, int dc, int halo) {
+  if (d_lo < 1 || d_hi > SF_MAX_DISPARITY || d_lo > d_hi) return 1;
+  if (dc == 0) {   // drop overrides of this class
+    int w = 0;
+    for (int i = 0; i < g_nover; i++)
+      if (!(g_over[i].lo == d_lo && g_over[i].hi == d_hi)) g_over[w++] = g_over[i];
+    g_nover = w;
+    return 0;
+  }
+  for (int D = d_lo; D <= d_hi; D++) {
+    int chunks = 1;
+    while (chunks * dc < D) chunks <<= 1;
+    if (!shape_supported(dc, chunks, halo)) return 1;
+  }
+  if (g_nover == 16) return 1;
+  g_over[g_nover++] = {d_lo, d_hi, dc, halo};
+  return 0;
 }
 
 template <int DC, int CHUNKS, int HALO, bool UP>
@@ -829,22 +936,19 @@ static cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   // one wave of CTAs; tasks come from a queue, and a task is only waited on
   // after a running CTA has taken it, so no co-residency guarantee is needed
-  const int grid = std::max(1, std::min(a.items * a.nb, per_sm * sms));
+  const int grid = std::max(1, std::min(a.ntasks, per_sm * sms));
   kern<<<grid, Cfg::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <bool UP>
 static cudaError_t sweep_select(const SweepArgs& a, cudaStream_t s) {
-  const Shape sh = shape_for(a.D);
-  if (sh.dc == 16) return sweep_dispatch<16, 16, 8, UP>(a, s);   // 128 < D <= 256
-  switch (sh.chunks) {
-    case 1: return sweep_dispatch<8, 1, 16, UP>(a, s);
-    case 2: return sweep_dispatch<8, 2, 16, UP>(a, s);
-    case 4: return sweep_dispatch<8, 4, 16, UP>(a, s);
-    case 8: return sweep_dispatch<8, 8, 16, UP>(a, s);
-    default: return sweep_dispatch<8, 16, 16, UP>(a, s);
-  }
+  const Shape sh = shape_for(a.Dmax);
+#define SF_CASE(DC_, CH_, HA_) \
+  if (sh.dc == DC_ && sh.chunks == CH_ && sh.halo == HA_) return sweep_dispatch<DC_, CH_, HA_, UP>(a, s);
+  SF_SWEEP_SHAPES(SF_CASE)
+#undef SF_CASE
+  return cudaErrorInvalidConfiguration;
 }
 
 cudaError_t launch_sweep(const SweepArgs& a, bool up, cudaStream_t s) {

@@ -1,0 +1,129 @@
+"""Batched quadruples of uneven size and disparity range (one persistent sweep
+launch per kernel shape, optional CUDA-graph replay): every output bit-equal
+to per-instance sf_scene_flow runs, and one small item checked against the
+oracle; tuned sweep shapes give identical results."""
+import numpy as np
+import pytest
+
+from gpu_helpers import SUBPIXEL_ATOL, assert_nan_equal_close, to_dev, to_np
+from paper_1801_04720_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04720_gb300 import _lib, build
+    build.build()
+    _lib.load()
+    return _lib
+
+
+def _scene(sf, q):
+    return {"left_t": to_dev(q.left_t), "right_t": to_dev(q.right_t), "left_t1": to_dev(q.left_t1),
+            "right_t1": to_dev(q.right_t1), "flow": to_dev(q.flow), "D": q.D,
+            "cam": sf.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)}
+
+
+SMALL = [(96, 64, 16), (130, 41, 48), (67, 53, 32), (200, 60, 64), (97, 40, 100), (130, 41, 128),
+         (64, 48, 16), (160, 50, 192)]
+
+
+def _quads(specs, seed0=0):
+    out = []
+    for k, (W, H, D) in enumerate(specs):
+        disp = (2, max(3, D // 3), max(4, D - 5))
+        out.append(synth.fronto_planes(W=W, H=H, D=D, disparities=disp, seed=seed0 + k))
+    return out
+
+
+def _compare(sf, quads, graph, repeats=1):
+    import torch
+    p = sf.params()
+    scenes = [_scene(sf, q) for q in quads]
+    outs = [sf.alloc_scene_flow_outputs(q.shape[1], q.shape[0], "cuda") for q in quads]
+    items = sf.make_batch(scenes, outs)
+    ws = torch.empty(sf.sf_batch_workspace_size(items, p), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream() if graph else torch.cuda.current_stream()
+    for _ in range(repeats):
+        for o in outs:
+            for v in o.values():
+                if v is not None:
+                    v.fill_(0)
+        torch.cuda.synchronize()
+        sf.sf_batch_run(items, p, ws, graph=graph, stream=stream)
+        torch.cuda.synchronize()
+        for q, sc, o in zip(quads, scenes, outs):
+            H, W = q.shape
+            pq = sf.params(D=q.D)
+            ref = sf.sf_scene_flow([sc["left_t"], sc["right_t"], sc["left_t1"], sc["right_t1"]],
+                                   sc["flow"], pq, sc["cam"])
+            for k in ("s4", "motion", "point", "valid", "D0", "D1"):
+                a, b = to_np(o[k]), to_np(ref[k])
+                assert np.array_equal(np.nan_to_num(a, nan=-9.0), np.nan_to_num(b, nan=-9.0)), (q.D, k)
+    return outs
+
+
+def test_batch_equals_per_instance(sf):
+    _compare(sf, _quads(SMALL), graph=False)
+
+
+def test_batch_graph_replay_equals_per_instance(sf):
+    _compare(sf, _quads(SMALL, seed0=20), graph=True, repeats=3)
+    sf.sf_batch_release_graphs()
+
+
+def test_batch_small_item_against_oracle(sf, oracle_mod):
+    quads = _quads([(64, 48, 16), (96, 64, 32)], seed0=7)
+    outs = _compare(sf, quads, graph=False)
+    q, o = quads[0], outs[0]
+    r0 = oracle_mod.disparity(q.left_t, q.right_t, D=q.D)
+    assert_nan_equal_close(to_np(o["D0"]), r0["disp"], SUBPIXEL_ATOL, "D0")
+
+
+def test_batch_graph_needs_a_created_stream(sf):
+    import torch
+    quads = _quads([(64, 48, 16)])
+    p = sf.params()
+    sc = [_scene(sf, q) for q in quads]
+    o = [sf.alloc_scene_flow_outputs(64, 48, "cuda")]
+    items = sf.make_batch(sc, o)
+    ws = torch.empty(sf.sf_batch_workspace_size(items, p), dtype=torch.uint8, device="cuda")
+    null = type("S", (), {"cuda_stream": 0})()
+    with pytest.raises(sf.SFError):
+        sf.sf_batch_run(items, p, ws, graph=True, stream=null)
+
+
+def test_batch_rejects_bad_items(sf):
+    import ctypes
+    import torch
+    q = _quads([(64, 48, 16)])[0]
+    sc = _scene(sf, q)
+    o = sf.alloc_scene_flow_outputs(64, 48, "cuda")
+    items = sf.make_batch([sc], [o])
+    items[0].D = 0
+    assert sf.sf_batch_workspace_size(items, sf.params()) == 0
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sf.SFError):
+        sf.sf_batch_run(items, sf.params(), ws)
+
+
+@pytest.mark.parametrize("dc,halo", [(8, 8), (16, 8), (16, 16), (8, 16)])
+def test_tuned_shapes_are_bit_identical(sf, dc, halo):
+    quads = _quads([(130, 41, 64), (97, 40, 128)], seed0=40)
+    base = [_scene(sf, q) for q in quads]
+    ref = [sf.sf_scene_flow([s["left_t"], s["right_t"], s["left_t1"], s["right_t1"]], s["flow"],
+                            sf.params(D=q.D), s["cam"]) for s, q in zip(base, quads)]
+    sf.sf_set_sweep_shape(33, 128, dc, halo)     # every provided shape covers this class
+    try:
+        got = [sf.sf_scene_flow([s["left_t"], s["right_t"], s["left_t1"], s["right_t1"]], s["flow"],
+                                sf.params(D=q.D), s["cam"]) for s, q in zip(base, quads)]
+    finally:
+        sf.sf_set_sweep_shape(33, 128, 0, 0)
+    for a, b in zip(got, ref):
+        for k in ("valid", "D0", "D1", "s4"):
+            x, y = to_np(a[k]), to_np(b[k])
+            assert np.array_equal(np.nan_to_num(x, nan=-9.0), np.nan_to_num(y, nan=-9.0)), k
