@@ -31,12 +31,18 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in sweep shape instead of the tuned one")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="quadruples in the uneven-batch measurement (0 = skip)")
     ap.add_argument("--profile", action="store_true",
                     help="short run for ncu: no clock-sampling load phase, no e2e, no CPU baseline")
     args = ap.parse_args()
     if args.profile:
         args.no_e2e = True
         args.no_cpu_baseline = True
+        args.batch = 0
+        args.no_autotune = True
     return args
 
 
@@ -140,6 +146,10 @@ def run_ours(args, world, rank, local):
     build.build()
     _lib.load()
     dev = torch.device("cuda", local)
+    tuned = None
+    if not args.no_autotune:
+        from paper_1801_04720_gb300 import autotune
+        tuned = autotune.load_or_tune(W=W_IMG, H=H_IMG, classes=[(65, 128)])
     q = synth.automotive(seed=args.seed + rank)
     H, W = q.shape
     N = W * H
@@ -253,8 +263,54 @@ def run_ours(args, world, rank, local):
                      "avg_launch_ms": round(dom_ms, 5)},
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_tot.items()},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+        "sweep_shape": tuned["classes"] if tuned else "built-in",
     }
+    if args.batch > 0:
+        result["batch"] = run_batch(args, dev, _lib, synth, torch)
     return result, q
+
+
+def run_batch(args, dev, _lib, synth, torch):
+    """Uneven batch: quadruples with sizes drawn from {320x240, 640x480,
+    1024x320, 1242x375} and D from {64, 128, 192} (fronto-parallel plane
+    recipe), all in one sf_batch_run per step, replayed as a CUDA graph."""
+    quads = [synth.batch_recipe(seed=k) for k in range(args.batch)]
+    scenes, outs = [], []
+    for q in quads:
+        scenes.append({"left_t": torch.from_numpy(q.left_t).to(dev),
+                       "right_t": torch.from_numpy(q.right_t).to(dev),
+                       "left_t1": torch.from_numpy(q.left_t1).to(dev),
+                       "right_t1": torch.from_numpy(q.right_t1).to(dev),
+                       "flow": torch.from_numpy(q.flow).to(dev), "D": q.D,
+                       "cam": _lib.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)})
+        outs.append(_lib.alloc_scene_flow_outputs(q.shape[1], q.shape[0], dev))
+    items = _lib.make_batch(scenes, outs)
+    p = _lib.params()
+    ws = torch.empty(_lib.sf_batch_workspace_size(items, p), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(max(2, args.warmup)):
+        _lib.sf_batch_run(items, p, ws, graph=True, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 10))
+    ms = []
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _lib.sf_batch_run(items, p, ws, graph=True, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    _lib.sf_batch_release_graphs()
+    mean = statistics.mean(ms)
+    pixels = sum(q.shape[0] * q.shape[1] for q in quads)
+    return {"metric": "scene-flow quadruples/s, uneven batch", "value": round(len(quads) * 1000.0 / mean, 2),
+            "unit": "quadruples/s", "items": len(quads), "ms_per_step": round(mean, 3),
+            "megapixels_per_step": round(pixels / 1e6, 3),
+            "workspace_gb": round(ws.numel() / 1e9, 2), "graph": True,
+            "sizes": sorted({f"{q.shape[1]}x{q.shape[0]}/D{q.D}" for q in quads})}
 
 
 def cpu_baseline(q):

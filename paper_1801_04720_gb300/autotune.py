@@ -1,0 +1,99 @@
+"""Autotuner for the band-sweep kernel shape.
+
+For each class of disparity counts it times every sweep shape the library
+provides (disparities per thread dc, halo width) on a synthetic quadruple of
+the requested size through sf_scene_flow, keeps the fastest, and stores the
+choice in a JSON cache keyed by GPU name and size.  ``apply`` installs a cached
+choice with sf_set_sweep_shape.  Every shape computes identical integers; only
+the speed differs."""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+import numpy as np
+import torch
+
+from . import _lib, synth
+
+CANDIDATES = [(8, 16), (8, 8), (16, 8), (16, 16)]
+DEFAULT_CLASSES = [(1, 32), (33, 64), (65, 128), (129, 256)]
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
+
+
+def _time_scene_flow(q, D, steps, warmup):
+    dev = torch.device("cuda")
+    imgs = [torch.from_numpy(np.ascontiguousarray(im)).to(dev) for im in q.images()]
+    flow = torch.from_numpy(q.flow).to(dev)
+    p = _lib.params(D=D)
+    cam = _lib.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
+    ws = _lib.workspace(q.shape[1], q.shape[0], p, dev)
+    out = _lib.alloc_scene_flow_outputs(q.shape[1], q.shape[0], dev)
+    for _ in range(warmup):
+        _lib.sf_scene_flow(imgs, flow, p, cam, ws=ws, out=out)
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _lib.sf_scene_flow(imgs, flow, p, cam, ws=ws, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def tune(W=1242, H=375, classes=DEFAULT_CLASSES, steps=5, warmup=2, cache=CACHE, seed=0):
+    """Times every candidate shape per class; returns and stores the choice."""
+    _lib.load()
+    result = {"gpu": torch.cuda.get_device_name(), "W": W, "H": H, "classes": []}
+    for lo, hi in classes:
+        D = hi
+        q = synth.fronto_planes(W=W, H=H, D=D, disparities=(2, max(3, D // 3), max(4, D - 5)),
+                                seed=seed)
+        timings = {}
+        for dc, halo in CANDIDATES:
+            try:
+                _lib.sf_set_sweep_shape(lo, hi, dc, halo)
+            except _lib.SFError:
+                continue
+            try:
+                timings[f"{dc}x{halo}"] = _time_scene_flow(q, D, steps, warmup)
+            finally:
+                _lib.sf_set_sweep_shape(lo, hi, 0, 0)
+        if not timings:
+            continue
+        best = min(timings, key=timings.get)
+        dc, halo = (int(v) for v in best.split("x"))
+        result["classes"].append({"lo": lo, "hi": hi, "dc": dc, "halo": halo,
+                                  "ms": round(timings[best], 4),
+                                  "candidates_ms": {k: round(v, 4) for k, v in timings.items()}})
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        with open(cache, "w") as f:
+            json.dump(result, f, indent=1)
+    return result
+
+
+def apply(result):
+    """Installs the shapes of a tune() result; returns how many were set."""
+    n = 0
+    for c in result.get("classes", []):
+        _lib.sf_set_sweep_shape(c["lo"], c["hi"], c["dc"], c["halo"])
+        n += 1
+    return n
+
+
+def load_or_tune(W=1242, H=375, cache=CACHE, **kw):
+    """Uses the cached choice for this GPU and size, tuning when there is none."""
+    try:
+        with open(cache) as f:
+            res = json.load(f)
+        if res.get("gpu") == torch.cuda.get_device_name() and res.get("W") == W and res.get("H") == H:
+            apply(res)
+            return res
+    except (OSError, ValueError):
+        pass
+    res = tune(W=W, H=H, cache=cache, **kw)
+    apply(res)
+    return res
