@@ -278,8 +278,8 @@ uint64_t sf_kernel_launches(void);
 /* Process-wide choice between the fused stereo kernels (1, default) and the
  * staged kernels (0: stored cost volume, one kernel per path, separate
  * selection).  Both compute the same integers; the staged kernels also serve
- * requests the fused ones do not take (a row of W*D distances beyond one
- * CTA's shared memory, D not a multiple of 16 in sf_sgm_aggregate). */
+ * the request the fused ones do not take (D not a multiple of 16 in
+ * sf_sgm_aggregate). */
 sf_status sf_set_fused(int32_t enable);
 
 /* Reads the device-side error word of a workspace used by sf_sgm_full

@@ -154,8 +154,9 @@ bool g_use_fused = true;
 // shared memory.
 bool fused_eligible(int W, int H, const sf_sgm_params* p) {
   (void)H;
-  if (!g_use_fused) return false;
-  return fused::cost_pair_smem(W, p->D) <= 227u * 1024u;
+  (void)W;
+  (void)p;
+  return g_use_fused;
 }
 
 // ---- fused-path workspace --------------------------------------------------
@@ -464,7 +465,6 @@ sf_status check_item(const sf_batch_item& it, const sf_sgm_params* p) {
   sf_sgm_params q = *p;
   q.D = it.D;
   if ((st = check_params(&q, it.W, it.H)) != SF_OK) return st;
-  if (fused::cost_pair_smem(it.W, it.D) > 227u * 1024u) return SF_ERR_UNSUPPORTED;
   return SF_OK;
 }
 

@@ -74,6 +74,8 @@ inline size_t sdown_bytes(int W, int H, int Dshape) {
 }
 inline size_t bs_bytes(int W, int D) { return (size_t)2 * 3 * W * padded_d(D); }
 inline size_t cost_pair_smem(int W, int D) { return (size_t)W * 16 + (size_t)W * padded_d(D); }
+// rows whose census pair + distances exceed this use per-reference x-tiles
+constexpr size_t kCostPairSmemMax = 227u * 1024u;
 
 cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
                              int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s);

@@ -8,6 +8,8 @@
 //      C_L[y][x][d] = H(cL(x), cR(x-d)) and the right-reference volume
 //      C_R[y][x][d] = H(cR(x), cL(x+d)).  POPC runs at a quarter of the
 //      integer rate, so sharing the distances between both passes halves it.
+//      Rows whose W x (Dp + 16) bytes exceed one CTA's shared memory take
+//      cost_tiled_kernel instead: one launch per reference image, x-tiles.
 //   2. hline_kernel: the two horizontal paths (+1,0) and (-1,0), each row an
 //      independent line; two rows share a register (u16x2 lanes).  Writes
 //      L_r as uint8 volumes.  Runs beside the down sweep.
@@ -103,6 +105,43 @@ __global__ void __launch_bounds__(512)
       }
       dst[i] = packed;
     }
+  }
+}
+
+// Rows too wide for one CTA's shared memory (W x Dp > ~200 KB): each
+// reference volume is computed on its own from x-tiles of census strings.
+constexpr int kCostTileX = 64;
+
+__global__ void __launch_bounds__(256)
+    cost_tiled_kernel(const uint64_t* __restrict__ cref, const uint64_t* __restrict__ coth, int W,
+                      int H, int D, int Dp, int cmax, int ref_is_right, uint8_t* __restrict__ out) {
+  __shared__ uint64_t sref[kCostTileX];
+  __shared__ uint64_t soth[kCostTileX + SF_MAX_DISPARITY];
+  const int y = blockIdx.y;
+  const int xs = blockIdx.x * kCostTileX;
+  const int nx = min(kCostTileX, W - xs);
+  const int o_lo = ref_is_right ? xs : xs - (Dp - 1);   // candidate columns [o_lo, o_lo + nx + Dp - 1)
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) sref[i] = cref[(size_t)y * W + xs + i];
+  for (int i = threadIdx.x; i < nx + Dp - 1; i += blockDim.x) {
+    const int xo = o_lo + i;
+    soth[i] = (xo >= 0 && xo < W) ? coth[(size_t)y * W + xo] : 0ull;
+  }
+  __syncthreads();
+  const int groups = Dp / 4;
+  uint32_t* row = reinterpret_cast<uint32_t*>(out + ((size_t)y * W + xs) * Dp);
+  for (int i = threadIdx.x; i < nx * groups; i += blockDim.x) {
+    const int px = i / groups, d0 = (i - px * groups) * 4;
+    const int x = xs + px;
+    uint32_t packed = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int d = d0 + k;
+      const int xo = ref_is_right ? x + d : x - d;
+      const uint32_t c = (d < D && xo >= 0 && xo < W) ? (uint32_t)__popcll(sref[px] ^ soth[xo - o_lo])
+                                                       : (uint32_t)cmax;
+      packed |= c << (8 * k);
+    }
+    row[i] = packed;
   }
 }
 
@@ -823,6 +862,13 @@ cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int 
                              int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
   const size_t smem = (size_t)W * 16 + (size_t)W * Dp;
+  if (smem > kCostPairSmemMax) {
+    count_launches(2);
+    dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
+    cost_tiled_kernel<<<grid, 256, 0, s>>>(cL, cR, W, H, D, Dp, cmax, 0, CL);
+    cost_tiled_kernel<<<grid, 256, 0, s>>>(cR, cL, W, H, D, Dp, cmax, 1, CR);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaFuncSetAttribute(cost_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        227 * 1024);
   if (e != cudaSuccess) return e;

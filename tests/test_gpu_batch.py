@@ -76,6 +76,11 @@ def test_batch_graph_replay_equals_per_instance(sf):
     sf.sf_batch_release_graphs()
 
 
+def test_batch_with_wide_rows_equals_per_instance(sf):
+    # 1242 x 192 and 900 x 256 distances per row exceed one CTA's shared memory
+    _compare(sf, _quads([(1242, 24, 192), (96, 64, 16), (900, 20, 256)], seed0=40), graph=True)
+
+
 def test_batch_small_item_against_oracle(sf, oracle_mod):
     quads = _quads([(64, 48, 16), (96, 64, 32)], seed0=7)
     outs = _compare(sf, quads, graph=False)

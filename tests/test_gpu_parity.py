@@ -170,7 +170,9 @@ def test_sgm_full_planes(sf, oracle_mod, seed, path):
 
 @pytest.mark.parametrize("W,H,D,seed", [(67, 53, 24, 5), (130, 41, 48, 6), (200, 60, 64, 7),
                                         (33, 9, 16, 8), (97, 40, 100, 9), (130, 41, 192, 10),
-                                        (300, 25, 256, 11), (31, 13, 16, 12), (95, 19, 128, 13)])
+                                        (300, 25, 256, 11), (31, 13, 16, 12), (95, 19, 128, 13),
+                                        # rows of more distances than one CTA holds (tiled cost)
+                                        (1300, 20, 192, 14), (900, 18, 256, 15)])
 def test_sgm_full_ragged(sf, oracle_mod, W, H, D, seed, path):
     q = synth.fronto_planes(W=W, H=H, D=D, disparities=(2, D // 3, D - 5), seed=seed)
     p = sf.params(D=D)
