@@ -137,6 +137,21 @@ def bytes_model(stage, N, D, passes=4):
     return 3 * N * D
 
 
+def measured_traffic(stage):
+    """DRAM bytes per launch of `stage` from the committed ncu capture, or None
+    when there is none or the kernel sources changed since it was taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(prof)).get(stage)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        return rec["bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+    except (OSError, ValueError, KeyError, TypeError, AttributeError):
+        return None
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -211,13 +226,7 @@ def run_ours(args, world, rank, local):
     hbm_peak, peak_kind = peaks()
     algo_bytes = bytes_model(dominant, N, D_MAX)
     achieved = algo_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get(dominant)
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(dominant)
 
     e2e = None
     if not args.no_e2e:
