@@ -115,6 +115,55 @@ size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p)
 sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
                            uint16_t* agg_out, void* workspace, size_t ws_bytes, void* stream);
 
+/* Bytes of the scratch array built into the library for
+ * sf_sgm_aggregate_noalloc (32 MiB per device). */
+#define SF_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* sf_sgm_aggregate without a caller-provided workspace.  The paper has no
+ * counterpart: this is a calling convention of the library, not a step of the
+ * method.  It computes exactly what sf_sgm_aggregate computes (same S, bit for
+ * bit) with the fused band sweeps, whose scratch lives in a file-scope device
+ * array of SF_NOALLOC_SCRATCH_BYTES inside the library instead of the
+ * caller's workspace.
+ *
+ * Who needs it: callers that cannot allocate device memory, e.g. a host
+ * program that owns no device allocator (no PyTorch or memory pool to draw a
+ * workspace from), or a latency-bound loop that must not call cudaMalloc /
+ * cudaFree (they can synchronise the whole device and take driver locks).
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ *
+ * cost: uint8 [H][W][D], 16-byte aligned; agg_out: uint16 [H][W][D];
+ * err_out: one int32 in device memory or NULL; after the call has run on
+ * `stream` it holds 0, or 1 if a bounded inter-CTA wait of the sweeps gave up
+ * (agg_out is then invalid).  All pointers are device pointers; the
+ * parameters are read on the host during the call.
+ *
+ * Limits: D % 16 == 0, and the scratch the sweeps need for W x H x D (about
+ * 4 x W x H x D bytes, more when D is not a power of two, plus small tables)
+ * must fit SF_NOALLOC_SCRATCH_BYTES (e.g. 320 x 240 at D = 64, 640 x 480 at
+ * D = 16, 1242 x 40 at D = 128); larger requests and other D return
+ * SF_ERR_UNSUPPORTED before anything is enqueued.  Other argument
+ * errors return SF_ERR_INVALID_ARG as in sf_sgm_aggregate.
+ *
+ * Zero state: the flags, task counters and error word at the start of the
+ * scratch are cleared on `stream` by every call (cudaMemsetAsync); no other
+ * part of the scratch has to start at zero.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current; this may load the
+ * library's device code).  Make that first call on each device before any
+ * stream capture begins.  The current device must be the device of `stream`.
+ *
+ * Concurrency: there is ONE scratch array per device and process.  Two calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads, without ordering between them) use the same scratch and race;
+ * their results are then undefined.  Order such calls on one stream or
+ * synchronise between them. */
+sf_status sf_sgm_aggregate_noalloc(const uint8_t* cost, int32_t W, int32_t H,
+                                   const sf_sgm_params* p, uint16_t* agg_out, int32_t* err_out,
+                                   void* stream);
+
 /* Winner-take-all and parabolic subpixel refinement (Sec. 3.1).  d* is the
  * smallest d reaching min_d S; for subpixel = 1 and 0 < d* < D-1 the output is
  * d* + (a-b)/(2(a+b)) with a = S(d*-1)-S(d*), b = S(d*+1)-S(d*), else d*.

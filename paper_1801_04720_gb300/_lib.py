@@ -29,7 +29,10 @@ EXPORTED = [
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
     "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
     "sf_batch_workspace_size", "sf_batch_run", "sf_batch_release_graphs", "sf_set_sweep_shape",
+    "sf_sgm_aggregate_noalloc",
 ]
+
+SF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 SF_BATCH_GRAPH = 1
 
@@ -97,6 +100,7 @@ def load(path: str = LIB_PATH):
             "sf_cost_volume": (i32, [P, P, i32, i32, i32, PP, i32, P, P]),
             "sf_aggregate_workspace_size": (sz, [i32, i32, PP]),
             "sf_sgm_aggregate": (i32, [P, i32, i32, PP, P, P, sz, P]),
+            "sf_sgm_aggregate_noalloc": (i32, [P, i32, i32, PP, P, P, P]),
             "sf_disparity_select": (i32, [P, i32, i32, i32, i32, P, P, P]),
             "sf_lr_check": (i32, [P, P, P, i32, i32, i32, P, P, P]),
             "sf_combine_sceneflow": (i32, [P, P, P, i32, i32, PC, P, P, P, P, P]),
@@ -193,6 +197,20 @@ def sf_sgm_aggregate(cost, p: SgmParams, out=None, ws="auto", stream=None):
     nbytes = ws.numel() if ws is not None else 0
     _check("sf_sgm_aggregate", load().sf_sgm_aggregate(_ptr(cost), W, H, ctypes.byref(p), _ptr(out),
                                                        _ptr(ws), nbytes, _stream(stream)))
+    return out
+
+
+def sf_sgm_aggregate_noalloc(cost, p: SgmParams, out, err=None, stream=None):
+    """S of `cost` into the caller's `out` (uint16/int16 [H][W][D]) with the
+    library's built-in scratch: no device allocation.  `err` (one int32 on
+    the device, optional) receives the sweeps' bounded-wait status."""
+    _dev(cost, torch.uint8, "cost")
+    H, W, D = cost.shape
+    if D != p.D:
+        raise ValueError("cost volume depth must equal p.D")
+    _check("sf_sgm_aggregate_noalloc",
+           load().sf_sgm_aggregate_noalloc(_ptr(cost), W, H, ctypes.byref(p), _ptr(out), _ptr(err),
+                                           _stream(stream)))
     return out
 
 

@@ -957,3 +957,105 @@ sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Aggregation without a caller-provided workspace.
+//
+// For callers that cannot allocate device memory: a host program that owns no
+// device allocator (no PyTorch, no pool), or a latency-bound loop that must
+// not call cudaMalloc/cudaFree (they can synchronise the device and take
+// locks).  The band sweeps' scratch then lives in this file-scope array, one
+// copy per device, reserved when the library's device code is loaded.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) uint8_t g_noalloc_scratch[SF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first lookup may load the module's device code).
+sf_status noalloc_scratch(uint8_t** out) {
+  int dev = -1;
+  SF_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return SF_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (rc != cudaSuccess || !p) {
+      (void)cudaGetLastError();
+      return SF_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<uint8_t*>(g_noalloc_ptr[dev]);
+  return SF_OK;
+}
+
+}  // namespace
+
+// Scratch of one aggregation pass: control words (error word, the two sweep
+// task counters, the strip flags of both sweeps), then the two horizontal
+// path volumes, the down-sweep partial sum and the band-end states.
+struct NoallocLayout {
+  size_t err = 0, counters = 0, flags = 0, control_bytes = 0, hf = 0, hb = 0, sdown = 0, bs = 0,
+         total = 0;
+  NoallocLayout(int W, int H, int D) {
+    const size_t N = (size_t)W * H;
+    const int J = (W + fused::kTW - 1) / fused::kTW;
+    const int Dp = fused::padded_d(D);
+    size_t c = 0;
+    err = c; c += sizeof(int);
+    counters = c; c += 2 * sizeof(int);
+    flags = c; c += (size_t)2 * J * sizeof(int);
+    control_bytes = align_up(c, 256);
+    size_t o = control_bytes;
+    hf = o; o = align_up(o + N * Dp, 256);
+    hb = o; o = align_up(o + N * Dp, 256);
+    sdown = o; o = align_up(o + fused::sdown_bytes(W, H, D), 256);
+    bs = o; o = align_up(o + fused::bs_bytes(W, D), 256);
+    total = o;
+  }
+};
+
+extern "C" sf_status sf_sgm_aggregate_noalloc(const uint8_t* cost, int32_t W, int32_t H,
+                                              const sf_sgm_params* p, uint16_t* agg_out,
+                                              int32_t* err_out, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!cost || !agg_out) return SF_ERR_INVALID_ARG;
+  if ((st = check_params(p, W, H)) != SF_OK) return st;
+  if (p->D % 16 != 0) return SF_ERR_UNSUPPORTED;
+  if (!aligned(cost, 16) || !aligned(agg_out, 2) || !aligned(err_out, 4)) return SF_ERR_INVALID_ARG;
+  const NoallocLayout lay(W, H, p->D);
+  if (lay.total > (size_t)SF_NOALLOC_SCRATCH_BYTES) return SF_ERR_UNSUPPORTED;
+  uint8_t* ws = nullptr;
+  if ((st = noalloc_scratch(&ws)) != SF_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the control words start every call at zero; the rest of the scratch is
+  // fully written before it is read
+  SF_TRY_CUDA(cudaMemsetAsync(ws, 0, lay.control_bytes, s));
+  fused::PassDesc d{};
+  d.W = W; d.H = H; d.D = p->D; d.Dp = fused::padded_d(p->D);
+  d.J = (W + fused::kTW - 1) / fused::kTW;
+  d.nb = (H + fused::band_rows(p->D) - 1) / fused::band_rows(p->D);
+  d.cost = cost;
+  d.hfwd = ws + lay.hf;
+  d.hbwd = ws + lay.hb;
+  d.sdown = reinterpret_cast<uint32_t*>(ws + lay.sdown);
+  d.bs = ws + lay.bs;
+  d.flags_down = reinterpret_cast<int*>(ws + lay.flags);
+  d.flags_up = d.flags_down + d.J;
+  d.dint = nullptr;
+  d.dsub = nullptr;
+  d.S = agg_out;
+  st = run_sweeps(p, &d, 1, p->D, nullptr, nullptr, nullptr, nullptr,
+                  reinterpret_cast<int*>(ws + lay.counters), reinterpret_cast<int*>(ws + lay.err), s);
+  if (st != SF_OK) return st;
+  if (err_out)
+    SF_TRY_CUDA(cudaMemcpyAsync(err_out, ws + lay.err, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  return SF_OK;
+}
