@@ -368,3 +368,15 @@ def stream(n_frames, seed=0, W=2048, H=1024, D=256, n_segments=40, **kw):
     scene drawn from the automotive recipe at this size."""
     return [automotive(seed=seed * 1000 + k, W=W, H=H, D=D, n_segments=n_segments, **kw)
             for k in range(n_frames)]
+
+
+def confnet_init(seed, layers):
+    """Seeded initial parameters of a 3x3 convolutional network: for each
+    (in_channels, out_channels) in `layers`, He-normal weights [co][3][3][ci]
+    (std sqrt(2 / (9 ci))) then zero biases, flattened, float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in layers:
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), size=9 * ci * co))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
