@@ -305,6 +305,8 @@ typedef enum {
   SF_STAGE_LRCHECK = 4,     /* left-right check                              */
   SF_STAGE_COMBINE = 5,     /* scene-flow combination                        */
   SF_STAGE_SGM_SWEEP = 6,   /* fused cost + aggregation sweep                */
+  SF_STAGE_FEATURES = 7,    /* learned path: features of the cost curve      */
+  SF_STAGE_CONFNET = 8,     /* learned path: confidence network inference    */
   SF_NUM_STAGES = 7
 } sf_stage;
 
@@ -338,6 +340,107 @@ sf_status sf_set_fused(int32_t enable);
  * otherwise. */
 sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const sf_sgm_params* p,
                              int32_t npairs, void* stream);
+
+/* ==== Learned confidence ====================================================
+ * No counterpart in the paper: the paper keeps a disparity where the
+ * left-right check of Sec. 3.1 passes, which costs a second SGM pass with the
+ * right image as reference.  These calls predict that check's outcome from
+ * the left pass alone, with a small network trained on labels made by the
+ * check itself.
+ *
+ * Features (bfloat16 [H][W][8], per pixel of the left pass, S = sum of the
+ * eight paths, d* its first argmin, S0 = S(d*)):
+ *   0  S0 / 1024
+ *   1  (S2 - S0) / 256, S2 = min S(d) over |d - d*| >= 2 (S0 if none)
+ *   2  curvature / 256: S(d*-1) + S(d*+1) - 2 S0, or 2 (S(nb) - S0) at an end
+ *   3  path disagreement / 16: sum over the groups {(+1,0),(-1,0)},
+ *      {(0,+1),(+1,+1),(-1,+1)}, {(0,-1),(-1,-1),(+1,-1)} of
+ *      min(|d*_group - d*|, 16), d*_group the first argmin of the group's sum
+ *   4  d* / 128
+ *   5  clamp(x - d*, 0, 64) / 64
+ *   6  C(d*) / 64
+ *   7  min(S(d*-1), S(d*+1)) - S0 (the one neighbour at an end) / 256
+ * Each is an integer over a power of two, rounded once to bfloat16.
+ *
+ * Network: z1 = b1 + conv3x3(f, W1), a1 = bf16(relu(z1)); a2, a3 likewise
+ * with W2, W3 (32 channels); logit z4 = b4 + conv3x3(a3, W4); probability
+ * sigmoid(z4).  Zero padding, weights rounded to bfloat16, fp32 biases and
+ * accumulation.  A pixel is accepted iff x - d* >= 0 and prob >= threshold.
+ * Parameters (fp32, this order): W1 [32][3][3][8], b1 [32], W2 [32][3][3][32],
+ * b2 [32], W3 [32][3][3][32], b3 [32], W4 [1][3][3][32], b4 [1]. */
+#define SF_CONFNET_FEATURES 8
+#define SF_CONFNET_CHANNELS 32
+
+/* Number of network parameters (21121). */
+int32_t sf_confnet_param_count(void);
+
+/* Bytes of the packed inference weights written by sf_confnet_pack. */
+size_t sf_confnet_packed_bytes(void);
+
+/* Packs device fp32 parameters into the device blob `packed` (16-byte
+ * aligned, sf_confnet_packed_bytes() bytes) used by the inference calls. */
+sf_status sf_confnet_pack(const float* params, void* packed, void* stream);
+
+/* Network inference on the tensor cores.  features: bf16 [H][W][8];
+ * dint, dsub: the left pass's winners (needed for valid_out / disp_out);
+ * prob_out: float [H][W] or NULL; valid_out: uint8 [H][W] or NULL
+ * (1 = accepted); disp_out: float [H][W] or NULL (dsub where accepted, NaN
+ * elsewhere).  All device pointers. */
+sf_status sf_confnet_infer(const void* packed, const uint16_t* features, const int16_t* dint,
+                           const float* dsub, int32_t W, int32_t H, float threshold, float* prob_out,
+                           uint8_t* valid_out, float* disp_out, void* stream);
+
+/* Optimiser settings of one training step: Adam (bias-corrected, step >= 1)
+ * on the loss sum(w (softplus(z) - y z)) / sum(w), w = 1 for label 1, w_neg
+ * for label 0, 0 for label 255. */
+typedef struct {
+  float lr, beta1, beta2, eps, w_neg;
+  int32_t step;
+} sf_confnet_hparams;
+
+/* Workspace bytes of sf_confnet_train_step for a batch of B images of W x H. */
+size_t sf_confnet_train_workspace_size(int32_t B, int32_t W, int32_t H);
+
+/* One training step on the CUDA cores: forward with the inference roundings
+ * (bf16 weights and activations, fp32 sums), loss, gradients (rounding taken
+ * as identity), then Adam on `params` (skipped when adam_m or adam_v is
+ * NULL).  features: bf16 [B][H][W][8]; labels: uint8 [B][H][W] or NULL
+ * (forward only); grad_out: float [param_count] or NULL (gradient before the
+ * update); loss_out: one device float or NULL; logits_out: float [B][H][W]
+ * or NULL.  All device pointers except hp. */
+sf_status sf_confnet_train_step(float* params, float* adam_m, float* adam_v, const uint16_t* features,
+                                const uint8_t* labels, int32_t B, int32_t W, int32_t H,
+                                const sf_confnet_hparams* hp, float* grad_out, float* loss_out,
+                                float* logits_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* The Adam update alone, with a given gradient (device, param_count floats). */
+sf_status sf_confnet_adam(float* params, float* adam_m, float* adam_v, const float* grad,
+                          const sf_confnet_hparams* hp, void* stream);
+
+/* Workspace bytes of sf_sgm_learned (npairs = 1) or sf_scene_flow_learned
+ * (npairs = 2). */
+size_t sf_learned_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p, int32_t npairs);
+
+/* Stereo with learned confidence: census, the left-reference cost, the eight
+ * paths (path_mask must be 0xFF), the features, then (packed != NULL) the
+ * network and the acceptance rule.  dint_out: int16 [H][W] or NULL;
+ * features_out: bf16 [H][W][8] or NULL; prob_out, valid_out, disp_out as in
+ * sf_confnet_infer (ignored when packed is NULL). */
+sf_status sf_sgm_learned(const uint8_t* left, const uint8_t* right, int32_t W, int32_t H,
+                         int32_t pitch, const sf_sgm_params* p, const void* packed, float threshold,
+                         int16_t* dint_out, float* prob_out, uint8_t* valid_out, float* disp_out,
+                         uint16_t* features_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Scene flow with learned confidence in place of both left-right checks:
+ * D0 and D1 from sf_sgm_learned on the pairs at t and t+1, then the
+ * combination of Sec. 3.3 exactly as in sf_scene_flow.  Outputs as in
+ * sf_scene_flow; workspace of sf_learned_workspace_size(W, H, p, 2). */
+sf_status sf_scene_flow_learned(const uint8_t* left_t, const uint8_t* right_t, const uint8_t* left_t1,
+                                const uint8_t* right_t1, int32_t pitch, const float* flow, int32_t W,
+                                int32_t H, const sf_sgm_params* p, const sf_camera* cam,
+                                const void* packed, float threshold, float* s4_out, float* motion_out,
+                                float* point_out, uint8_t* valid_out, float* D0_out, float* D1_out,
+                                void* workspace, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

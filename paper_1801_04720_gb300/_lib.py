@@ -29,14 +29,18 @@ EXPORTED = [
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
     "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
     "sf_batch_workspace_size", "sf_batch_run", "sf_batch_release_graphs", "sf_set_sweep_shape",
-    "sf_sgm_aggregate_noalloc",
+    "sf_sgm_aggregate_noalloc", "sf_confnet_param_count", "sf_confnet_packed_bytes",
+    "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
+    "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
+    "sf_scene_flow_learned",
 ]
 
 SF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 SF_BATCH_GRAPH = 1
 
-STAGE_NAMES = ["census", "cost", "aggregate", "select", "lrcheck", "combine", "sgm_sweep"]
+STAGE_NAMES = ["census", "cost", "aggregate", "select", "lrcheck", "combine", "sgm_sweep",
+               "features", "confnet"]
 
 
 class SFError(RuntimeError):
@@ -66,6 +70,15 @@ class BatchItem(ctypes.Structure):
                 ("D0_out", ctypes.c_void_p), ("D1_out", ctypes.c_void_p)]
 
 
+class ConfnetHparams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("w_neg", ctypes.c_float), ("step", ctypes.c_int32)]
+
+
+def hparams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, w_neg=1.0, step=1):
+    return ConfnetHparams(lr, beta1, beta2, eps, w_neg, step)
+
+
 def params(D=128, P1=7, P2=86, census_w=9, census_h=7, path_mask=0xFF, subpixel=True, lr_tol=1):
     return SgmParams(census_w, census_h, P1, P2, path_mask, D, int(subpixel), lr_tol)
 
@@ -93,6 +106,7 @@ def load(path: str = LIB_PATH):
         sz = ctypes.c_size_t
         PP = ctypes.POINTER(SgmParams)
         PC = ctypes.POINTER(Camera)
+        PH = ctypes.POINTER(ConfnetHparams)
         sig = {
             "sf_default_params": (None, [PP]),
             "sf_status_string": (ctypes.c_char_p, [i32]),
@@ -118,6 +132,18 @@ def load(path: str = LIB_PATH):
             "sf_batch_release_graphs": (None, []),
             "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
             "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
+            "sf_confnet_param_count": (i32, []),
+            "sf_confnet_packed_bytes": (sz, []),
+            "sf_confnet_pack": (i32, [P, P, P]),
+            "sf_confnet_infer": (i32, [P, P, P, P, i32, i32, ctypes.c_float, P, P, P, P]),
+            "sf_confnet_train_workspace_size": (sz, [i32, i32, i32]),
+            "sf_confnet_train_step": (i32, [P, P, P, P, P, i32, i32, i32, PH, P, P, P, P, sz, P]),
+            "sf_confnet_adam": (i32, [P, P, P, P, PH, P]),
+            "sf_learned_workspace_size": (sz, [i32, i32, PP, i32]),
+            "sf_sgm_learned": (i32, [P, P, i32, i32, i32, PP, P, ctypes.c_float, P, P, P, P, P, P,
+                                     sz, P]),
+            "sf_scene_flow_learned": (i32, [P, P, P, P, i32, P, i32, i32, PP, PC, P, ctypes.c_float,
+                                            P, P, P, P, P, P, P, sz, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -414,3 +440,104 @@ def sf_batch_release_graphs():
 
 def sf_set_sweep_shape(d_lo, d_hi, dc, halo):
     _check("sf_set_sweep_shape", load().sf_set_sweep_shape(d_lo, d_hi, dc, halo))
+
+
+# ---- learned confidence ------------------------------------------------------
+
+def confnet_param_count() -> int:
+    return int(load().sf_confnet_param_count())
+
+
+def confnet_pack(params_t, stream=None):
+    """fp32 parameters (device) -> packed bf16 inference blob (device uint8)."""
+    _dev(params_t, torch.float32, "params")
+    packed = torch.empty(int(load().sf_confnet_packed_bytes()), dtype=torch.uint8,
+                         device=params_t.device)
+    _check("sf_confnet_pack", load().sf_confnet_pack(_ptr(params_t), _ptr(packed), _stream(stream)))
+    return packed
+
+
+def confnet_infer(packed, features, dint=None, dsub=None, threshold=0.5, prob=True, stream=None):
+    """Network inference; returns {"prob", "valid", "disp"} (None where not asked)."""
+    H, W = features.shape[0], features.shape[1]
+    dev = features.device
+    out = {"prob": torch.empty((H, W), dtype=torch.float32, device=dev) if prob else None,
+           "valid": torch.empty((H, W), dtype=torch.uint8, device=dev) if dint is not None else None,
+           "disp": torch.empty((H, W), dtype=torch.float32, device=dev) if dint is not None else None}
+    _check("sf_confnet_infer",
+           load().sf_confnet_infer(_ptr(packed), _ptr(features), _ptr(dint), _ptr(dsub), W, H,
+                                   float(threshold), _ptr(out["prob"]), _ptr(out["valid"]),
+                                   _ptr(out["disp"]), _stream(stream)))
+    return out
+
+
+def confnet_train_workspace(B, W, H, device):
+    n = int(load().sf_confnet_train_workspace_size(B, W, H))
+    if n == 0:
+        raise ValueError("batch too large for one training step")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def confnet_train_step(params_t, m, v, features, labels, hp: ConfnetHparams, ws=None, grad=None,
+                       loss=None, logits=None, stream=None):
+    """features: bf16-as-int16 [B][H][W][8]; labels uint8 [B][H][W] or None."""
+    B, H, W = features.shape[0], features.shape[1], features.shape[2]
+    if ws is None:
+        ws = confnet_train_workspace(B, W, H, features.device)
+    _check("sf_confnet_train_step",
+           load().sf_confnet_train_step(_ptr(params_t), _ptr(m), _ptr(v), _ptr(features),
+                                        _ptr(labels), B, W, H, ctypes.byref(hp), _ptr(grad),
+                                        _ptr(loss), _ptr(logits), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+
+
+def confnet_adam(params_t, m, v, grad, hp: ConfnetHparams, stream=None):
+    _check("sf_confnet_adam", load().sf_confnet_adam(_ptr(params_t), _ptr(m), _ptr(v), _ptr(grad),
+                                                     ctypes.byref(hp), _stream(stream)))
+
+
+def learned_workspace(W, H, p: SgmParams, npairs, device):
+    n = int(load().sf_learned_workspace_size(W, H, ctypes.byref(p), npairs))
+    if n == 0:
+        raise ValueError("unsupported learned-path size")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def sf_sgm_learned(left, right, p: SgmParams, packed=None, threshold=0.5, ws=None, features=True,
+                   stream=None):
+    """Left pass + features (+ network when `packed` is given).  Returns
+    {"dint", "features", "prob", "valid", "disp"}."""
+    H, W = left.shape
+    dev = left.device
+    if ws is None:
+        ws = learned_workspace(W, H, p, 1, dev)
+    out = {"dint": torch.empty((H, W), dtype=torch.int16, device=dev),
+           "features": torch.empty((H, W, 8), dtype=torch.int16, device=dev) if features else None,
+           "prob": torch.empty((H, W), dtype=torch.float32, device=dev) if packed is not None else None,
+           "valid": torch.empty((H, W), dtype=torch.uint8, device=dev) if packed is not None else None,
+           "disp": torch.empty((H, W), dtype=torch.float32, device=dev) if packed is not None else None}
+    _check("sf_sgm_learned",
+           load().sf_sgm_learned(_ptr(left), _ptr(right), W, H, W, ctypes.byref(p), _ptr(packed),
+                                 float(threshold), _ptr(out["dint"]), _ptr(out["prob"]),
+                                 _ptr(out["valid"]), _ptr(out["disp"]), _ptr(out["features"]),
+                                 _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def sf_scene_flow_learned(images, flow, p: SgmParams, cam: Camera, packed, threshold, ws=None,
+                          out=None, stream=None):
+    left_t, right_t, left_t1, right_t1 = images
+    H, W = left_t.shape
+    dev = left_t.device
+    if ws is None:
+        ws = learned_workspace(W, H, p, 2, dev)
+    if out is None:
+        out = alloc_scene_flow_outputs(W, H, dev)
+    _check("sf_scene_flow_learned",
+           load().sf_scene_flow_learned(_ptr(left_t), _ptr(right_t), _ptr(left_t1), _ptr(right_t1),
+                                        W, _ptr(flow), W, H, ctypes.byref(p), ctypes.byref(cam),
+                                        _ptr(packed), float(threshold), _ptr(out["s4"]),
+                                        _ptr(out["motion"]), _ptr(out["point"]), _ptr(out["valid"]),
+                                        _ptr(out["D0"]), _ptr(out["D1"]), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+    return out

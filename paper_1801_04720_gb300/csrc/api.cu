@@ -7,6 +7,7 @@
 #include <vector>
 #include <algorithm>
 
+#include "sf_confnet.cuh"
 #include "sf_fused.cuh"
 #include "sf_internal.cuh"
 
@@ -1059,3 +1060,274 @@ extern "C" sf_status sf_sgm_aggregate_noalloc(const uint8_t* cost, int32_t W, in
     SF_TRY_CUDA(cudaMemcpyAsync(err_out, ws + lay.err, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   return SF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned confidence: the left pass, its features, the network.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct LearnedPair {
+  size_t census_l = 0, census_r = 0, cost = 0, hf = 0, hb = 0, sdown = 0, bs = 0, S = 0, feat = 0,
+         dint = 0, dsub = 0, disp = 0, flags = 0;
+};
+
+struct LearnedPlan {
+  size_t err = 0, counters = 0, control_bytes = 0, total = 0;
+  LearnedPair pr[2];
+  LearnedPlan(int W, int H, int D, int npairs) {
+    const size_t N = (size_t)W * H;
+    const int J = (W + fused::kTW - 1) / fused::kTW;
+    const int Dp = fused::padded_d(D);
+    size_t c = 0;
+    err = c; c += sizeof(int);
+    counters = c; c += 2 * sizeof(int);
+    for (int k = 0; k < npairs; k++) {
+      pr[k].flags = c;
+      c += (size_t)2 * J * sizeof(int);
+    }
+    control_bytes = align_up(c, 256);
+    size_t o = control_bytes;
+    auto carve = [&](size_t bytes) {
+      const size_t at = o;
+      o = align_up(o + bytes, 256);
+      return at;
+    };
+    for (int k = 0; k < npairs; k++) {
+      LearnedPair& b = pr[k];
+      b.census_l = carve(N * 8);
+      b.census_r = carve(N * 8);
+      b.cost = carve(N * Dp);
+      b.hf = carve(N * Dp);
+      b.hb = carve(N * Dp);
+      b.sdown = carve(fused::sdown_bytes(W, H, D));
+      b.bs = carve(fused::bs_bytes(W, D));
+      b.S = carve(N * D * sizeof(uint16_t));
+      b.feat = carve(N * 16);
+      b.dint = carve(N * sizeof(int16_t));
+      b.dsub = carve(N * sizeof(float));
+      b.disp = carve(N * sizeof(float));
+    }
+    total = o;
+  }
+};
+
+sf_status check_learned(int W, int H, const sf_sgm_params* p) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if ((st = check_params(p, W, H)) != SF_OK) return st;
+  if (p->path_mask != 0xFFu) return SF_ERR_UNSUPPORTED;   // features use all eight paths
+  return SF_OK;
+}
+
+// Learned stereo for npairs (1 or 2) pairs of one size: both left passes
+// share the sweep launches.
+sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_t* const* right, int W,
+                            int H, int pitch, const sf_sgm_params* p, const void* packed, float threshold,
+                            int16_t* const* dint_out, float* const* prob_out, uint8_t* const* valid_out,
+                            float* const* disp_out, uint16_t* const* feat_out, uint8_t* ws,
+                            cudaStream_t s) {
+  const LearnedPlan plan(W, H, p->D, npairs);
+  const int D = p->D, Dp = fused::padded_d(D);
+  const int J = (W + fused::kTW - 1) / fused::kTW;
+  SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
+  fused::PassDesc d[2];
+  for (int k = 0; k < npairs; k++) {
+    const LearnedPair& b = plan.pr[k];
+    uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b.census_l);
+    uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b.census_r);
+    SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, cl, s));
+    SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, cr, s));
+    SF_TRY_CUDA(fused::launch_cost_left(cl, cr, W, H, D, Dp, p->census_w * p->census_h - 1, ws + b.cost, s));
+    fused::PassDesc& pd = d[k];
+    pd = fused::PassDesc{};
+    pd.W = W; pd.H = H; pd.D = D; pd.Dp = Dp; pd.J = J;
+    pd.nb = (H + fused::band_rows(D) - 1) / fused::band_rows(D);
+    pd.cost = ws + b.cost;
+    pd.hfwd = ws + b.hf;
+    pd.hbwd = ws + b.hb;
+    pd.sdown = reinterpret_cast<uint32_t*>(ws + b.sdown);
+    pd.bs = ws + b.bs;
+    pd.flags_down = reinterpret_cast<int*>(ws + b.flags);
+    pd.flags_up = pd.flags_down + J;
+    pd.dint = nullptr;
+    pd.dsub = nullptr;
+    pd.S = reinterpret_cast<uint16_t*>(ws + b.S);
+  }
+  sf_status st = run_sweeps(p, d, npairs, D, nullptr, nullptr, nullptr, nullptr,
+                            reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s);
+  if (st != SF_OK) return st;
+  const fused::Shape shape = fused::shape_for(D);
+  for (int k = 0; k < npairs; k++) {
+    const LearnedPair& b = plan.pr[k];
+    confnet::FeatureArgs fa{};
+    fa.W = W; fa.H = H; fa.D = D; fa.Dp = Dp; fa.J = J;
+    fa.dpad_shape = shape.chunks * shape.dc;
+    fa.subpixel = p->subpixel;
+    fa.S = reinterpret_cast<const uint16_t*>(ws + b.S);
+    fa.sdown = reinterpret_cast<const uint32_t*>(ws + b.sdown);
+    fa.hfwd = ws + b.hf;
+    fa.hbwd = ws + b.hb;
+    fa.cost = ws + b.cost;
+    fa.feat = feat_out && feat_out[k] ? feat_out[k] : reinterpret_cast<uint16_t*>(ws + b.feat);
+    fa.dint = dint_out && dint_out[k] ? dint_out[k] : reinterpret_cast<int16_t*>(ws + b.dint);
+    fa.dsub = reinterpret_cast<float*>(ws + b.dsub);
+    {
+      StageTrace trace(SF_STAGE_FEATURES, s);
+      SF_TRY_CUDA(confnet::launch_features(fa, s));
+    }
+    if (packed) {
+      confnet::InferArgs ia{};
+      ia.W = W; ia.H = H;
+      ia.packed = packed;
+      ia.feat = fa.feat;
+      ia.dint = fa.dint;
+      ia.dsub = fa.dsub;
+      ia.threshold = threshold;
+      ia.prob = prob_out ? prob_out[k] : nullptr;
+      ia.valid = valid_out ? valid_out[k] : nullptr;
+      ia.disp = disp_out ? disp_out[k] : nullptr;
+      ia.err = reinterpret_cast<int*>(ws + plan.err);
+      StageTrace trace(SF_STAGE_CONFNET, s);
+      SF_TRY_CUDA(confnet::launch_infer(ia, s));
+    }
+  }
+  return SF_OK;
+}
+
+bool hparams_ok(const sf_confnet_hparams* hp) {
+  return hp && hp->step >= 1 && hp->lr >= 0.0f && hp->beta1 >= 0.0f && hp->beta1 < 1.0f &&
+         hp->beta2 >= 0.0f && hp->beta2 < 1.0f && hp->eps > 0.0f && hp->w_neg >= 0.0f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sf_confnet_param_count(void) { return confnet::kParamCount; }
+
+size_t sf_confnet_packed_bytes(void) { return confnet::kPackedBytes; }
+
+sf_status sf_confnet_pack(const float* params, void* packed, void* stream) {
+  if (!params || !packed || !aligned(packed, 16) || !aligned(params, 4)) return SF_ERR_INVALID_ARG;
+  SF_TRY_CUDA(confnet::launch_pack(params, packed, (cudaStream_t)stream));
+  return SF_OK;
+}
+
+sf_status sf_confnet_infer(const void* packed, const uint16_t* features, const int16_t* dint,
+                           const float* dsub, int32_t W, int32_t H, float threshold, float* prob_out,
+                           uint8_t* valid_out, float* disp_out, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!packed || !features || !aligned(packed, 16) || !aligned(features, 16)) return SF_ERR_INVALID_ARG;
+  if ((valid_out || disp_out) && (!dint || !dsub)) return SF_ERR_INVALID_ARG;
+  if (!aligned(dint, 2) || !aligned(dsub, 4) || !aligned(prob_out, 4) || !aligned(disp_out, 4))
+    return SF_ERR_INVALID_ARG;
+  confnet::InferArgs ia{};
+  ia.W = W; ia.H = H;
+  ia.packed = packed;
+  ia.feat = features;
+  ia.dint = dint;
+  ia.dsub = dsub;
+  ia.threshold = threshold;
+  ia.prob = prob_out;
+  ia.valid = valid_out;
+  ia.disp = disp_out;
+  ia.err = nullptr;
+  SF_TRY_CUDA(confnet::launch_infer(ia, (cudaStream_t)stream));
+  return SF_OK;
+}
+
+size_t sf_confnet_train_workspace_size(int32_t B, int32_t W, int32_t H) {
+  if (B < 1 || W < 1 || H < 1 || (size_t)B * W * H > (size_t)1 << 26) return 0;
+  return confnet::train_workspace_bytes(B, W, H);
+}
+
+sf_status sf_confnet_train_step(float* params, float* adam_m, float* adam_v, const uint16_t* features,
+                                const uint8_t* labels, int32_t B, int32_t W, int32_t H,
+                                const sf_confnet_hparams* hp, float* grad_out, float* loss_out,
+                                float* logits_out, void* workspace, size_t ws_bytes, void* stream) {
+  if (B < 1 || W < 1 || H < 1 || (size_t)B * W * H > (size_t)1 << 26) return SF_ERR_INVALID_ARG;
+  if (!params || !features || !workspace || !hparams_ok(hp)) return SF_ERR_INVALID_ARG;
+  if (ws_bytes < confnet::train_workspace_bytes(B, W, H) || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  if (!aligned(params, 4) || !aligned(features, 16) || !aligned(grad_out, 4) || !aligned(loss_out, 4) ||
+      !aligned(logits_out, 4) || !aligned(adam_m, 4) || !aligned(adam_v, 4))
+    return SF_ERR_INVALID_ARG;
+  confnet::TrainArgs t{};
+  t.B = B; t.W = W; t.H = H;
+  t.params = params;
+  t.adam_m = labels ? adam_m : nullptr;
+  t.adam_v = labels ? adam_v : nullptr;
+  t.features = features;
+  t.labels = labels;
+  t.lr = hp->lr; t.beta1 = hp->beta1; t.beta2 = hp->beta2; t.eps = hp->eps; t.w_neg = hp->w_neg;
+  t.step = hp->step;
+  t.grad_out = grad_out;
+  t.loss_out = loss_out;
+  t.logits_out = logits_out;
+  t.workspace = workspace;
+  SF_TRY_CUDA(confnet::launch_train_step(t, (cudaStream_t)stream));
+  return SF_OK;
+}
+
+sf_status sf_confnet_adam(float* params, float* adam_m, float* adam_v, const float* grad,
+                          const sf_confnet_hparams* hp, void* stream) {
+  if (!params || !adam_m || !adam_v || !grad || !hparams_ok(hp)) return SF_ERR_INVALID_ARG;
+  SF_TRY_CUDA(confnet::launch_adam(params, adam_m, adam_v, grad, confnet::kParamCount, hp->lr, hp->beta1,
+                                   hp->beta2, hp->eps, hp->step, (cudaStream_t)stream));
+  return SF_OK;
+}
+
+size_t sf_learned_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p, int32_t npairs) {
+  if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
+  if (npairs != 1 && npairs != 2) return 0;
+  return LearnedPlan(W, H, p->D, npairs).total;
+}
+
+sf_status sf_sgm_learned(const uint8_t* left, const uint8_t* right, int32_t W, int32_t H,
+                         int32_t pitch, const sf_sgm_params* p, const void* packed, float threshold,
+                         int16_t* dint_out, float* prob_out, uint8_t* valid_out, float* disp_out,
+                         uint16_t* features_out, void* workspace, size_t ws_bytes, void* stream) {
+  sf_status st = check_learned(W, H, p);
+  if (st != SF_OK) return st;
+  if (!left || !right || !workspace || pitch < W) return SF_ERR_INVALID_ARG;
+  if (ws_bytes < LearnedPlan(W, H, p->D, 1).total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  if (!aligned(packed, 16) || !aligned(features_out, 16) || !aligned(dint_out, 2) || !aligned(prob_out, 4) ||
+      !aligned(disp_out, 4))
+    return SF_ERR_INVALID_ARG;
+  return run_learned_pairs(1, &left, &right, W, H, pitch, p, packed, threshold, &dint_out, &prob_out,
+                           &valid_out, &disp_out, &features_out, (uint8_t*)workspace, (cudaStream_t)stream);
+}
+
+sf_status sf_scene_flow_learned(const uint8_t* left_t, const uint8_t* right_t, const uint8_t* left_t1,
+                                const uint8_t* right_t1, int32_t pitch, const float* flow, int32_t W,
+                                int32_t H, const sf_sgm_params* p, const sf_camera* cam,
+                                const void* packed, float threshold, float* s4_out, float* motion_out,
+                                float* point_out, uint8_t* valid_out, float* D0_out, float* D1_out,
+                                void* workspace, size_t ws_bytes, void* stream) {
+  sf_status st = check_learned(W, H, p);
+  if (st != SF_OK) return st;
+  if (!left_t || !right_t || !left_t1 || !right_t1 || !flow || !cam || !s4_out || !valid_out || !packed ||
+      !workspace || pitch < W)
+    return SF_ERR_INVALID_ARG;
+  if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
+  const LearnedPlan plan(W, H, p->D, 2);
+  if (ws_bytes < plan.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  if (!aligned(packed, 16) || !aligned(flow, 8) || !aligned(s4_out, 16) || !aligned(motion_out, 4) ||
+      !aligned(point_out, 4) || !aligned(D0_out, 4) || !aligned(D1_out, 4))
+    return SF_ERR_INVALID_ARG;
+  uint8_t* ws = (uint8_t*)workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + plan.pr[0].disp);
+  float* D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + plan.pr[1].disp);
+  const uint8_t* L[2] = {left_t, left_t1};
+  const uint8_t* R[2] = {right_t, right_t1};
+  float* disp[2] = {D0, D1};
+  if ((st = run_learned_pairs(2, L, R, W, H, pitch, p, packed, threshold, nullptr, nullptr, nullptr, disp,
+                              nullptr, ws, s)) != SF_OK)
+    return st;
+  SF_TRY_CUDA(launch_combine(D0, D1, flow, W, H, cam->f, cam->B, cam->cx, cam->cy, s4_out, motion_out,
+                             point_out, valid_out, s));
+  return SF_OK;
+}
+
+}  // extern "C"

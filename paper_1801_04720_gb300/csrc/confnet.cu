@@ -1,0 +1,838 @@
+// Learned confidence in place of the right-image SGM pass.
+//
+// The paper keeps a disparity where the left-right check of Sec. 3.1 passes,
+// which needs a second SGM pass with the right image as reference.  This
+// path predicts that check's outcome from the left pass alone:
+//
+//   1. features_kernel: eight channels per pixel of the left pass's
+//      aggregated cost curve S (best cost, margin to the best cost outside
+//      the winner's neighbourhood, curvature, disagreement of the three path
+//      groups, winner, distance to the left border, matching cost at the
+//      winner, smaller neighbour rise), each an integer over a power of two,
+//      stored as bfloat16 [H][W][8].  The winner and its parabolic subpixel
+//      value come out of the same pass, computed exactly like the plain
+//      select.
+//   2. infer_kernel: a 4-layer 3x3 network (8 -> 32 -> 32 -> 32 -> 1, ReLU,
+//      sigmoid), bfloat16 weights and activations, fp32 accumulation on the
+//      5th-generation tensor cores: tcgen05.mma with operands in shared
+//      memory and accumulators in tensor memory, one elected thread issuing,
+//      all four layers of an output tile fused in shared memory.
+//   3. training kernels (fp32 CUDA cores): forward with the same bfloat16
+//      roundings, weighted binary cross-entropy, data and weight gradients,
+//      Adam.
+//
+// Implicit-GEMM layout of the inference kernel.  An output tile is TX x TY
+// pixels; layer l (1..4) is evaluated on a region that extends 4 - l pixels
+// past the tile on every side, enumerated row-major with a fixed pitch P, so
+// that the input of tap (ky, kx) for output pixel m is input pixel
+// m + ky P + kx.  Activations are stored as K-chunk planes [chunk][pixel][8
+// channels] (16 bytes per pixel and chunk): eight consecutive pixels form one
+// 8 x 16-byte core matrix of the no-swizzle K-major operand layout, so a tap
+// is just a 16-byte shift of the descriptor's start address.
+#include <math.h>
+
+#include <cuda_bf16.h>
+
+#include "sf_confnet.cuh"
+
+namespace sf {
+namespace confnet {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// 1. features
+// ---------------------------------------------------------------------------
+constexpr int kMaxPerLane = SF_MAX_DISPARITY / 32;
+
+__global__ void __launch_bounds__(256)
+    features_kernel(FeatureArgs a) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.W * a.H) return;
+  const int y = warp / a.W, x = warp - y * a.W;
+  const size_t pix = (size_t)y * a.W + x;
+  const uint16_t* srow = a.S + pix * a.D;
+  const uint8_t* hf = a.hfwd + pix * a.Dp;
+  const uint8_t* hb = a.hbwd + pix * a.Dp;
+  // partial sum of the three downward paths, tile layout of the band sweeps
+  const int j = x >> 5, c = x & 31, pr = c & 15, hi = c >> 4;
+  const uint32_t* sd = a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape;
+  uint32_t s[kMaxPerLane];
+  uint32_t ks = 0xffffffffu, kh = 0xffffffffu, kd = 0xffffffffu, ku = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < kMaxPerLane; k++) {
+    const int d = lane + 32 * k;
+    s[k] = 0xffffffffu;
+    if (d < a.D) {
+      const uint32_t sv = srow[d];
+      const uint32_t gh = (uint32_t)hf[d] + (uint32_t)hb[d];
+      const uint32_t w = sd[d];
+      const uint32_t gd = hi ? (w >> 16) : (w & 0xffffu);
+      const uint32_t gu = sv - gh - gd;
+      s[k] = sv;
+      ks = min(ks, (sv << 8) | (uint32_t)d);
+      kh = min(kh, (gh << 8) | (uint32_t)d);
+      kd = min(kd, (gd << 8) | (uint32_t)d);
+      ku = min(ku, (gu << 8) | (uint32_t)d);
+    }
+  }
+  ks = __reduce_min_sync(kFullMask, ks);
+  kh = __reduce_min_sync(kFullMask, kh);
+  kd = __reduce_min_sync(kFullMask, kd);
+  ku = __reduce_min_sync(kFullMask, ku);
+  const int ds = (int)(ks & 0xffu);
+  const uint32_t s0 = ks >> 8;
+  uint32_t far = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < kMaxPerLane; k++) {
+    const int d = lane + 32 * k;
+    if (d < a.D && (d - ds >= 2 || ds - d >= 2)) far = min(far, s[k]);
+  }
+  far = __reduce_min_sync(kFullMask, far);
+  if (lane != 0) return;
+  const uint32_t s2 = far == 0xffffffffu ? s0 : far;
+  int curv = 0, rise = 0;
+  if (a.D > 1) {
+    if (ds == 0) {
+      const int n = (int)srow[1] - (int)s0;
+      curv = 2 * n;
+      rise = n;
+    } else if (ds == a.D - 1) {
+      const int n = (int)srow[a.D - 2] - (int)s0;
+      curv = 2 * n;
+      rise = n;
+    } else {
+      const int am = (int)srow[ds - 1] - (int)s0, bp = (int)srow[ds + 1] - (int)s0;
+      curv = am + bp;
+      rise = min(am, bp);
+    }
+  }
+  const int gh_d = (int)(kh & 0xffu), gd_d = (int)(kd & 0xffu), gu_d = (int)(ku & 0xffu);
+  const int dis = min(abs(gh_d - ds), 16) + min(abs(gd_d - ds), 16) + min(abs(gu_d - ds), 16);
+  const int margin = min(max(x - ds, 0), 64);
+  const int cstar = a.cost[pix * a.Dp + ds];
+  // integers over powers of two: exact in fp32, then rounded once to bf16
+  const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
+                       (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
+                       (float)ds * (1.0f / 128.0f),   (float)margin * (1.0f / 64.0f),
+                       (float)cstar * (1.0f / 64.0f), (float)rise * (1.0f / 256.0f)};
+  uint32_t packed[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    packed[i] = *reinterpret_cast<const uint32_t*>(&h2);
+  }
+  reinterpret_cast<uint4*>(a.feat)[pix] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  a.dint[pix] = (int16_t)ds;
+  float v = (float)ds;
+  if (a.subpixel && ds > 0 && ds < a.D - 1) {
+    const int am = (int)srow[ds - 1] - (int)s0, bp = (int)srow[ds + 1] - (int)s0;
+    v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+  }
+  a.dsub[pix] = v;
+}
+
+// ---------------------------------------------------------------------------
+// 2. weight packing for the tensor-core kernel
+// ---------------------------------------------------------------------------
+// Parameter vector offsets (same order as the flat layout of the ABI):
+// W1 [32][3][3][8], b1, W2 [32][3][3][32], b2, W3, b3, W4 [1][3][3][32], b4.
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 9 * kF * kC, kOffW2 = kOffB1 + kC;
+constexpr int kOffB2 = kOffW2 + 9 * kC * kC, kOffW3 = kOffB2 + kC;
+constexpr int kOffB3 = kOffW3 + 9 * kC * kC, kOffW4 = kOffB3 + kC, kOffB4 = kOffW4 + 9 * kC;
+static_assert(kOffB4 + 1 == kParamCount, "parameter layout");
+
+__device__ __forceinline__ float layer_weight(const float* th, int layer, int co, int tap, int ci) {
+  const int ky = tap / 3, kx = tap % 3;
+  if (layer == 0) return th[kOffW1 + ((co * 3 + ky) * 3 + kx) * kF + ci];
+  if (layer == 1) return th[kOffW2 + ((co * 3 + ky) * 3 + kx) * kC + ci];
+  if (layer == 2) return th[kOffW3 + ((co * 3 + ky) * 3 + kx) * kC + ci];
+  return th[kOffW4 + (ky * 3 + kx) * kC + ci];
+}
+
+// Packed blob: bf16 operand blocks of the four layers, then fp32 biases.
+// Block = [K-chunk 0..1][n 0..N-1][8 k-elements].
+//   layer 1: block j (0..4) pairs taps 2j and 2j+1 (tap 9 = zeros), 8 channels each
+//   layers 2, 3: block 2t + s = tap t, input channels 16s .. 16s+15
+//   layer 4: as layers 2, 3 with N = 16 (output 0 real, 1..15 zero)
+__global__ void pack_kernel(const float* __restrict__ th, uint16_t* __restrict__ packed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kWElems) {
+    int layer, rem;
+    if (i < kW1Elems) {
+      layer = 0; rem = i;
+    } else if (i < kW1Elems + kW2Elems) {
+      layer = 1; rem = i - kW1Elems;
+    } else if (i < kW1Elems + 2 * kW2Elems) {
+      layer = 2; rem = i - kW1Elems - kW2Elems;
+    } else {
+      layer = 3; rem = i - kW1Elems - 2 * kW2Elems;
+    }
+    const int N = layer == 3 ? 16 : kC;
+    const int e = rem % 8;
+    const int n = (rem / 8) % N;
+    const int chunk = (rem / (8 * N)) % 2;
+    const int blk = rem / (16 * N);
+    float w = 0.0f;
+    if (layer == 0) {
+      const int tap = 2 * blk + chunk;
+      if (tap < 9) w = layer_weight(th, 0, n, tap, e);
+    } else {
+      const int tap = blk >> 1, s = blk & 1;
+      if (layer < 3 || n == 0) w = layer_weight(th, layer, n, tap, 16 * s + 8 * chunk + e);
+    }
+    packed[i] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+  }
+  if (i < kBiasFloats) {
+    float* bias = reinterpret_cast<float*>(packed + kWElems);
+    float v = 0.0f;
+    if (i < kC) v = th[kOffB1 + i];
+    else if (i < 2 * kC) v = th[kOffB2 + i - kC];
+    else if (i < 3 * kC) v = th[kOffB3 + i - 2 * kC];
+    else if (i == 3 * kC) v = th[kOffB4];
+    bias[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. tensor-core inference (tcgen05)
+// ---------------------------------------------------------------------------
+constexpr int kP = 64;                 // region pitch (pixels)
+constexpr int kTX = kP - 8;            // output tile width
+constexpr int kTY = 8;                 // output tile height
+// rows of the region of layer l (0 = the features, 4 = the output tile)
+__host__ __device__ constexpr int region_rows(int l) { return kTY + 8 - 2 * l; }
+constexpr int kNPix0 = region_rows(0) * kP + 8, kNPix1 = region_rows(1) * kP + 8;
+constexpr int kNPix2 = region_rows(2) * kP + 8, kNPix3 = region_rows(3) * kP + 8;
+constexpr int kPlane0 = kNPix0 * 16, kPlane1 = kNPix1 * 16, kPlane2 = kNPix2 * 16;
+constexpr int kPlane3 = kNPix3 * 16;
+constexpr int kSmFeat = 0;
+constexpr int kSmX = kSmFeat + kPlane0;             // layer-1 then layer-3 activations
+constexpr int kSmY = kSmX + 4 * kPlane1;            // layer-2 activations
+constexpr int kSmW = kSmY + 4 * kPlane2;            // packed weights
+constexpr int kSmBias = kSmW + kWElems * 2;
+constexpr int kSmBar = kSmBias + kBiasFloats * 4;
+constexpr int kSmTmem = kSmBar + 8;
+constexpr int kSmTotal = kSmTmem + 8;
+constexpr int kThreads = 256;
+constexpr uint32_t kTmemCols = 256;
+constexpr long long kMmaSpin = 1ll << 24;
+static_assert(4 * kPlane3 <= 4 * kPlane1, "layer-3 activations reuse the layer-1 buffer");
+static_assert((region_rows(1) * kP) % 128 == 0 && (region_rows(4) * kP) % 128 == 0, "whole M tiles");
+static_assert(kSmTotal <= 227 * 1024, "shared memory");
+static_assert(kSmX % 16 == 0 && kSmY % 16 == 0 && kSmW % 16 == 0 && kSmBar % 8 == 0, "alignment");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major:
+//   start address, leading byte offset (next 8-element K chunk), stride byte
+//   offset (next group of 8 rows), descriptor version 1.
+__device__ __forceinline__ uint64_t mat_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, M = 128, N as given.
+__host__ __device__ constexpr uint32_t instr_desc(int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// 32 consecutive fp32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  return __uint_as_float(r);
+}
+
+// Offset (pixels) of tap t = 3 ky + kx in a pitch-kP region; tap 9 (the
+// zero-weight partner of tap 8 in layer 1) reads the next pixel.
+__device__ __forceinline__ int tap_off(int t) { return t < 9 ? (t / 3) * kP + (t % 3) : 2 * kP + 3; }
+
+__global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint8_t* feat_s = sm + kSmFeat;
+  uint8_t* bufx = sm + kSmX;
+  uint8_t* bufy = sm + kSmY;
+  const float* bias = reinterpret_cast<const float*>(sm + kSmBias);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kSmBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmTmem);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;
+
+  // zero everything once (region slack stays finite), weights and biases in
+  for (int i = tid; i < kSmW / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  const uint4* wsrc = reinterpret_cast<const uint4*>(a.packed);
+  for (int i = tid; i < (kWElems * 2 + kBiasFloats * 4) / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sm + kSmW)[i] = wsrc[i];
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t barp = smem_u32(bar);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
+  const int ntiles = tiles_x * tiles_y;
+  const uint32_t w_base = smem_u32(sm + kSmW);
+  const uint32_t w2_base = w_base + kW1Elems * 2, w3_base = w2_base + kW2Elems * 2;
+  const uint32_t w4_base = w3_base + kW2Elems * 2;
+
+  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int X0 = (tile % tiles_x) * kTX, Y0 = (tile / tiles_x) * kTY;
+    // ---- features of region 0 (origin X0-4, Y0-4), zero outside the image ----
+    for (int i = tid; i < region_rows(0) * kP; i += kThreads) {
+      const int gy = Y0 - 4 + i / kP, gx = X0 - 4 + i % kP;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+        v = reinterpret_cast<const uint4*>(a.feat)[(size_t)gy * a.W + gx];
+      reinterpret_cast<uint4*>(feat_s)[i] = v;
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+
+    for (int layer = 0; layer < 4 && !failed; layer++) {
+      const int out_rows = region_rows(layer + 1);
+      const int nm = out_rows * kP / 128;
+      const int N = layer == 3 ? 16 : kC;
+      const uint32_t idesc = instr_desc(N);
+      // ---- issue: one thread, all M tiles of the layer ----
+      if (tid == 0) {
+        fence_after();
+        if (layer == 0) {
+          const uint32_t ab = smem_u32(feat_s);
+          for (int mt = 0; mt < nm; mt++) {
+            for (int j = 0; j < 5; j++) {
+              const int o0 = tap_off(2 * j), o1 = tap_off(2 * j + 1);
+              const uint64_t ad = mat_desc(ab + 16u * (uint32_t)(128 * mt + o0), 16u * (uint32_t)(o1 - o0), 128u);
+              const uint64_t bd = mat_desc(w_base + (uint32_t)j * 2u * kC * 16u, kC * 16u, 128u);
+              mma_bf16(tmem + (uint32_t)(kC * mt), ad, bd, idesc, j > 0);
+            }
+          }
+        } else {
+          const uint32_t ab = smem_u32(layer == 2 ? bufy : bufx);
+          const uint32_t plane = layer == 1 ? kPlane1 : layer == 2 ? kPlane2 : kPlane3;
+          const uint32_t wb = layer == 1 ? w2_base : layer == 2 ? w3_base : w4_base;
+          for (int mt = 0; mt < nm; mt++) {
+            for (int t = 0; t < 9; t++) {
+              for (int s = 0; s < 2; s++) {
+                const uint64_t ad =
+                    mat_desc(ab + 2u * s * plane + 16u * (uint32_t)(128 * mt + tap_off(t)), plane, 128u);
+                const uint64_t bd = mat_desc(wb + (uint32_t)(2 * t + s) * 2u * N * 16u, (uint32_t)N * 16u, 128u);
+                mma_bf16(tmem + (uint32_t)(N * mt), ad, bd, idesc, (t | s) != 0);
+              }
+            }
+          }
+        }
+        mma_commit(barp);
+      }
+      // ---- wait for the layer's accumulators (bounded) ----
+      long long spins = 0;
+      bool timed_out = false;
+      while (!bar_try_wait(barp, phase)) {
+        if (++spins > kMmaSpin) {
+          timed_out = true;
+          break;
+        }
+      }
+      phase ^= 1u;
+      failed = __syncthreads_or(timed_out) != 0;
+      if (failed) {
+        if (tid == 0) atomicExch(a.err, 1);
+        break;
+      }
+      fence_after();
+      // ---- epilogue: this warp's 32 rows of its M tiles ----
+      const int rg0 = 4 - (layer + 1);                  // region origin offset of the output
+      const int wl = kP - 2 * (layer + 1);              // valid region width
+      if (layer < 3) {
+        uint8_t* out = layer == 1 ? bufy : bufx;
+        const int plane = layer == 0 ? kPlane1 : layer == 1 ? kPlane2 : kPlane3;
+        const float* bl = bias + kC * layer;
+        for (int mt = half; mt < nm; mt += 2) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(kC * mt), v);
+          const int m = 128 * mt + 32 * quad + lane;
+          const int i = m / kP, jj = m - i * kP;
+          const int gy = Y0 - rg0 + i, gx = X0 - rg0 + jj;
+          const bool keep = jj < wl && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+#pragma unroll
+          for (int cgrp = 0; cgrp < 4; cgrp++) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const float lo = keep ? fmaxf(v[8 * cgrp + 2 * e] + bl[8 * cgrp + 2 * e], 0.0f) : 0.0f;
+              const float hi = keep ? fmaxf(v[8 * cgrp + 2 * e + 1] + bl[8 * cgrp + 2 * e + 1], 0.0f) : 0.0f;
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+              w4[e] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            *reinterpret_cast<uint4*>(out + cgrp * plane + 16 * m) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+          }
+        }
+      } else {
+        for (int mt = half; mt < nm; mt += 2) {
+          const float z = tmem_ld1(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(16 * mt)) + bias[3 * kC];
+          const int m = 128 * mt + 32 * quad + lane;
+          const int i = m / kP, jj = m - i * kP;
+          const int gy = Y0 + i, gx = X0 + jj;
+          if (jj < kTX && gy < a.H && gx < a.W) {
+            const float prob = 1.0f / (1.0f + expf(-z));
+            const size_t pix = (size_t)gy * a.W + gx;
+            if (a.prob) a.prob[pix] = prob;
+            if (a.valid || a.disp) {
+              const bool ok = gx - (int)a.dint[pix] >= 0 && prob >= a.threshold;
+              if (a.valid) a.valid[pix] = ok ? 1 : 0;
+              if (a.disp) a.disp[pix] = ok ? a.dsub[pix] : __int_as_float(0x7fc00000);
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// 4. training kernels (fp32 CUDA cores)
+// ---------------------------------------------------------------------------
+constexpr int kTTX = 16, kTTY = 8;            // training tile (one thread per pixel)
+
+__device__ __forceinline__ float bf16_round(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+// fp32 copy of the parameters with every weight rounded to bf16 (biases kept)
+__global__ void round_weights_kernel(const float* __restrict__ th, float* __restrict__ wr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kParamCount) return;
+  const bool is_bias = (i >= kOffB1 && i < kOffW2) || (i >= kOffB2 && i < kOffW3) ||
+                       (i >= kOffB3 && i < kOffW4) || i == kOffB4;
+  wr[i] = is_bias ? th[i] : bf16_round(th[i]);
+}
+
+// Layer input as fp32: bf16 features (layer 1) or stored activations.
+template <int CI>
+__device__ __forceinline__ void load_in_tile(const void* in, bool in_bf16, float* tile, int b, int H, int W,
+                                             int y0, int x0) {
+  const int n = (kTTY + 2) * (kTTX + 2) * CI;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int ci = i % CI, p = i / CI;
+    const int ty = p / (kTTX + 2), tx = p % (kTTX + 2);
+    const int gy = y0 - 1 + ty, gx = x0 - 1 + tx;
+    float v = 0.0f;
+    if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+      const size_t idx = (((size_t)b * H + gy) * W + gx) * CI + ci;
+      v = in_bf16 ? __bfloat162float(__ushort_as_bfloat16(reinterpret_cast<const uint16_t*>(in)[idx]))
+                  : reinterpret_cast<const float*>(in)[idx];
+    }
+    tile[i] = v;
+  }
+}
+
+// z = b + conv3x3(a_in, wr); out = bf16(relu(z)) (hidden layers) or z (last).
+template <int CI, int CO, bool HIDDEN>
+__global__ void __launch_bounds__(kTTX * kTTY) fwd_kernel(const void* in, int in_bf16, const float* wr, int woff,
+                                                        int boff, float* out, int H, int W) {
+  extern __shared__ float dsm[];
+  float* tile = dsm;                                   // [(kTTY + 2) * (kTTX + 2) * CI]
+  float* ws = dsm + (kTTY + 2) * (kTTX + 2) * CI;      // [CO * 9 * CI]
+  const int tx_n = (W + kTTX - 1) / kTTX, ty_n = (H + kTTY - 1) / kTTY;
+  const int b = blockIdx.x / (tx_n * ty_n), r = blockIdx.x % (tx_n * ty_n);
+  const int y0 = (r / tx_n) * kTTY, x0 = (r % tx_n) * kTTX;
+  load_in_tile<CI>(in, in_bf16 != 0, tile, b, H, W, y0, x0);
+  for (int i = threadIdx.x; i < CO * 9 * CI; i += blockDim.x) ws[i] = wr[woff + i];
+  __syncthreads();
+  const int ly = threadIdx.x / kTTX, lx = threadIdx.x % kTTX;
+  const int y = y0 + ly, x = x0 + lx;
+  if (y >= H || x >= W) return;
+  float acc[CO];
+#pragma unroll
+  for (int co = 0; co < CO; co++) acc[co] = wr[boff + co];
+  for (int t = 0; t < 9; t++) {
+    const float* ip = tile + ((ly + t / 3) * (kTTX + 2) + lx + t % 3) * CI;
+    for (int ci = 0; ci < CI; ci++) {
+      const float v = ip[ci];
+#pragma unroll
+      for (int co = 0; co < CO; co++) acc[co] = fmaf(ws[(co * 9 + t) * CI + ci], v, acc[co]);
+    }
+  }
+  float* op = out + (((size_t)b * H + y) * W + x) * CO;
+#pragma unroll
+  for (int co = 0; co < CO; co++) op[co] = HIDDEN ? bf16_round(fmaxf(acc[co], 0.0f)) : acc[co];
+}
+
+// dz_in(p)[ci] = [a_in(p)[ci] > 0] * sum over taps, co of wr[co][t][ci] dz_out(p - t + 1)[co]
+template <int CI, int CO>
+__global__ void __launch_bounds__(kTTX * kTTY) bwd_data_kernel(const float* dz_out, const float* wr, int woff,
+                                                             const float* a_in, float* dz_in, int H, int W) {
+  extern __shared__ float dsm[];
+  float* tile = dsm;                                   // [(kTTY + 2) * (kTTX + 2) * CO]
+  float* ws = dsm + (kTTY + 2) * (kTTX + 2) * CO;      // [CO * 9 * CI]
+  const int tx_n = (W + kTTX - 1) / kTTX, ty_n = (H + kTTY - 1) / kTTY;
+  const int b = blockIdx.x / (tx_n * ty_n), r = blockIdx.x % (tx_n * ty_n);
+  const int y0 = (r / tx_n) * kTTY, x0 = (r % tx_n) * kTTX;
+  load_in_tile<CO>(dz_out, false, tile, b, H, W, y0, x0);
+  for (int i = threadIdx.x; i < CO * 9 * CI; i += blockDim.x) ws[i] = wr[woff + i];
+  __syncthreads();
+  const int ly = threadIdx.x / kTTX, lx = threadIdx.x % kTTX;
+  const int y = y0 + ly, x = x0 + lx;
+  if (y >= H || x >= W) return;
+  float acc[CI];
+#pragma unroll
+  for (int ci = 0; ci < CI; ci++) acc[ci] = 0.0f;
+  for (int t = 0; t < 9; t++) {
+    // dz_out at p - (ky - 1, kx - 1): tile coordinates (ly + 2 - ky, lx + 2 - kx)
+    const float* dp = tile + ((ly + 2 - t / 3) * (kTTX + 2) + lx + 2 - t % 3) * CO;
+    for (int co = 0; co < CO; co++) {
+      const float g = dp[co];
+#pragma unroll
+      for (int ci = 0; ci < CI; ci++) acc[ci] = fmaf(ws[(co * 9 + t) * CI + ci], g, acc[ci]);
+    }
+  }
+  const size_t base = (((size_t)b * H + y) * W + x) * CI;
+#pragma unroll
+  for (int ci = 0; ci < CI; ci++) dz_in[base + ci] = a_in[base + ci] > 0.0f ? acc[ci] : 0.0f;
+}
+
+// Partial weight and bias gradients of one tile: part[blk][CO*9*CI + CO].
+template <int CI, int CO>
+__global__ void __launch_bounds__(256) wgrad_kernel(const float* dz, const void* a_in, int in_bf16, float* part,
+                                                  int H, int W) {
+  __shared__ float tile[(kTTY + 2) * (kTTX + 2) * CI];
+  __shared__ float dzs[kTTY * kTTX * CO];
+  const int tx_n = (W + kTTX - 1) / kTTX, ty_n = (H + kTTY - 1) / kTTY;
+  const int b = blockIdx.x / (tx_n * ty_n), r = blockIdx.x % (tx_n * ty_n);
+  const int y0 = (r / tx_n) * kTTY, x0 = (r % tx_n) * kTTX;
+  load_in_tile<CI>(a_in, in_bf16 != 0, tile, b, H, W, y0, x0);
+  for (int i = threadIdx.x; i < kTTY * kTTX * CO; i += blockDim.x) {
+    const int co = i % CO, p = i / CO;
+    const int gy = y0 + p / kTTX, gx = x0 + p % kTTX;
+    dzs[i] = (gy < H && gx < W) ? dz[(((size_t)b * H + gy) * W + gx) * CO + co] : 0.0f;
+  }
+  __syncthreads();
+  constexpr int NW = CO * 9 * CI;
+  float* out = part + (size_t)blockIdx.x * (NW + CO);
+  for (int e = threadIdx.x; e < NW + CO; e += blockDim.x) {
+    float acc = 0.0f;
+    if (e < NW) {
+      const int ci = e % CI, t = (e / CI) % 9, co = e / (9 * CI);
+      for (int p = 0; p < kTTY * kTTX; p++) {
+        const int ly = p / kTTX, lx = p % kTTX;
+        acc = fmaf(dzs[p * CO + co], tile[((ly + t / 3) * (kTTX + 2) + lx + t % 3) * CI + ci], acc);
+      }
+    } else {
+      const int co = e - NW;
+      for (int p = 0; p < kTTY * kTTX; p++) acc += dzs[p * CO + co];
+    }
+    out[e] = acc;
+  }
+}
+
+// grad[off + e] = sum over blocks of part[blk][e], in block order
+__global__ void reduce_parts_kernel(const float* part, int nblk, int n, float* grad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  float acc = 0.0f;
+  for (int k = 0; k < nblk; k++) acc += part[(size_t)k * n + e];
+  grad[e] = acc;
+}
+
+// Loss partials per block: [sum w, sum w * (softplus(z) - y z)]
+__global__ void loss_parts_kernel(const float* z, const uint8_t* lab, size_t n, float w_neg, float* part) {
+  __shared__ float sw[256], sl[256];
+  float aw = 0.0f, al = 0.0f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const uint8_t y = lab[i];
+    const float w = y == 1 ? 1.0f : (y == 0 ? w_neg : 0.0f);
+    if (w != 0.0f) {
+      const float zz = z[i];
+      const float sp = fmaxf(zz, 0.0f) + log1pf(expf(-fabsf(zz)));
+      aw += w;
+      al += w * (sp - (y == 1 ? zz : 0.0f));
+    }
+  }
+  sw[threadIdx.x] = aw;
+  sl[threadIdx.x] = al;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sw[threadIdx.x] += sw[threadIdx.x + o];
+      sl[threadIdx.x] += sl[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sw[0];
+    part[2 * blockIdx.x + 1] = sl[0];
+  }
+}
+
+__global__ void loss_final_kernel(const float* part, int nblk, float* tot, float* loss_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float sw = 0.0f, sl = 0.0f;
+  for (int k = 0; k < nblk; k++) {
+    sw += part[2 * k];
+    sl += part[2 * k + 1];
+  }
+  tot[0] = sw;
+  if (loss_out) *loss_out = sw > 0.0f ? sl / sw : 0.0f;
+}
+
+// dz4 = w (sigmoid(z) - y) / sum w
+__global__ void loss_grad_kernel(const float* z, const uint8_t* lab, size_t n, float w_neg, const float* tot,
+                                 float* dz) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t y = lab[i];
+  const float w = y == 1 ? 1.0f : (y == 0 ? w_neg : 0.0f);
+  const float zz = z[i];
+  const float e = expf(-fabsf(zz));
+  const float sig = zz >= 0.0f ? 1.0f / (1.0f + e) : e / (1.0f + e);
+  dz[i] = tot[0] > 0.0f ? w * (sig - (y == 1 ? 1.0f : 0.0f)) / tot[0] : 0.0f;
+}
+
+__global__ void adam_kernel(float* th, float* m, float* v, const float* g, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_features(const FeatureArgs& a, cudaStream_t s) {
+  count_launches(1);
+  const size_t threads = (size_t)a.W * a.H * 32;
+  features_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float* params, void* packed, cudaStream_t s) {
+  count_launches(1);
+  pack_kernel<<<(kWElems + 255) / 256, 256, 0, s>>>(params, reinterpret_cast<uint16_t*>(packed));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_infer(const InferArgs& a, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmTotal);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int ntiles = ((a.W + kTX - 1) / kTX) * ((a.H + kTY - 1) / kTY);
+  count_launches(1);
+  infer_kernel<<<(unsigned)std::min(ntiles, sms), kThreads, kSmTotal, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CI, int CO, bool HIDDEN>
+void fwd(const void* in, int in_bf16, const float* wr, int woff, int boff, float* out, int H, int W, int nblk,
+         cudaStream_t s) {
+  const size_t smem = ((size_t)(kTTY + 2) * (kTTX + 2) * CI + (size_t)CO * 9 * CI) * 4;
+  static bool set = false;
+  if (!set) {
+    cudaFuncSetAttribute(fwd_kernel<CI, CO, HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = true;
+  }
+  fwd_kernel<CI, CO, HIDDEN><<<nblk, kTTX * kTTY, smem, s>>>(in, in_bf16, wr, woff, boff, out, H, W);
+}
+
+template <int CI, int CO>
+void bwd_data(const float* dz_out, const float* wr, int woff, const float* a_in, float* dz_in, int H, int W,
+              int nblk, cudaStream_t s) {
+  const size_t smem = ((size_t)(kTTY + 2) * (kTTX + 2) * CO + (size_t)CO * 9 * CI) * 4;
+  static bool set = false;
+  if (!set) {
+    cudaFuncSetAttribute(bwd_data_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = true;
+  }
+  bwd_data_kernel<CI, CO><<<nblk, kTTX * kTTY, smem, s>>>(dz_out, wr, woff, a_in, dz_in, H, W);
+}
+
+size_t train_workspace_bytes(int B, int W, int H) {
+  const size_t npx = (size_t)B * W * H;
+  const size_t nblk = (size_t)B * ((H + kTTY - 1) / kTTY) * ((W + kTTX - 1) / kTTX);
+  size_t o = 0;
+  auto carve = [&](size_t bytes) { o = align_up(o + bytes, 256); };
+  carve(kParamCount * 4);          // rounded weights
+  carve(kParamCount * 4);          // gradient
+  carve(3 * npx * kC * 4);         // a1, a2, a3
+  carve(npx * 4);                  // z4
+  carve(2 * npx * kC * 4);         // dz ping-pong
+  carve(nblk * (9 * kC * kC + kC) * 4);   // weight-gradient partials
+  carve(2 * 1024 * 4 + 256);       // loss partials and totals
+  return o;
+}
+
+cudaError_t launch_train_step(const TrainArgs& t, cudaStream_t s) {
+  const int B = t.B, W = t.W, H = t.H;
+  const size_t npx = (size_t)B * W * H;
+  const int nblk = B * ((H + kTTY - 1) / kTTY) * ((W + kTTX - 1) / kTTX);
+  uint8_t* ws = reinterpret_cast<uint8_t*>(t.workspace);
+  size_t o = 0;
+  auto carve = [&](size_t bytes) {
+    uint8_t* p = ws + o;
+    o = align_up(o + bytes, 256);
+    return p;
+  };
+  float* wr = reinterpret_cast<float*>(carve(kParamCount * 4));
+  float* grad = reinterpret_cast<float*>(carve(kParamCount * 4));
+  float* a1 = reinterpret_cast<float*>(carve(3 * npx * kC * 4));
+  float* a2 = a1 + npx * kC;
+  float* a3 = a2 + npx * kC;
+  float* z4 = reinterpret_cast<float*>(carve(npx * 4));
+  float* dzA = reinterpret_cast<float*>(carve(2 * npx * kC * 4));
+  float* dzB = dzA + npx * kC;
+  float* part = reinterpret_cast<float*>(carve((size_t)nblk * (9 * kC * kC + kC) * 4));
+  float* lpart = reinterpret_cast<float*>(carve(2 * 1024 * 4 + 256));
+  float* ltot = lpart + 2 * 1024;
+  int launches = 0;
+  round_weights_kernel<<<(kParamCount + 255) / 256, 256, 0, s>>>(t.params, wr);
+  fwd<kF, kC, true>(t.features, 1, wr, kOffW1, kOffB1, a1, H, W, nblk, s);
+  fwd<kC, kC, true>(a1, 0, wr, kOffW2, kOffB2, a2, H, W, nblk, s);
+  fwd<kC, kC, true>(a2, 0, wr, kOffW3, kOffB3, a3, H, W, nblk, s);
+  fwd<kC, 1, false>(a3, 0, wr, kOffW4, kOffB4, z4, H, W, nblk, s);
+  launches += 5;
+  if (t.logits_out) {
+    cudaError_t e = cudaMemcpyAsync(t.logits_out, z4, npx * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (!t.labels) {
+    count_launches(launches);
+    return cudaGetLastError();
+  }
+  const int lblk = (int)std::min<size_t>(1024, (npx + 255) / 256);
+  loss_parts_kernel<<<lblk, 256, 0, s>>>(z4, t.labels, npx, t.w_neg, lpart);
+  loss_final_kernel<<<1, 32, 0, s>>>(lpart, lblk, ltot, t.loss_out);
+  loss_grad_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, s>>>(z4, t.labels, npx, t.w_neg, ltot, dzA);
+  launches += 3;
+  // layer 4 (CI = 32, CO = 1)
+  wgrad_kernel<kC, 1><<<nblk, 256, 0, s>>>(dzA, a3, 0, part, H, W);
+  reduce_parts_kernel<<<(9 * kC + 1 + 255) / 256, 256, 0, s>>>(part, nblk, 9 * kC + 1, grad + kOffW4);
+  bwd_data<kC, 1>(dzA, wr, kOffW4, a3, dzB, H, W, nblk, s);
+  // layer 3
+  wgrad_kernel<kC, kC><<<nblk, 256, 0, s>>>(dzB, a2, 0, part, H, W);
+  reduce_parts_kernel<<<(9 * kC * kC + kC + 255) / 256, 256, 0, s>>>(part, nblk, 9 * kC * kC + kC, grad + kOffW3);
+  bwd_data<kC, kC>(dzB, wr, kOffW3, a2, dzA, H, W, nblk, s);
+  // layer 2
+  wgrad_kernel<kC, kC><<<nblk, 256, 0, s>>>(dzA, a1, 0, part, H, W);
+  reduce_parts_kernel<<<(9 * kC * kC + kC + 255) / 256, 256, 0, s>>>(part, nblk, 9 * kC * kC + kC, grad + kOffW2);
+  bwd_data<kC, kC>(dzA, wr, kOffW2, a1, dzB, H, W, nblk, s);
+  // layer 1
+  wgrad_kernel<kF, kC><<<nblk, 256, 0, s>>>(dzB, t.features, 1, part, H, W);
+  reduce_parts_kernel<<<(9 * kF * kC + kC + 255) / 256, 256, 0, s>>>(part, nblk, 9 * kF * kC + kC, grad + kOffW1);
+  launches += 11;
+  if (t.grad_out) {
+    cudaError_t e = cudaMemcpyAsync(t.grad_out, grad, kParamCount * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (t.adam_m && t.adam_v) {
+    const float c1 = 1.0f - powf(t.beta1, (float)t.step), c2 = 1.0f - powf(t.beta2, (float)t.step);
+    adam_kernel<<<(kParamCount + 255) / 256, 256, 0, s>>>(t.params, t.adam_m, t.adam_v, grad, kParamCount, t.lr,
+                                                          t.beta1, t.beta2, t.eps, c1, c2);
+    launches += 1;
+  }
+  count_launches(launches);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* params, float* m, float* v, const float* grad, int n, float lr, float beta1,
+                        float beta2, float eps, int step, cudaStream_t s) {
+  const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+  count_launches(1);
+  adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(params, m, v, grad, n, lr, beta1, beta2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace confnet
+}  // namespace sf

@@ -79,6 +79,9 @@ constexpr size_t kCostPairSmemMax = 227u * 1024u;
 
 cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
                              int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s);
+// left-reference volume only (x-tiled, one POPC per distance)
+cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
+                             int cmax, uint8_t* CL, cudaStream_t s);
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs& a, bool up, cudaStream_t s);
 

@@ -858,6 +858,15 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
 
 }  // namespace
 
+cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
+                             int cmax, uint8_t* CL, cudaStream_t s) {
+  StageTrace trace(SF_STAGE_COST, s);
+  count_launches(1);
+  dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
+  cost_tiled_kernel<<<grid, 256, 0, s>>>(cL, cR, W, H, D, Dp, cmax, 0, CL);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
                              int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
