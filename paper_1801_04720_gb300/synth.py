@@ -380,3 +380,13 @@ def confnet_init(seed, layers):
         parts.append(rng.normal(0.0, np.sqrt(2.0 / (9 * ci)), size=9 * ci * co))
         parts.append(np.zeros(co))
     return np.concatenate(parts).astype(np.float32)
+
+
+def confidence_recipe(seed, W=1242, H=375, D=128, n_planes=6):
+    """Scenes for training and evaluating the learned confidence: the
+    fronto-parallel plane recipe rendered at W x H with n_planes rectangles at
+    seeded disparities in [2, D - 5]."""
+    rng = np.random.default_rng(2_000_003 + seed)
+    disparities = sorted(int(v) for v in rng.integers(2, max(3, min(D - 4, W // 4)), size=n_planes))
+    return fronto_planes(W=W, H=H, D=D, disparities=disparities, seed=seed, f=721.5, B=0.54,
+                         max_shift=8, bg_disp=1, size_frac=(0.12, 0.3))
