@@ -35,6 +35,9 @@ def parse():
                     help="keep the built-in sweep shape instead of the tuned one")
     ap.add_argument("--batch", type=int, default=64,
                     help="quadruples in the uneven-batch measurement (0 = skip)")
+    ap.add_argument("--learned-eval", type=int, default=200,
+                    help="held-out scenes for the learned path's false-accept rate "
+                         "(0 = timing only, -1 = skip the learned path)")
     ap.add_argument("--profile", action="store_true",
                     help="short run for ncu: no clock-sampling load phase, no e2e, no CPU baseline")
     args = ap.parse_args()
@@ -43,6 +46,7 @@ def parse():
         args.no_cpu_baseline = True
         args.batch = 0
         args.no_autotune = True
+        args.learned_eval = -1
     return args
 
 
@@ -276,6 +280,9 @@ def run_ours(args, world, rank, local):
     }
     if args.batch > 0:
         result["batch"] = run_batch(args, dev, _lib, synth, torch)
+    if args.learned_eval >= 0:
+        result["learned"] = run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush,
+                                        result["value"])
     return result, q
 
 
@@ -320,6 +327,61 @@ def run_batch(args, dev, _lib, synth, torch):
             "megapixels_per_step": round(pixels / 1e6, 3),
             "workspace_gb": round(ws.numel() / 1e9, 2), "graph": True,
             "sizes": sorted({f"{q.shape[1]}x{q.shape[0]}/D{q.D}" for q in quads})}
+
+
+def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps):
+    """The same frame with learned confidence in place of both left-right
+    checks (two SGM passes + features + network + combination), and its
+    false-accept / false-reject rates against the plain check: on this frame
+    and on the held-out plane-recipe scenes at 1242x375, D=128."""
+    from paper_1801_04720_gb300 import train_confnet
+    theta, meta = train_confnet.load()
+    params_t = torch.from_numpy(theta).to(dev)
+    packed = _lib.confnet_pack(params_t)
+    thr = float(meta["threshold"])
+    H, W = q.shape
+    ws = _lib.learned_workspace(W, H, p, 2, dev)
+    out = _lib.alloc_scene_flow_outputs(W, H, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        _lib.sf_scene_flow_learned(imgs, flow, p, cam, packed, thr, ws=ws, out=out, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    tracer = _lib.StageTracer(n_records=64 * args.steps)
+    launches0 = _lib.kernel_launches()
+    with tracer:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    launches = _lib.kernel_launches() - launches0
+    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    stages = {k: round(sum(v) / args.steps, 5) for k, v in tracer.durations().items()}
+    # accuracy against the plain check on this frame (pair at t)
+    plain = _lib.sf_sgm_full(imgs[0], imgs[1], p)
+    lo = _lib.sf_sgm_learned(imgs[0], imgs[1], p, packed=packed, threshold=thr)
+    frame_rates = train_confnet.rates([(lo["prob"], lo["dint"], plain["valid"])], thr)
+    res = {"metric": "scene-flow frames/s, learned confidence in place of the L-R check",
+           "value": round(1000.0 / ms, 2), "unit": "frames/s", "ms_per_step": round(ms, 4),
+           "vs_plain": round(1000.0 / ms / plain_fps, 3), "threshold": thr,
+           "gpu_launches": int(launches), "stages_ms_per_step": stages,
+           "automotive_frame": {k: round(v, 5) for k, v in frame_rates.items()}}
+    n_eval = min(args.learned_eval, len(train_confnet.EVAL_SEEDS))
+    if n_eval > 0:
+        seeds = list(train_confnet.EVAL_SEEDS)[:n_eval]
+        pairs = train_confnet.render_pairs(seeds, W, H, D_MAX)
+        ev = train_confnet.rates(train_confnet.decisions(_lib, packed, pairs, D_MAX), thr)
+        res["eval"] = {"scenes": n_eval, "seeds": [seeds[0], seeds[-1]],
+                       "recipe": "fronto-parallel plane recipe at 1242x375, D=128",
+                       **{k: round(v, 5) for k, v in ev.items()}}
+    return res
 
 
 def cpu_baseline(q):
