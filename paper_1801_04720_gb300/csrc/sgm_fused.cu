@@ -32,9 +32,8 @@
 
 // Sweep shapes this build provides: (disparities per thread, chunks, halo).
 #define SF_SWEEP_SHAPES(X)                                                                   \
-  X(8, 1, 16) X(8, 2, 16) X(8, 4, 16) X(8, 8, 16) X(8, 16, 16) X(8, 1, 8) X(8, 2, 8)      \
-  X(8, 4, 8) X(8, 8, 8) X(8, 16, 8) X(16, 4, 8) X(16, 8, 8) X(16, 16, 8) X(16, 4, 16)     \
-  X(16, 8, 16)
+  X(8, 2, 16) X(8, 4, 16) X(8, 8, 16) X(8, 16, 16) X(8, 2, 8) X(8, 4, 8) X(8, 8, 8)        \
+  X(8, 16, 8) X(16, 4, 8) X(16, 8, 8) X(16, 16, 8) X(16, 4, 16) X(16, 8, 16)
 
 
 namespace sf {
@@ -424,12 +423,17 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
   const bool en_v = (a.path_mask >> (UP ? 3 : 2)) & 1u;
   const bool en_fl = (a.path_mask >> (UP ? 6 : 4)) & 1u;
   const bool en_fr = (a.path_mask >> (UP ? 5 : 7)) & 1u;
-  // lanes of owned pairs in this warp (owned and halo pairs share a warp
-  // only when CHUNKS == 1)
-  const unsigned own_mask = __ballot_sync(0xffffffffu, owned);
+  static_assert(CHUNKS >= 2, "owned pairs fill whole warps");
   constexpr int HH = HALO / 2;             // pairs per halo side
   constexpr int LH0 = 16, RH0 = 16 + HH;    // first left / right halo pair
   const int role = owned ? 0 : (pr < RH0 ? 1 : 2);   // 0 owned, 1 left halo, 2 right halo
+  // lanes of this thread's role in its warp: owned pairs fill whole warps;
+  // a warp may hold pairs of both halo sides (whole pairs of CHUNKS lanes),
+  // and each side runs its own code with its own shuffles
+  const unsigned role_mask = __ballot_sync(0xffffffffu, owned) * (role == 0) +
+                             __ballot_sync(0xffffffffu, role == 1) * (role == 1) +
+                             __ballot_sync(0xffffffffu, role == 2) * (role == 2);
+  const bool en_all = en_v && en_fl && en_fr;
   const int hh = role == 1 ? pr - LH0 : pr - RH0;
   // hand-over sources: FL from column x-1, FR from column x+1.  Whole
   // registers move between pairs except at the seams of the layout, where
@@ -485,6 +489,9 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       xhi = x0 + kTW + HH + hh;
     }
     const bool lo_in = live && xlo >= 0 && xlo < W, hi_in = live && xhi >= 0 && xhi < W;
+    // this thread's S_down tiles (down sweep): row y at sd_out + y * sd_row
+    uint4* const sd_out = reinterpret_cast<uint4*>(pd.sdown) + ((size_t)(j * 16 + pr) * CHUNKS + q) * G;
+    const size_t sd_row = (size_t)J * 16 * CHUNKS * G;
     // ---- prefetch ring: the first rows' inputs are requested before the
     // neighbour wait (they do not depend on it) ----
     auto issue_row = [&](int r) {
@@ -562,32 +569,27 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
             if (d0 + i >= D) r[i] = (have ? kPadCost2 : 0u) & keep;
         }
       };
-      if (owned) {
+#pragma unroll
+      for (int i = 0; i < DC; i++) Lv[i] = Lf[i] = Lr[i] = 0;
+      if (role == 0) {
         load_pair(bsv, xlo, xhi, Lv, 0xffffffffu);
+        load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
+        load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
+        const uint32_t av = group_min2<CHUNKS>(tree_min<DC>(Lv), role_mask);
+        const uint32_t af = group_min2<CHUNKS>(tree_min<DC>(Lf), role_mask);
+        const uint32_t ar = group_min2<CHUNKS>(tree_min<DC>(Lr), role_mask);
+        mv = have ? av : 0u;
+        mf = have ? (af & fl_keep) : 0u;
+        mr = have ? (ar & fr_keep) : 0u;
+      } else if (role == 1) {
+        load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
+        const uint32_t af = group_min2<CHUNKS>(tree_min<DC>(Lf), role_mask);
+        mf = have ? (af & fl_keep) : 0u;
       } else {
-#pragma unroll
-        for (int i = 0; i < DC; i++) Lv[i] = 0;
+        load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
+        const uint32_t ar = group_min2<CHUNKS>(tree_min<DC>(Lr), role_mask);
+        mr = have ? (ar & fr_keep) : 0u;
       }
-      if (role != 2) load_pair(bsl, xlo - 1, xhi - 1, Lf, fl_keep);
-      else {
-#pragma unroll
-        for (int i = 0; i < DC; i++) Lf[i] = 0;
-      }
-      if (role != 1) load_pair(bsr, xlo + 1, xhi + 1, Lr, fr_keep);
-      else {
-#pragma unroll
-        for (int i = 0; i < DC; i++) Lr[i] = 0;
-      }
-      uint32_t av = tree_min<DC>(Lv), af = tree_min<DC>(Lf), ar = tree_min<DC>(Lr);
-#pragma unroll
-      for (int o = 1; o < CHUNKS; o <<= 1) {
-        av = vmin2(av, __shfl_xor_sync(0xffffffffu, av, o, CHUNKS));
-        af = vmin2(af, __shfl_xor_sync(0xffffffffu, af, o, CHUNKS));
-        ar = vmin2(ar, __shfl_xor_sync(0xffffffffu, ar, o, CHUNKS));
-      }
-      mv = have ? av : 0u;
-      mf = have ? (af & fl_keep) : 0u;
-      mr = have ? (ar & fr_keep) : 0u;
     }
 
     // winner-take-all + parabolic subpixel of row kk, done by halo threads
@@ -638,6 +640,15 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       }
     };
 
+    // neighbour disparities d0-1 and d0+DC of one path: from the adjacent
+    // chunks of the pair, or the end values (nothing beyond d = 0 / Dp-1)
+    auto neighbours = [&](const uint32_t* L, bool fresh, uint32_t keep, uint32_t& lo, uint32_t& hi) {
+      lo = __shfl_up_sync(role_mask, L[DC - 1], 1, CHUNKS);
+      hi = __shfl_down_sync(role_mask, L[0], 1, CHUNKS);
+      if (q == 0) lo = fresh ? 0u : (kInf2 & keep);
+      if (q == CHUNKS - 1) hi = fresh ? 0u : (kInf2 & keep);
+    };
+
     for (int k = 0; k < nrows; k++) {
       const int y = UP ? ytop + nrows - 1 - k : ytop + k;
       issue_row(k + RING - 1);
@@ -653,68 +664,41 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       }
       const int par = k & 1;
       const bool fresh = (bi == 0 && k == 0);
-      // ---- neighbour disparities d0-1 and d0+DC of all three paths ----
-      uint32_t lv = __shfl_up_sync(0xffffffffu, Lv[DC - 1], 1, CHUNKS);
-      uint32_t rv = __shfl_down_sync(0xffffffffu, Lv[0], 1, CHUNKS);
-      uint32_t lf = __shfl_up_sync(0xffffffffu, Lf[DC - 1], 1, CHUNKS);
-      uint32_t rf = __shfl_down_sync(0xffffffffu, Lf[0], 1, CHUNKS);
-      uint32_t lr = __shfl_up_sync(0xffffffffu, Lr[DC - 1], 1, CHUNKS);
-      uint32_t rr = __shfl_down_sync(0xffffffffu, Lr[0], 1, CHUNKS);
-      if (q == 0) {
-        lv = fresh ? 0u : kInf2;
-        lf = fresh ? 0u : (kInf2 & fl_keep);
-        lr = fresh ? 0u : (kInf2 & fr_keep);
-      }
-      if (q == CHUNKS - 1) {
-        rv = fresh ? 0u : kInf2;
-        rf = fresh ? 0u : (kInf2 & fl_keep);
-        rr = fresh ? 0u : (kInf2 & fr_keep);
-      }
-      // ---- all three paths ----
-      uint32_t Nv[DC], Nf[DC], Nr[DC];
-      // a halo pair works while one of its columns can still reach the strip
-      const bool act_fl = role == 0 || (role == 1 && hh + HH >= k);
-      const bool act_fr = role == 0 || (role == 2 && hh <= HALO - 1 - k);
-      if (owned) sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2x2, Nv);
-      if (act_fl) sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
-      else {
-#pragma unroll
-        for (int i = 0; i < DC; i++) Nf[i] = Lf[i];
-      }
-      if (act_fr) sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
-      else {
-#pragma unroll
-        for (int i = 0; i < DC; i++) Nr[i] = Lr[i];
-      }
-      uint32_t av = owned ? tree_min<DC>(Nv) : 0u;
-      uint32_t af = act_fl ? tree_min<DC>(Nf) : 0u, ar = act_fr ? tree_min<DC>(Nr) : 0u;
-#pragma unroll
-      for (int o = 1; o < CHUNKS; o <<= 1) {
-        av = vmin2(av, __shfl_xor_sync(0xffffffffu, av, o, CHUNKS));
-        af = vmin2(af, __shfl_xor_sync(0xffffffffu, af, o, CHUNKS));
-        ar = vmin2(ar, __shfl_xor_sync(0xffffffffu, ar, o, CHUNKS));
-      }
-      mv = av;
-      mf = af;
-      mr = ar;
-      // ---- diagonal hand-over to the next row (written early) ----
-      if (k + 1 < nrows) {
-        if (role != 2) store_u4<DC>(xfl + par * G * NT + t, NT, Nf);
-        if (role != 1) store_u4<DC>(xfr + par * G * NT + t, NT, Nr);
-        if (q == 0) {
-          mfl[par * NP + pr] = mf;
-          mfr[par * NP + pr] = mr;
+      const bool more = k + 1 < nrows;
+      if (role == 0) {
+        // ---- owned pairs: all three paths ----
+        uint32_t Nv[DC], Nf[DC], Nr[DC];
+        uint32_t lv, rv, lf, rf, lr, rr;
+        neighbours(Lv, fresh, 0xffffffffu, lv, rv);
+        neighbours(Lf, fresh, fl_keep, lf, rf);
+        neighbours(Lr, fresh, fr_keep, lr, rr);
+        sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2x2, Nv);
+        sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
+        sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+        mv = group_min2<CHUNKS>(tree_min<DC>(Nv), role_mask);
+        mf = group_min2<CHUNKS>(tree_min<DC>(Nf), role_mask);
+        mr = group_min2<CHUNKS>(tree_min<DC>(Nr), role_mask);
+        // diagonal hand-over to the next row (written early)
+        if (more) {
+          store_u4<DC>(xfl + par * G * NT + t, NT, Nf);
+          store_u4<DC>(xfr + par * G * NT + t, NT, Nr);
+          if (q == 0) {
+            mfl[par * NP + pr] = mf;
+            mfr[par * NP + pr] = mr;
+          }
         }
-      }
-      // ---- accumulate and emit (owned pairs) ----
-      if (owned) {
+        // ---- accumulate and emit ----
         uint32_t S[DC];
+        if (en_all) {
 #pragma unroll
-        for (int i = 0; i < DC; i++)
-          S[i] = (en_v ? Nv[i] : 0u) + (en_fl ? Nf[i] : 0u) + (en_fr ? Nr[i] : 0u);
+          for (int i = 0; i < DC; i++) S[i] = Nv[i] + Nf[i] + Nr[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < DC; i++)
+            S[i] = (en_v ? Nv[i] : 0u) + (en_fl ? Nf[i] : 0u) + (en_fr ? Nr[i] : 0u);
+        }
         if (!UP) {
-          const size_t tile = ((((size_t)y) * J + j) * 16 + pr) * CHUNKS + q;
-          store_u4<DC>(reinterpret_cast<uint4*>(pd.sdown) + tile * G, 1, S);
+          store_u4<DC>(sd_out + (size_t)y * sd_row, 1, S);
         } else {
           // add the down sweep and the horizontal paths
           uint32_t sdv[DC], hf[DC], hb[DC];
@@ -746,7 +730,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
             store_u4<DC>(srow + (k & 1) * G * NO + t, NO, S);
           } else if (pd.dint) {
             // winner-take-all: the smallest d with the minimal S, per lane
-            const uint32_t gmin = group_min2<CHUNKS>(tree_min<DC>(S), own_mask);
+            const uint32_t gmin = group_min2<CHUNKS>(tree_min<DC>(S), role_mask);
             uint32_t first = 0xffffffffu;
 #pragma unroll
             for (int i = DC - 1; i >= 0; i--) {
@@ -755,42 +739,40 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
               const uint32_t eq = ((x2 & 0xffffu) ? 0u : 0x0000ffffu) | ((x2 >> 16) ? 0u : 0xffff0000u);
               first = (first & ~eq) | (d2 & eq);
             }
-            const uint32_t dstar2 = group_min2<CHUNKS>(first, own_mask);
+            const uint32_t dstar2 = group_min2<CHUNKS>(first, role_mask);
             // S(d*-1) and S(d*+1) through shared memory, [group][thread];
             // chunk 0 finishes the low lane's column, chunk 1 the high one
             store_u4<DC>(srow + t, NO, S);
-            __syncwarp(own_mask);
-            const int lane = CHUNKS == 1 ? -1 : q;
-            for (int l = 0; l < 2; l++) {
-              if (!(lane == l || (CHUNKS == 1 && q == 0))) continue;
+            __syncwarp(role_mask);
+            if (q < 2) {
+              const int l = q;
               const int x = l ? xhi : xlo;
-              if (x < 0 || x >= W) continue;
-              const int sh = 16 * l;
-              const int ds = (dstar2 >> sh) & 0xffff;
-              const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow);
-              auto s_at = [&](int d) {   // S at disparity d of this pair
-                const int qq = d / DC, ii = d - qq * DC;
-                return (sw[((ii >> 2) * NO + pr * CHUNKS + qq) * 4 + (ii & 3)] >> sh) & 0xffffu;
-              };
-              float v = (float)ds;
-              if (a.subpixel && ds > 0 && ds < D - 1) {
-                const int sv = (int)s_at(ds);
-                const int am = (int)s_at(ds - 1) - sv;
-                const int bp = (int)s_at(ds + 1) - sv;
-                v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+              if (x >= 0 && x < W) {
+                const int sh = 16 * l;
+                const int ds = (dstar2 >> sh) & 0xffff;
+                const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow);
+                auto s_at = [&](int d) {   // S at disparity d of this pair
+                  const int qq = d / DC, ii = d - qq * DC;
+                  return (sw[((ii >> 2) * NO + pr * CHUNKS + qq) * 4 + (ii & 3)] >> sh) & 0xffffu;
+                };
+                float v = (float)ds;
+                if (a.subpixel && ds > 0 && ds < D - 1) {
+                  const int sv = (int)s_at(ds);
+                  const int am = (int)s_at(ds - 1) - sv;
+                  const int bp = (int)s_at(ds + 1) - sv;
+                  v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+                }
+                pd.dint[(size_t)y * W + x] = (int16_t)ds;
+                if (pd.dsub) pd.dsub[(size_t)y * W + x] = v;
               }
-              pd.dint[(size_t)y * W + x] = (int16_t)ds;
-              if (pd.dsub) pd.dsub[(size_t)y * W + x] = v;
             }
-            __syncwarp(own_mask);
+            __syncwarp(role_mask);
           }
         }
 #pragma unroll
         for (int i = 0; i < DC; i++) Lv[i] = Nv[i];
-      }
-      if (k + 1 == nrows) {
-        // band end: publish the states of the owned columns
-        if (owned) {
+        if (!more) {
+          // band end: publish the states of the owned columns
           V va, vb;
           pairs_to_bytes<DC>(Nv, va, vb);
           if (lo_in) *reinterpret_cast<V*>(wsv + (size_t)xlo * Dp + d0) = va;
@@ -802,8 +784,43 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
           if (lo_in) *reinterpret_cast<V*>(wsr + (size_t)xlo * Dp + d0) = va;
           if (hi_in) *reinterpret_cast<V*>(wsr + (size_t)xhi * Dp + d0) = vb;
         }
-        break;
+      } else if (role == 1) {
+        // ---- left halo: the path entering from x-1 only, while one of the
+        // pair's columns can still reach the strip ----
+        if (more) {
+          uint32_t Nf[DC];
+          uint32_t lf, rf;
+          neighbours(Lf, fresh, fl_keep, lf, rf);
+          const bool act = hh + HH >= k;
+          if (act) {
+            sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
+          } else {
+#pragma unroll
+            for (int i = 0; i < DC; i++) Nf[i] = Lf[i];
+          }
+          mf = group_min2<CHUNKS>(act ? tree_min<DC>(Nf) : 0u, role_mask);
+          store_u4<DC>(xfl + par * G * NT + t, NT, Nf);
+          if (q == 0) mfl[par * NP + pr] = mf;
+        }
+      } else {
+        // ---- right halo: the path entering from x+1 only ----
+        if (more) {
+          uint32_t Nr[DC];
+          uint32_t lr, rr;
+          neighbours(Lr, fresh, fr_keep, lr, rr);
+          const bool act = hh <= HALO - 1 - k;
+          if (act) {
+            sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+          } else {
+#pragma unroll
+            for (int i = 0; i < DC; i++) Nr[i] = Lr[i];
+          }
+          mr = group_min2<CHUNKS>(act ? tree_min<DC>(Nr) : 0u, role_mask);
+          store_u4<DC>(xfr + par * G * NT + t, NT, Nr);
+          if (q == 0) mfr[par * NP + pr] = mr;
+        }
       }
+      if (!more) break;
       __syncthreads();
       if (role != 2) {
         const uint4* b = xfl + par * G * NT;
@@ -909,7 +926,6 @@ cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
     }
   }
   switch (sh.chunks) {
-    case 1: return hline_dispatch<8, 1>(a, s);
     case 2: return hline_dispatch<8, 2>(a, s);
     case 4: return hline_dispatch<8, 4>(a, s);
     case 8: return hline_dispatch<8, 8>(a, s);
@@ -926,11 +942,18 @@ ShapeOverride g_over[16];
 int g_nover = 0;
 }  // namespace
 
+// chunks of dc disparities covering D, at least two (owned pairs then fill
+// whole warps)
+static int chunks_for(int dc, int D) {
+  int c = 2;
+  while (c * dc < D) c <<= 1;
+  return c;
+}
+
 static Shape builtin_shape(int D) {
   Shape s;
   s.dc = D > 128 ? 16 : 8;
-  s.chunks = 1;
-  while (s.chunks * s.dc < D) s.chunks <<= 1;
+  s.chunks = chunks_for(s.dc, D);
   s.halo = s.dc == 8 ? 16 : 8;
   return s;
 }
@@ -949,8 +972,7 @@ Shape shape_for(int D) {
       Shape s;
       s.dc = g_over[i].dc;
       s.halo = g_over[i].halo;
-      s.chunks = 1;
-      while (s.chunks * s.dc < D) s.chunks <<= 1;
+      s.chunks = chunks_for(s.dc, D);
       return s;
     }
   }
@@ -966,11 +988,8 @@ int set_shape_override(int d_lo, int d_hi, int dc, int halo) {
     g_nover = w;
     return 0;
   }
-  for (int D = d_lo; D <= d_hi; D++) {
-    int chunks = 1;
-    while (chunks * dc < D) chunks <<= 1;
-    if (!shape_supported(dc, chunks, halo)) return 1;
-  }
+  for (int D = d_lo; D <= d_hi; D++)
+    if (!shape_supported(dc, chunks_for(dc, D), halo)) return 1;
   if (g_nover == 16) return 1;
   g_over[g_nover++] = {d_lo, d_hi, dc, halo};
   return 0;
