@@ -388,10 +388,16 @@ struct SweepCfg {
   }
 };
 
-// Registers are capped so that a 512-thread sweep CTA leaves room on its SM
-// for the horizontal-path blocks that run beside it.
+// Registers are capped at 48K per CTA (at most 168 a thread) so that a sweep
+// CTA leaves room on its SM for the horizontal-path blocks beside it; the
+// 16-disparity shapes keep 168 (they run one CTA per SM).
+constexpr int sweep_max_regs(int nt) {
+  return (49152 / nt) > 168 ? 168 : ((49152 / nt) / 8) * 8;
+}
+
 template <int DC, int CHUNKS, int HALO, bool UP>
-__global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ? 96 : 168)
+__global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
+    __maxnreg__(DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
   using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
   using V = typename ByteVec<DC>::T;
@@ -503,8 +509,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
       cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : pd.cost, ok && hi_in);
       if (UP && owned) {
         uint4* xs = ringx + (r % RING) * XW * NO + t;
-        const size_t tile = ((((size_t)(ok ? yy : 0)) * J + j) * 16 + pr) * CHUNKS + q;
-        const uint4* sd = reinterpret_cast<const uint4*>(pd.sdown) + tile * G;
+        const uint4* sd = sd_out + (ok ? (size_t)yy * sd_row : 0);
 #pragma unroll
         for (int w = 0; w < G; w++) cp_async<16>(xs + w * NO, sd + w, ok);
         const size_t ol = ((size_t)yy * W + xlo) * Dp + d0, oh = ((size_t)yy * W + xhi) * Dp + d0;
@@ -641,12 +646,15 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
     };
 
     // neighbour disparities d0-1 and d0+DC of one path: from the adjacent
-    // chunks of the pair, or the end values (nothing beyond d = 0 / Dp-1)
-    auto neighbours = [&](const uint32_t* L, bool fresh, uint32_t keep, uint32_t& lo, uint32_t& hi) {
+    // chunks of the pair, or "none" (kInf2) past d = 0 and d = Dp-1.  A lane
+    // without a predecessor (first row, or its column just entered the
+    // image) has L = 0 and m = 0, so its update is C whatever these values.
+    const bool q_first = q == 0, q_last = q == CHUNKS - 1;
+    auto neighbours = [&](const uint32_t* L, uint32_t& lo, uint32_t& hi) {
       lo = __shfl_up_sync(role_mask, L[DC - 1], 1, CHUNKS);
       hi = __shfl_down_sync(role_mask, L[0], 1, CHUNKS);
-      if (q == 0) lo = fresh ? 0u : (kInf2 & keep);
-      if (q == CHUNKS - 1) hi = fresh ? 0u : (kInf2 & keep);
+      if (q_first) lo = kInf2;
+      if (q_last) hi = kInf2;
     };
 
     for (int k = 0; k < nrows; k++) {
@@ -663,15 +671,14 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
           if (d0 + i >= D) Cc[i] = kPadCost2;
       }
       const int par = k & 1;
-      const bool fresh = (bi == 0 && k == 0);
       const bool more = k + 1 < nrows;
       if (role == 0) {
         // ---- owned pairs: all three paths ----
         uint32_t Nv[DC], Nf[DC], Nr[DC];
         uint32_t lv, rv, lf, rf, lr, rr;
-        neighbours(Lv, fresh, 0xffffffffu, lv, rv);
-        neighbours(Lf, fresh, fl_keep, lf, rf);
-        neighbours(Lr, fresh, fr_keep, lr, rr);
+        neighbours(Lv, lv, rv);
+        neighbours(Lf, lf, rf);
+        neighbours(Lr, lr, rr);
         sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2x2, Nv);
         sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
         sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
@@ -790,7 +797,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         if (more) {
           uint32_t Nf[DC];
           uint32_t lf, rf;
-          neighbours(Lf, fresh, fl_keep, lf, rf);
+          neighbours(Lf, lf, rf);
           const bool act = hh + HH >= k;
           if (act) {
             sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
@@ -807,7 +814,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1) __maxnreg__(DC == 8 ?
         if (more) {
           uint32_t Nr[DC];
           uint32_t lr, rr;
-          neighbours(Lr, fresh, fr_keep, lr, rr);
+          neighbours(Lr, lr, rr);
           const bool act = hh <= HALO - 1 - k;
           if (act) {
             sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
