@@ -323,12 +323,14 @@ TaskTables build_tables(const fused::PassDesc* d, int npass) {
 sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass, int Dshape,
                      const fused::PassDesc* d_dev_down, const fused::PassDesc* d_dev_up,
                      const int* tab_dev, const TaskTables* tt, int* counters, int* err,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool tuned = true) {
   const bool inl = d_dev_down == nullptr;
   fused::HLineArgs ha{};
   ha.P1 = p->P1; ha.P2 = p->P2; ha.Dmax = Dshape; ha.npass = npass; ha.path_mask = p->path_mask;
+  ha.builtin_shape = tuned ? 0 : 1;
   ha.err = err;
   fused::SweepArgs sa{};
+  sa.builtin_shape = tuned ? 0 : 1;
   sa.P1 = p->P1; sa.P2 = p->P2; sa.subpixel = p->subpixel; sa.Dmax = Dshape; sa.npass = npass;
   sa.path_mask = p->path_mask;
   sa.en_h0 = (p->path_mask >> 0) & 1u;
@@ -1099,7 +1101,7 @@ struct LearnedPlan {
       b.cost = carve(N * Dp);
       b.hf = carve(N * Dp);
       b.hb = carve(N * Dp);
-      b.sdown = carve(fused::sdown_bytes(W, H, D));
+      b.sdown = carve(fused::sdown_bytes(W, H, D, false));
       b.bs = carve(fused::bs_bytes(W, D));
       b.S = carve(N * D * sizeof(uint16_t));
       b.feat = carve(N * 16);
@@ -1141,7 +1143,7 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
     fused::PassDesc& pd = d[k];
     pd = fused::PassDesc{};
     pd.W = W; pd.H = H; pd.D = D; pd.Dp = Dp; pd.J = J;
-    pd.nb = (H + fused::band_rows(D) - 1) / fused::band_rows(D);
+    pd.nb = (H + fused::band_rows(D, false) - 1) / fused::band_rows(D, false);
     pd.cost = ws + b.cost;
     pd.hfwd = ws + b.hf;
     pd.hbwd = ws + b.hb;
@@ -1153,10 +1155,13 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
     pd.dsub = nullptr;
     pd.S = reinterpret_cast<uint16_t*>(ws + b.S);
   }
+  // the learned path's two passes keep the built-in sweep shape (tuned
+  // overrides are measured on the four passes of the plain frame)
   sf_status st = run_sweeps(p, d, npairs, D, nullptr, nullptr, nullptr, nullptr,
-                            reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s);
+                            reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s,
+                            false);
   if (st != SF_OK) return st;
-  const fused::Shape shape = fused::shape_for(D);
+  const fused::Shape shape = fused::shape_for(D, false);
   for (int k = 0; k < npairs; k++) {
     const LearnedPair& b = plan.pr[k];
     confnet::FeatureArgs fa{};

@@ -45,73 +45,62 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int kMaxPerLane = SF_MAX_DISPARITY / 32;
 
-__global__ void __launch_bounds__(256)
-    features_kernel(FeatureArgs a) {
-  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (warp >= a.W * a.H) return;
-  const int y = warp / a.W, x = warp - y * a.W;
-  const size_t pix = (size_t)y * a.W + x;
-  const uint16_t* srow = a.S + pix * a.D;
-  const uint8_t* hf = a.hfwd + pix * a.Dp;
-  const uint8_t* hb = a.hbwd + pix * a.Dp;
-  // partial sum of the three downward paths, tile layout of the band sweeps
-  const int j = x >> 5, c = x & 31, pr = c & 15, hi = c >> 4;
-  const uint32_t* sd = a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape;
+__device__ __forceinline__ uint32_t warp_min(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFullMask, v, o));
+  return v;
+}
+
+// One pixel's curve, spread over the warp: lane l holds d = l + 32 k.
+struct Curve {
   uint32_t s[kMaxPerLane];
-  uint32_t ks = 0xffffffffu, kh = 0xffffffffu, kd = 0xffffffffu, ku = 0xffffffffu;
+  uint32_t ks, kh, kd, ku;     // (value << 8 | d) minima: S, horizontal, downward, upward
+};
+
+// Features, winner and subpixel winner of one pixel; every lane takes part,
+// lane `out_lane` writes.
+__device__ __forceinline__ void finish_pixel(const FeatureArgs& a, Curve& c, int x, size_t pix, int lane,
+                                             int out_lane) {
+  c.ks = warp_min(c.ks);
+  c.kh = warp_min(c.kh);
+  c.kd = warp_min(c.kd);
+  c.ku = warp_min(c.ku);
+  const int ds = (int)(c.ks & 0xffu);
+  const uint32_t s0 = c.ks >> 8;
+  uint32_t far = 0xffffffffu, vm = 0u, vp = 0u;
 #pragma unroll
   for (int k = 0; k < kMaxPerLane; k++) {
     const int d = lane + 32 * k;
-    s[k] = 0xffffffffu;
     if (d < a.D) {
-      const uint32_t sv = srow[d];
-      const uint32_t gh = (uint32_t)hf[d] + (uint32_t)hb[d];
-      const uint32_t w = sd[d];
-      const uint32_t gd = hi ? (w >> 16) : (w & 0xffffu);
-      const uint32_t gu = sv - gh - gd;
-      s[k] = sv;
-      ks = min(ks, (sv << 8) | (uint32_t)d);
-      kh = min(kh, (gh << 8) | (uint32_t)d);
-      kd = min(kd, (gd << 8) | (uint32_t)d);
-      ku = min(ku, (gu << 8) | (uint32_t)d);
+      if (d - ds >= 2 || ds - d >= 2) far = min(far, c.s[k]);
+      if (d == ds - 1) vm = c.s[k];
+      if (d == ds + 1) vp = c.s[k];
     }
   }
-  ks = __reduce_min_sync(kFullMask, ks);
-  kh = __reduce_min_sync(kFullMask, kh);
-  kd = __reduce_min_sync(kFullMask, kd);
-  ku = __reduce_min_sync(kFullMask, ku);
-  const int ds = (int)(ks & 0xffu);
-  const uint32_t s0 = ks >> 8;
-  uint32_t far = 0xffffffffu;
-#pragma unroll
-  for (int k = 0; k < kMaxPerLane; k++) {
-    const int d = lane + 32 * k;
-    if (d < a.D && (d - ds >= 2 || ds - d >= 2)) far = min(far, s[k]);
-  }
-  far = __reduce_min_sync(kFullMask, far);
-  if (lane != 0) return;
+  far = warp_min(far);
+  // S(d*-1), S(d*+1) from the lanes that hold them (0 when out of range)
+  vm = __shfl_sync(kFullMask, vm, (ds + 31) & 31);
+  vp = __shfl_sync(kFullMask, vp, (ds + 1) & 31);
+  if (lane != out_lane) return;
+  const int cstar = a.cost[pix * a.Dp + ds];
   const uint32_t s2 = far == 0xffffffffu ? s0 : far;
   int curv = 0, rise = 0;
   if (a.D > 1) {
     if (ds == 0) {
-      const int n = (int)srow[1] - (int)s0;
-      curv = 2 * n;
-      rise = n;
+      curv = 2 * ((int)vp - (int)s0);
+      rise = (int)vp - (int)s0;
     } else if (ds == a.D - 1) {
-      const int n = (int)srow[a.D - 2] - (int)s0;
-      curv = 2 * n;
-      rise = n;
+      curv = 2 * ((int)vm - (int)s0);
+      rise = (int)vm - (int)s0;
     } else {
-      const int am = (int)srow[ds - 1] - (int)s0, bp = (int)srow[ds + 1] - (int)s0;
+      const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
       curv = am + bp;
       rise = min(am, bp);
     }
   }
-  const int gh_d = (int)(kh & 0xffu), gd_d = (int)(kd & 0xffu), gu_d = (int)(ku & 0xffu);
+  const int gh_d = (int)(c.kh & 0xffu), gd_d = (int)(c.kd & 0xffu), gu_d = (int)(c.ku & 0xffu);
   const int dis = min(abs(gh_d - ds), 16) + min(abs(gd_d - ds), 16) + min(abs(gu_d - ds), 16);
   const int margin = min(max(x - ds, 0), 64);
-  const int cstar = a.cost[pix * a.Dp + ds];
   // integers over powers of two: exact in fp32, then rounded once to bf16
   const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
                        (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
@@ -127,7 +116,159 @@ __global__ void __launch_bounds__(256)
   a.dint[pix] = (int16_t)ds;
   float v = (float)ds;
   if (a.subpixel && ds > 0 && ds < a.D - 1) {
-    const int am = (int)srow[ds - 1] - (int)s0, bp = (int)srow[ds + 1] - (int)s0;
+    const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
+    v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+  }
+  a.dsub[pix] = v;
+}
+
+// Scalar form (any D): one warp per column pair (x, x + 16) of a 32-column
+// strip row; the two columns share the words of the down sweep's partial sum.
+__global__ void __launch_bounds__(256)
+    features_kernel(FeatureArgs a) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int per_row = a.J * 16;
+  if (warp >= a.H * per_row) return;
+  const int y = warp / per_row, r = warp - y * per_row;
+  const int j = r >> 4, pr = r & 15;
+  const int xa = j * 32 + pr, xb = xa + 16;
+  const bool in_a = xa < a.W, in_b = xb < a.W;
+  const size_t pa = (size_t)y * a.W + xa, pb = (size_t)y * a.W + xb;
+  const uint32_t* sd = a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape;
+  Curve ca, cb;
+  ca.ks = ca.kh = ca.kd = ca.ku = 0xffffffffu;
+  cb.ks = cb.kh = cb.kd = cb.ku = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < kMaxPerLane; k++) {
+    const int d = lane + 32 * k;
+    ca.s[k] = cb.s[k] = 0xffffffffu;
+    if (d < a.D) {
+      const uint32_t w = sd[d];
+      if (in_a) {
+        const uint32_t sv = a.S[pa * a.D + d];
+        const uint32_t gh = (uint32_t)a.hfwd[pa * a.Dp + d] + (uint32_t)a.hbwd[pa * a.Dp + d];
+        const uint32_t gd = w & 0xffffu;
+        ca.s[k] = sv;
+        ca.ks = min(ca.ks, (sv << 8) | (uint32_t)d);
+        ca.kh = min(ca.kh, (gh << 8) | (uint32_t)d);
+        ca.kd = min(ca.kd, (gd << 8) | (uint32_t)d);
+        ca.ku = min(ca.ku, ((sv - gh - gd) << 8) | (uint32_t)d);
+      }
+      if (in_b) {
+        const uint32_t sv = a.S[pb * a.D + d];
+        const uint32_t gh = (uint32_t)a.hfwd[pb * a.Dp + d] + (uint32_t)a.hbwd[pb * a.Dp + d];
+        const uint32_t gd = w >> 16;
+        cb.s[k] = sv;
+        cb.ks = min(cb.ks, (sv << 8) | (uint32_t)d);
+        cb.kh = min(cb.kh, (gh << 8) | (uint32_t)d);
+        cb.kd = min(cb.kd, (gd << 8) | (uint32_t)d);
+        cb.ku = min(cb.ku, ((sv - gh - gd) << 8) | (uint32_t)d);
+      }
+    }
+  }
+  if (in_a) finish_pixel(a, ca, xa, pa, lane, 0);
+  if (in_b) finish_pixel(a, cb, xb, pb, lane, 1);
+}
+
+// Vector form (D % 4 == 0): one warp per pixel, lane l holding disparities
+// 4l .. 4l+3 (+128 for a second chunk): 8-byte loads of S, 4-byte loads of
+// the horizontal paths, 16-byte loads of the partial-sum words.
+template <int NCH>
+__global__ void __launch_bounds__(256)
+    features_vec_kernel(FeatureArgs a) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.W * a.H) return;
+  const int y = warp / a.W, x = warp - y * a.W;
+  const size_t pix = (size_t)y * a.W + x;
+  const int j = x >> 5, c = x & 31, pr = c & 15, hi = c >> 4;
+  const uint32_t* sd = a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape;
+  uint32_t sv[4 * NCH];
+  uint32_t ks = 0xffffffffu, kh = 0xffffffffu, kd = 0xffffffffu, ku = 0xffffffffu;
+#pragma unroll
+  for (int ch = 0; ch < NCH; ch++) {
+    const int d0 = 128 * ch + 4 * lane;
+    if (d0 < a.D) {
+      const uint2 s4 = *reinterpret_cast<const uint2*>(a.S + pix * a.D + d0);
+      const uint32_t hf4 = *reinterpret_cast<const uint32_t*>(a.hfwd + pix * a.Dp + d0);
+      const uint32_t hb4 = *reinterpret_cast<const uint32_t*>(a.hbwd + pix * a.Dp + d0);
+      const uint4 w4 = *reinterpret_cast<const uint4*>(sd + d0);
+      const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+      const uint32_t ss[4] = {s4.x & 0xffffu, s4.x >> 16, s4.y & 0xffffu, s4.y >> 16};
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const uint32_t d = (uint32_t)(d0 + e);
+        const uint32_t gh = ((hf4 >> (8 * e)) & 0xffu) + ((hb4 >> (8 * e)) & 0xffu);
+        const uint32_t gd = hi ? (ww[e] >> 16) : (ww[e] & 0xffffu);
+        sv[4 * ch + e] = ss[e];
+        ks = min(ks, (ss[e] << 8) | d);
+        kh = min(kh, (gh << 8) | d);
+        kd = min(kd, (gd << 8) | d);
+        ku = min(ku, ((ss[e] - gh - gd) << 8) | d);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; e++) sv[4 * ch + e] = 0xffffffffu;
+    }
+  }
+  ks = warp_min(ks);
+  kh = warp_min(kh);
+  kd = warp_min(kd);
+  ku = warp_min(ku);
+  const int ds = (int)(ks & 0xffu);
+  const uint32_t s0 = ks >> 8;
+  uint32_t far = 0xffffffffu, vm = 0u, vp = 0u;
+#pragma unroll
+  for (int ch = 0; ch < NCH; ch++) {
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int d = 128 * ch + 4 * lane + e;
+      if (d < a.D) {
+        if (d - ds >= 2 || ds - d >= 2) far = min(far, sv[4 * ch + e]);
+        if (d == ds - 1) vm = sv[4 * ch + e];
+        if (d == ds + 1) vp = sv[4 * ch + e];
+      }
+    }
+  }
+  far = warp_min(far);
+  vm = __shfl_sync(kFullMask, vm, ((ds + 127) >> 2) & 31);   // lane of d* - 1
+  vp = __shfl_sync(kFullMask, vp, ((ds + 1) >> 2) & 31);     // lane of d* + 1
+  if (lane != 0) return;
+  const int cstar = a.cost[pix * a.Dp + ds];
+  const uint32_t s2 = far == 0xffffffffu ? s0 : far;
+  int curv = 0, rise = 0;
+  if (a.D > 1) {
+    if (ds == 0) {
+      curv = 2 * ((int)vp - (int)s0);
+      rise = (int)vp - (int)s0;
+    } else if (ds == a.D - 1) {
+      curv = 2 * ((int)vm - (int)s0);
+      rise = (int)vm - (int)s0;
+    } else {
+      const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
+      curv = am + bp;
+      rise = min(am, bp);
+    }
+  }
+  const int dis = min(abs((int)(kh & 0xffu) - ds), 16) + min(abs((int)(kd & 0xffu) - ds), 16) +
+                  min(abs((int)(ku & 0xffu) - ds), 16);
+  const int margin = min(max(x - ds, 0), 64);
+  const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
+                       (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
+                       (float)ds * (1.0f / 128.0f),   (float)margin * (1.0f / 64.0f),
+                       (float)cstar * (1.0f / 64.0f), (float)rise * (1.0f / 256.0f)};
+  uint32_t packed[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    packed[i] = *reinterpret_cast<const uint32_t*>(&h2);
+  }
+  reinterpret_cast<uint4*>(a.feat)[pix] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  a.dint[pix] = (int16_t)ds;
+  float v = (float)ds;
+  if (a.subpixel && ds > 0 && ds < a.D - 1) {
+    const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
     v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
   }
   a.dsub[pix] = v;
@@ -687,8 +828,16 @@ __global__ void adam_kernel(float* th, float* m, float* v, const float* g, int n
 // ---------------------------------------------------------------------------
 cudaError_t launch_features(const FeatureArgs& a, cudaStream_t s) {
   count_launches(1);
-  const size_t threads = (size_t)a.W * a.H * 32;
-  features_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  if (a.D % 4 == 0) {
+    const size_t threads = (size_t)a.W * a.H * 32;
+    if (a.D <= 128)
+      features_vec_kernel<1><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+    else
+      features_vec_kernel<2><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  } else {
+    const size_t threads = (size_t)a.J * 16 * a.H * 32;
+    features_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

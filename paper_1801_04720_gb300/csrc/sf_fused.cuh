@@ -18,11 +18,12 @@ constexpr int kMaxPass = 4;
 struct Shape {
   int dc, chunks, halo;
 };
-Shape shape_for(int D);   // built-in rule unless a tuned override covers D
+// built-in rule unless a tuned override covers D (and `tuned` allows it)
+Shape shape_for(int D, bool tuned = true);
 bool shape_supported(int dc, int chunks, int halo);
 int set_shape_override(int d_lo, int d_hi, int dc, int halo);   // 0 = ok
 inline int padded_d(int D) { return ((D + 15) / 16) * 16; }
-inline int band_rows(int D) { return shape_for(D).halo + 1; }
+inline int band_rows(int D, bool tuned = true) { return shape_for(D, tuned).halo + 1; }
 
 // One stereo pass (one reference image) of the band sweeps and the
 // horizontal paths: its sizes and buffers.
@@ -42,6 +43,7 @@ struct PassDesc {
 
 struct HLineArgs {
   int P1, P2, Dmax, npass, nblocks;
+  int builtin_shape;           // 1: ignore tuned shape overrides
   uint32_t path_mask;
   int uniform_blocks;          // > 0: every pass has this many blocks
   const int* block_prefix;     // otherwise: first block of each pass [npass + 1]
@@ -52,6 +54,7 @@ struct HLineArgs {
 
 struct SweepArgs {
   int P1, P2, subpixel, Dmax, npass, ntasks;
+  int builtin_shape;           // 1: ignore tuned shape overrides
   uint32_t path_mask;
   int en_h0, en_h1;
   int uniform_items;           // > 0: all passes alike, tasks per band
@@ -67,9 +70,9 @@ struct SweepArgs {
 };
 
 // per-pass buffer sizes (the shape is the launch's, chosen from its largest D)
-inline size_t sdown_bytes(int W, int H, int Dshape) {
+inline size_t sdown_bytes(int W, int H, int Dshape, bool tuned = true) {
   const int J = (W + kTW - 1) / kTW;
-  const Shape s = shape_for(Dshape);
+  const Shape s = shape_for(Dshape, tuned);
   return (size_t)H * J * 16 * s.chunks * s.dc * sizeof(uint32_t);
 }
 inline size_t bs_bytes(int W, int D) { return (size_t)2 * 3 * W * padded_d(D); }

@@ -379,6 +379,10 @@ struct SweepCfg {
   static constexpr int TH = HALO + 1;       // band rows
   static constexpr int RING = UP ? 2 : 3;   // prefetch depth in rows
   static constexpr int XW = DC / 4 + 4;     // uint4 slots per owned thread per row (UP)
+  static constexpr bool select_by_halo() {
+    return UP && CHUNKS >= 2 && (HALO * CHUNKS) / kTW >= 1 &&
+           (CHUNKS % ((HALO * CHUNKS) / kTW > 0 ? (HALO * CHUNKS) / kTW : 1)) == 0;
+  }
   static constexpr size_t smem_bytes() {
     return (size_t)2 * 2 * (DC / 4) * NT * 16     // diagonal hand-over
            + (size_t)2 * 2 * NP * 4                // pair minima
@@ -388,16 +392,18 @@ struct SweepCfg {
   }
 };
 
-// Registers are capped at 48K per CTA (at most 168 a thread) so that a sweep
-// CTA leaves room on its SM for the horizontal-path blocks beside it; the
-// 16-disparity shapes keep 168 (they run one CTA per SM).
-constexpr int sweep_max_regs(int nt) {
-  return (49152 / nt) > 168 ? 168 : ((49152 / nt) / 8) * 8;
+// Registers: the down sweep is capped at 48K per CTA so that it leaves room
+// on its SM for the horizontal-path blocks that run beside it; the up sweep
+// runs alone and may use the whole register file (at most 168 a thread;
+// the 16-disparity shapes keep 168, one CTA per SM).
+constexpr int sweep_max_regs(int nt, bool up) {
+  const int budget = (up ? 65536 : 49152) / nt;
+  return budget > 168 ? 168 : (budget / 8) * 8;
 }
 
 template <int DC, int CHUNKS, int HALO, bool UP>
 __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
-    __maxnreg__(DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS))
+    __maxnreg__(DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS, UP))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
   using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
   using V = typename ByteVec<DC>::T;
@@ -406,7 +412,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   // winner selection by the halo warps (they carry two paths, the owned
   // warps three plus the sums): SEL_T threads per output column
   constexpr int SEL_T = (HALO * CHUNKS) / kTW;
-  constexpr bool HALO_SELECT = UP && CHUNKS >= 2 && SEL_T >= 1 && (CHUNKS % SEL_T) == 0;
+  constexpr bool HALO_SELECT = Cfg::select_by_halo();
   extern __shared__ __align__(16) uint8_t smem[];
   // diagonal hand-over buffers, [parity][register group][thread] uint4
   // (consecutive threads hit consecutive 16-byte words: no bank conflicts)
@@ -476,6 +482,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     const PassDesc pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];   // by value: fields in registers
     const int W = pd.W, H = pd.H, Dp = pd.Dp, J = pd.J, D = pd.D;
     const bool pad = d0 + DC > D;
+    const bool s_vec = UP && pd.S && D % 8 == 0 && (reinterpret_cast<uintptr_t>(pd.S) & 15u) == 0;
     const bool live = d0 < Dp;   // chunks past the padded depth hold no data
     const int band = UP ? (pd.nb - 1 - bi) : bi;
     const int ytop = band * TH;
@@ -723,12 +730,26 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
               if (d0 + i >= D) S[i] = 0xffffffffu;
           }
           if (pd.S) {
-            // full aggregated cost, [H][W][D] uint16
+            // full aggregated cost, [H][W][D] uint16: eight disparities per
+            // 16-byte store where the rows allow it
+            if (s_vec && !pad) {
 #pragma unroll
-            for (int i = 0; i < DC; i++) {
-              if (d0 + i < D) {
-                if (lo_in) pd.S[((size_t)y * W + xlo) * D + d0 + i] = (uint16_t)(S[i] & 0xffffu);
-                if (hi_in) pd.S[((size_t)y * W + xhi) * D + d0 + i] = (uint16_t)(S[i] >> 16);
+              for (int w = 0; w < DC / 8; w++) {
+                const uint32_t* s8 = S + 8 * w;
+                const uint4 lo4 = make_uint4(prmt(s8[0], s8[1], 0x5410u), prmt(s8[2], s8[3], 0x5410u),
+                                             prmt(s8[4], s8[5], 0x5410u), prmt(s8[6], s8[7], 0x5410u));
+                const uint4 hi4 = make_uint4(prmt(s8[0], s8[1], 0x7632u), prmt(s8[2], s8[3], 0x7632u),
+                                             prmt(s8[4], s8[5], 0x7632u), prmt(s8[6], s8[7], 0x7632u));
+                if (lo_in) *reinterpret_cast<uint4*>(pd.S + ((size_t)y * W + xlo) * D + d0 + 8 * w) = lo4;
+                if (hi_in) *reinterpret_cast<uint4*>(pd.S + ((size_t)y * W + xhi) * D + d0 + 8 * w) = hi4;
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < DC; i++) {
+                if (d0 + i < D) {
+                  if (lo_in) pd.S[((size_t)y * W + xlo) * D + d0 + i] = (uint16_t)(S[i] & 0xffffu);
+                  if (hi_in) pd.S[((size_t)y * W + xhi) * D + d0 + i] = (uint16_t)(S[i] >> 16);
+                }
               }
             }
           }
@@ -924,7 +945,7 @@ static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   count_launches(1);
-  const Shape sh = shape_for(a.Dmax);
+  const Shape sh = shape_for(a.Dmax, a.builtin_shape == 0);
   if (sh.dc == 16) {
     switch (sh.chunks) {
       case 4: return hline_dispatch<16, 4>(a, s);
@@ -973,8 +994,8 @@ bool shape_supported(int dc, int chunks, int halo) {
   return false;
 }
 
-Shape shape_for(int D) {
-  for (int i = g_nover - 1; i >= 0; i--) {
+Shape shape_for(int D, bool tuned) {
+  for (int i = tuned ? g_nover - 1 : -1; i >= 0; i--) {
     if (D >= g_over[i].lo && D <= g_over[i].hi) {
       Shape s;
       s.dc = g_over[i].dc;
@@ -1024,7 +1045,7 @@ static cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
 
 template <bool UP>
 static cudaError_t sweep_select(const SweepArgs& a, cudaStream_t s) {
-  const Shape sh = shape_for(a.Dmax);
+  const Shape sh = shape_for(a.Dmax, a.builtin_shape == 0);
 #define SF_CASE(DC_, CH_, HA_) \
   if (sh.dc == DC_ && sh.chunks == CH_ && sh.halo == HA_) return sweep_dispatch<DC_, CH_, HA_, UP>(a, s);
   SF_SWEEP_SHAPES(SF_CASE)

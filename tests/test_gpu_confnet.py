@@ -61,7 +61,10 @@ def random_features(rng, H, W):
     return co.bf16(rng.uniform(0.0, 1.5, size=(H, W, co.F)))
 
 
-SCENES = [(64, 48, 16, 0), (97, 41, 48, 1), (130, 37, 32, 2)]
+# vector form of the features pass for D % 4 == 0 (one or two 128-disparity
+# chunks), scalar form otherwise
+SCENES = [(64, 48, 16, 0), (97, 41, 48, 1), (130, 37, 32, 2), (61, 29, 22, 3), (300, 20, 160, 4),
+          (200, 16, 150, 5)]
 
 
 @pytest.mark.parametrize("W,H,D,seed", SCENES)
