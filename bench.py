@@ -61,6 +61,22 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x (all ranks get it); x itself at N = 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ms_max, world, units_per_step=1):
+    """Whole-job throughput of `world` replicas that each process
+    units_per_step units in ms_max milliseconds (the slowest rank's time)."""
+    return world * units_per_step * 1000.0 / ms_max
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -218,11 +234,7 @@ def run_ours(args, world, rank, local):
         torch.distributed.barrier()
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), world, dev)
     stages = tracer.durations()
     stage_tot = {k: sum(v) for k, v in stages.items()}
     dominant = max(stage_tot, key=stage_tot.get)
@@ -251,17 +263,13 @@ def run_ours(args, world, rank, local):
             t0 = time.perf_counter()
             _lib.sf_scene_flow_host(h_imgs, h_flow, p, cam, ws_h, h_out, stream=stream)
             e_ms.append((time.perf_counter() - t0) * 1e3)
-        e_mean = statistics.mean(e_ms)
-        if world > 1:
-            t = torch.tensor([e_mean], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_mean = float(t.item())
-        e2e = {"value": round(world * 1000.0 / e_mean, 2), "unit": "frames/s",
+        e_mean = max_over_ranks(statistics.mean(e_ms), world, dev)
+        e2e = {"value": round(replica_rate(e_mean, world), 2), "unit": "frames/s",
                "h2d_bytes_per_step": 4 * N + 8 * N, "d2h_bytes_per_step": 16 * N + 12 * N + 12 * N + N,
                "ms_per_step": round(e_mean, 4)}
 
     result = {
-        "metric": METRIC, "value": round(world * 1000.0 / ms, 2), "unit": "frames/s",
+        "metric": METRIC, "value": round(replica_rate(ms, world), 2), "unit": "frames/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8/u16 integer SGM, f32 subpixel + scene flow",
@@ -320,9 +328,11 @@ def run_batch(args, dev, _lib, synth, torch):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     _lib.sf_batch_release_graphs()
-    mean = statistics.mean(ms)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    mean = max_over_ranks(statistics.mean(ms), world, dev)
     pixels = sum(q.shape[0] * q.shape[1] for q in quads)
-    return {"metric": "scene-flow quadruples/s, uneven batch", "value": round(len(quads) * 1000.0 / mean, 2),
+    return {"metric": "scene-flow quadruples/s, uneven batch",
+            "value": round(replica_rate(mean, world, len(quads)), 2),
             "unit": "quadruples/s", "items": len(quads), "ms_per_step": round(mean, 3),
             "megapixels_per_step": round(pixels / 1e6, 3),
             "workspace_gb": round(ws.numel() / 1e9, 2), "graph": True,
@@ -362,15 +372,16 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
             ends[k].record(stream)
     torch.cuda.synchronize()
     launches = _lib.kernel_launches() - launches0
-    ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    ms = max_over_ranks(statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     stages = {k: round(sum(v) / args.steps, 5) for k, v in tracer.durations().items()}
     # accuracy against the plain check on this frame (pair at t)
     plain = _lib.sf_sgm_full(imgs[0], imgs[1], p)
     lo = _lib.sf_sgm_learned(imgs[0], imgs[1], p, packed=packed, threshold=thr)
     frame_rates = train_confnet.rates([(lo["prob"], lo["dint"], plain["valid"])], thr)
     res = {"metric": "scene-flow frames/s, learned confidence in place of the L-R check",
-           "value": round(1000.0 / ms, 2), "unit": "frames/s", "ms_per_step": round(ms, 4),
-           "vs_plain": round(1000.0 / ms / plain_fps, 3), "threshold": thr,
+           "value": round(replica_rate(ms, world), 2), "unit": "frames/s", "ms_per_step": round(ms, 4),
+           "vs_plain": round(replica_rate(ms, world) / plain_fps, 3), "threshold": thr,
            "gpu_launches": int(launches), "stages_ms_per_step": stages,
            "automotive_frame": {k: round(v, 5) for k, v in frame_rates.items()}}
     n_eval = min(args.learned_eval, len(train_confnet.EVAL_SEEDS))

@@ -326,6 +326,19 @@ int32_t sf_trace_disarm(void);
  * (all threads), for launch accounting. */
 uint64_t sf_kernel_launches(void);
 
+/* Test hooks for failure detection (no counterpart in the paper).
+ * SF_DEBUG_SPIN_LIMIT: polls a bounded inter-CTA wait of the band sweeps
+ *   makes before it gives up (0 restores the default, about one second).
+ * SF_DEBUG_SKIP_TASKS: the down sweep's task queue starts at this task, so
+ *   the skipped tasks never run and the bands after them wait for flags that
+ *   nothing sets; the waits run out, set the workspace error word
+ *   (sf_check_workspace then returns SF_ERR_TIMEOUT) and the kernels return
+ *   normally.  0 (the default) skips nothing.
+ * Process-wide; not for production use. */
+#define SF_DEBUG_SPIN_LIMIT 1
+#define SF_DEBUG_SKIP_TASKS 2
+sf_status sf_debug_set(int32_t key, int64_t value);
+
 /* Process-wide choice between the fused stereo kernels (1, default) and the
  * staged kernels (0: stored cost volume, one kernel per path, separate
  * selection).  Both compute the same integers; the staged kernels also serve

@@ -32,8 +32,11 @@ EXPORTED = [
     "sf_sgm_aggregate_noalloc", "sf_confnet_param_count", "sf_confnet_packed_bytes",
     "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
     "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
-    "sf_scene_flow_learned",
+    "sf_scene_flow_learned", "sf_debug_set",
 ]
+
+SF_DEBUG_SPIN_LIMIT = 1
+SF_DEBUG_SKIP_TASKS = 2
 
 SF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -132,6 +135,7 @@ def load(path: str = LIB_PATH):
             "sf_batch_release_graphs": (None, []),
             "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
             "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
+            "sf_debug_set": (i32, [i32, ctypes.c_int64]),
             "sf_confnet_param_count": (i32, []),
             "sf_confnet_packed_bytes": (sz, []),
             "sf_confnet_pack": (i32, [P, P, P]),
@@ -238,6 +242,10 @@ def sf_sgm_aggregate_noalloc(cost, p: SgmParams, out, err=None, stream=None):
            load().sf_sgm_aggregate_noalloc(_ptr(cost), W, H, ctypes.byref(p), _ptr(out), _ptr(err),
                                            _stream(stream)))
     return out
+
+
+def sf_debug_set(key: int, value: int):
+    _check("sf_debug_set", load().sf_debug_set(int(key), int(value)))
 
 
 def sf_set_fused(enable: bool):

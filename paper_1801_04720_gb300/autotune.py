@@ -84,16 +84,22 @@ def apply(result):
     return n
 
 
-def load_or_tune(W=1242, H=375, cache=CACHE, **kw):
-    """Uses the cached choice for this GPU and size, tuning when there is none."""
+def cached(cache, gpu, W, H):
+    """The stored tune() result for this GPU name and size, or None."""
     try:
         with open(cache) as f:
             res = json.load(f)
-        if res.get("gpu") == torch.cuda.get_device_name() and res.get("W") == W and res.get("H") == H:
-            apply(res)
-            return res
     except (OSError, ValueError):
-        pass
-    res = tune(W=W, H=H, cache=cache, **kw)
+        return None
+    if res.get("gpu") == gpu and res.get("W") == W and res.get("H") == H:
+        return res
+    return None
+
+
+def load_or_tune(W=1242, H=375, cache=CACHE, **kw):
+    """Uses the cached choice for this GPU and size, tuning when there is none."""
+    res = cached(cache, torch.cuda.get_device_name(), W, H)
+    if res is None:
+        res = tune(W=W, H=H, cache=cache, **kw)
     apply(res)
     return res

@@ -233,6 +233,12 @@ FusedPlan single_plan(int W, int H, int D, int npairs) {
 
 constexpr long long kSpinLimit = 1ll << 24;   // bounded neighbour wait (~1 s)
 
+// Test hooks (sf_debug_set): poll limit of the bounded waits, and tasks the
+// down sweep's queue skips (their bands are never computed, so the waits of
+// later bands run out).
+std::atomic<long long> g_spin_limit{kSpinLimit};
+std::atomic<int> g_skip_down_tasks{0};
+
 // Side stream on which the horizontal-path kernel overlaps the down sweep
 // (one per device, created on first use; fork and join through events so the
 // pattern also works under CUDA graph capture of the caller's stream).
@@ -336,7 +342,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
   sa.en_h0 = (p->path_mask >> 0) & 1u;
   sa.en_h1 = (p->path_mask >> 1) & 1u;
   sa.err = err;
-  sa.spin_limit = kSpinLimit;
+  sa.spin_limit = g_spin_limit.load(std::memory_order_relaxed);
   if (inl) {
     for (int k = 0; k < npass; k++) ha.inl[k] = sa.inl[k] = d[k];
     ha.uniform_blocks = 2 * ((d[0].H + 15) / 16);
@@ -364,6 +370,11 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
   SF_TRY_CUDA(fused::launch_hline(ha, side->s));
   SF_TRY_CUDA(cudaEventRecord(side->join, side->s));
   sa.task_counter = counters;
+  if (const int skip = g_skip_down_tasks.load(std::memory_order_relaxed)) {
+    static int skip_host;
+    skip_host = skip;
+    SF_TRY_CUDA(cudaMemcpyAsync(counters, &skip_host, sizeof(int), cudaMemcpyHostToDevice, s));
+  }
   SF_TRY_CUDA(fused::launch_sweep(sa, false, s));
   if (inl) {
     for (int k = 0; k < npass; k++) sa.inl[k] = d[k];   // with outputs of the up sweep
@@ -865,6 +876,20 @@ int32_t sf_trace_disarm(void) {
 }
 
 uint64_t sf_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sf_status sf_debug_set(int32_t key, int64_t value) {
+  if (key == SF_DEBUG_SPIN_LIMIT) {
+    if (value < 0) return SF_ERR_INVALID_ARG;
+    g_spin_limit.store(value == 0 ? kSpinLimit : value, std::memory_order_relaxed);
+    return SF_OK;
+  }
+  if (key == SF_DEBUG_SKIP_TASKS) {
+    if (value < 0 || value > (1 << 30)) return SF_ERR_INVALID_ARG;
+    g_skip_down_tasks.store((int)value, std::memory_order_relaxed);
+    return SF_OK;
+  }
+  return SF_ERR_INVALID_ARG;
+}
 
 size_t sf_batch_workspace_size(const sf_batch_item* items, int32_t n, const sf_sgm_params* p) {
   BatchSetup b = batch_setup(items, n, p);

@@ -1,0 +1,58 @@
+"""Host side of the sweep-shape autotuner (no GPU): installing a tuned
+choice, rejecting shapes the library does not provide, and the cache key."""
+import json
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_04720_gb300 import _lib, build
+    build.build()
+    _lib.load()
+    yield _lib
+    for lo, hi in [(1, 32), (33, 64), (65, 128), (129, 256)]:
+        _lib.sf_set_sweep_shape(lo, hi, 0, 0)
+
+
+def test_apply_installs_every_class(lib):
+    from paper_1801_04720_gb300 import autotune
+    res = {"classes": [{"lo": 33, "hi": 64, "dc": 8, "halo": 8},
+                       {"lo": 65, "hi": 128, "dc": 16, "halo": 16}]}
+    assert autotune.apply(res) == 2
+    for c in res["classes"]:
+        lib.sf_set_sweep_shape(c["lo"], c["hi"], 0, 0)
+
+
+@pytest.mark.parametrize("lo,hi,dc,halo", [(1, 32, 4, 16), (65, 128, 8, 12), (200, 100, 8, 16),
+                                          (0, 32, 8, 16), (129, 257, 16, 8)])
+def test_unsupported_shapes_are_rejected(lib, lo, hi, dc, halo):
+    with pytest.raises(lib.SFError):
+        lib.sf_set_sweep_shape(lo, hi, dc, halo)
+
+
+def test_every_candidate_is_a_built_shape(lib):
+    from paper_1801_04720_gb300 import autotune
+    for lo, hi in autotune.DEFAULT_CLASSES:
+        ok = 0
+        for dc, halo in autotune.CANDIDATES:
+            try:
+                lib.sf_set_sweep_shape(lo, hi, dc, halo)
+                ok += 1
+            except lib.SFError:
+                pass
+            lib.sf_set_sweep_shape(lo, hi, 0, 0)
+        assert ok >= 1, (lo, hi)     # D > 128 has one built shape (16 disparities, halo 8)
+
+
+def test_cache_is_keyed_by_gpu_and_size(tmp_path):
+    from paper_1801_04720_gb300 import autotune
+    path = tmp_path / "tune.json"
+    res = {"gpu": "GPU-A", "W": 1242, "H": 375, "classes": [{"lo": 65, "hi": 128, "dc": 8, "halo": 16}]}
+    path.write_text(json.dumps(res))
+    assert autotune.cached(str(path), "GPU-A", 1242, 375) == res
+    assert autotune.cached(str(path), "GPU-B", 1242, 375) is None
+    assert autotune.cached(str(path), "GPU-A", 640, 480) is None
+    assert autotune.cached(str(tmp_path / "missing.json"), "GPU-A", 1242, 375) is None
+    path.write_text("{not json")
+    assert autotune.cached(str(path), "GPU-A", 1242, 375) is None
