@@ -54,55 +54,64 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // ---------------------------------------------------------------------------
 // 1. cost volumes of a stereo pair
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(1024)
     cost_pair_kernel(const uint64_t* __restrict__ cL, const uint64_t* __restrict__ cR, int W, int H,
                      int D, int Dp, int cmax, uint8_t* __restrict__ CL, uint8_t* __restrict__ CR) {
   extern __shared__ __align__(16) uint8_t smem[];
+  // left census row; right census row split by index mod 4 (srt[j & 3][j >> 2])
+  // so that lanes reading cR(x - 4 lane - k) hit consecutive words; the
+  // distances H(cL(x), cR(x-d)) as rows [W][Ds], 4 padding bytes per row
+  // spreading the diagonal reads of the right-reference pass over the banks
+  const int Q = (W + 3) >> 2;
   uint64_t* sl = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* sr = sl + W;
-  uint8_t* band = reinterpret_cast<uint8_t*>(sr + W);  // [W][Dp]: H(cL(x), cR(x-d))
+  uint64_t* srt = sl + W;
+  uint8_t* band = reinterpret_cast<uint8_t*>(srt + 4 * Q);
+  const int Ds = Dp + 4;
+  const int groups = Dp >> 2;   // 4 disparities per lane and step
   const int y = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < W; i += blockDim.x) {
     sl[i] = cL[(size_t)y * W + i];
-    sr[i] = cR[(size_t)y * W + i];
+    srt[(i & 3) * Q + (i >> 2)] = cR[(size_t)y * W + i];
   }
   __syncthreads();
-  // all distances of this row, four disparities per thread iteration
-  const int groups = Dp / 4;
-  for (int i = threadIdx.x; i < W * groups; i += blockDim.x) {
-    const int x = i / groups, d0 = (i - x * groups) * 4;
+  for (int x = warp; x < W; x += nw) {
     const uint64_t a = sl[x];
-    uint32_t packed = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const int d = d0 + k;
-      const int xr = x - d;
-      const uint32_t c = (d < D && xr >= 0) ? (uint32_t)__popcll(a ^ sr[xr]) : (uint32_t)cmax;
-      packed |= c << (8 * k);
-    }
-    *reinterpret_cast<uint32_t*>(band + (size_t)x * Dp + d0) = packed;
-  }
-  __syncthreads();
-  // left-reference row: a straight copy
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(band);
-    uint4* dst = reinterpret_cast<uint4*>(CL + (size_t)y * W * Dp);
-    for (int i = threadIdx.x; i < W * Dp / 16; i += blockDim.x) dst[i] = src[i];
-  }
-  // right-reference row: C_R(x, d) = band[x + d][d], or cmax past the edge
-  {
-    uint32_t* dst = reinterpret_cast<uint32_t*>(CR + (size_t)y * W * Dp);
-    for (int i = threadIdx.x; i < W * groups; i += blockDim.x) {
-      const int x = i / groups, d0 = (i - x * groups) * 4;
+    uint32_t* row = reinterpret_cast<uint32_t*>(band + x * Ds);
+    for (int g = lane; g < groups; g += 32) {
+      const int d0 = 4 * g;
       uint32_t packed = 0;
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        const int d = d0 + k;
-        const int xl = x + d;
-        const uint32_t c = (xl < W) ? (uint32_t)band[(size_t)xl * Dp + d] : (uint32_t)cmax;
+        const int j = x - d0 - k;   // right pixel
+        const bool ok = d0 + k < D && j >= 0;
+        // (index 0 where there is no candidate: every address stays in the row)
+        const uint64_t b = srt[ok ? (j & 3) * Q + (j >> 2) : 0];
+        const uint32_t c = ok ? (uint32_t)__popcll(a ^ b) : (uint32_t)cmax;
         packed |= c << (8 * k);
       }
-      dst[i] = packed;
+      row[g] = packed;
+    }
+  }
+  __syncthreads();
+  // left-reference row: the rows of the band, 4 bytes per lane
+  uint32_t* dl = reinterpret_cast<uint32_t*>(CL + (size_t)y * W * Dp);
+  uint32_t* dr = reinterpret_cast<uint32_t*>(CR + (size_t)y * W * Dp);
+  for (int x = warp; x < W; x += nw) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(band + x * Ds);
+    for (int g = lane; g < groups; g += 32) {
+      dl[x * groups + g] = src[g];
+      // right-reference row: C_R(x, d) = band[x + d][d], or cmax past the edge
+      const int d0 = 4 * g;
+      uint32_t packed = 0;
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int xl = x + d0 + k;
+        const uint32_t v = band[xl < W ? xl * Ds + d0 + k : 0];
+        const uint32_t c = xl < W ? v : (uint32_t)cmax;
+        packed |= c << (8 * k);
+      }
+      dr[x * groups + g] = packed;
     }
   }
 }
@@ -915,7 +924,7 @@ cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int 
 cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
                              int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
-  const size_t smem = (size_t)W * 16 + (size_t)W * Dp;
+  const size_t smem = cost_pair_smem(W, D);
   if (smem > kCostPairSmemMax) {
     count_launches(2);
     dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
@@ -927,7 +936,7 @@ cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int 
                                        227 * 1024);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  cost_pair_kernel<<<H, 512, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, CR);
+  cost_pair_kernel<<<H, 1024, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, CR);
   return cudaGetLastError();
 }
 
