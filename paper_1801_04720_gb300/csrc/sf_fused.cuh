@@ -77,7 +77,7 @@ inline size_t sdown_bytes(int W, int H, int Dshape, bool tuned = true) {
 }
 inline size_t bs_bytes(int W, int D) { return (size_t)2 * 3 * W * padded_d(D); }
 inline size_t cost_pair_smem(int W, int D) {
-  return (size_t)W * 8 + (size_t)((W + 3) / 4) * 32 + (size_t)W * (padded_d(D) + 4);
+  return 2 * ((size_t)W * 8 + (size_t)((W + 3) / 4) * 32) + (size_t)W * (padded_d(D) + 4);
 }
 // rows whose census pair + distances exceed this use per-reference x-tiles
 constexpr size_t kCostPairSmemMax = 227u * 1024u;

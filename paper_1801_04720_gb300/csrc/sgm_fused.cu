@@ -54,66 +54,81 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // ---------------------------------------------------------------------------
 // 1. cost volumes of a stereo pair
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
     cost_pair_kernel(const uint64_t* __restrict__ cL, const uint64_t* __restrict__ cR, int W, int H,
                      int D, int Dp, int cmax, uint8_t* __restrict__ CL, uint8_t* __restrict__ CR) {
   extern __shared__ __align__(16) uint8_t smem[];
-  // left census row; right census row split by index mod 4 (srt[j & 3][j >> 2])
-  // so that lanes reading cR(x - 4 lane - k) hit consecutive words; the
-  // distances H(cL(x), cR(x-d)) as rows [W][Ds], 4 padding bytes per row
-  // spreading the diagonal reads of the right-reference pass over the banks
+  // per census buffer (two, the next row's arriving while this row is
+  // computed): the left census row, then the right one split by index mod 4
+  // (srt[j & 3][j >> 2]) so that lanes reading cR(x - 4 lane - k) hit
+  // consecutive words.  Then the distances H(cL(x), cR(x-d)) as rows
+  // [W][Ds]; 4 padding bytes per row spread the diagonal reads of the
+  // right-reference pass over the banks.
   const int Q = (W + 3) >> 2;
-  uint64_t* sl = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* srt = sl + W;
-  uint8_t* band = reinterpret_cast<uint8_t*>(srt + 4 * Q);
+  const int cw = W + 4 * Q;   // 8-byte words per census buffer
+  uint64_t* cbuf = reinterpret_cast<uint64_t*>(smem);
+  uint8_t* band = reinterpret_cast<uint8_t*>(cbuf + 2 * cw);
   const int Ds = Dp + 4;
   const int groups = Dp >> 2;   // 4 disparities per lane and step
-  const int y = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) {
-    sl[i] = cL[(size_t)y * W + i];
-    srt[(i & 3) * Q + (i >> 2)] = cR[(size_t)y * W + i];
-  }
-  __syncthreads();
-  for (int x = warp; x < W; x += nw) {
-    const uint64_t a = sl[x];
-    uint32_t* row = reinterpret_cast<uint32_t*>(band + x * Ds);
-    for (int g = lane; g < groups; g += 32) {
-      const int d0 = 4 * g;
-      uint32_t packed = 0;
+  auto fetch = [&](int y, int buf) {
+    uint64_t* sl = cbuf + buf * cw;
+    uint64_t* srt = sl + W;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) {
+      cp_async<8>(sl + i, cL + (size_t)y * W + i, true);
+      cp_async<8>(srt + (i & 3) * Q + (i >> 2), cR + (size_t)y * W + i, true);
+    }
+    cp_async_commit();
+  };
+  int buf = 0;
+  if (blockIdx.x < H) fetch(blockIdx.x, 0);
+  for (int y = blockIdx.x; y < H; y += gridDim.x, buf ^= 1) {
+    cp_async_wait<0>();
+    __syncthreads();   // this row's census is in; the band is free
+    if (y + (int)gridDim.x < H) fetch(y + gridDim.x, buf ^ 1);
+    const uint64_t* sl = cbuf + buf * cw;
+    const uint64_t* srt = sl + W;
+    for (int x = warp; x < W; x += nw) {
+      const uint64_t a = sl[x];
+      uint32_t* row = reinterpret_cast<uint32_t*>(band + x * Ds);
+      for (int g = lane; g < groups; g += 32) {
+        const int d0 = 4 * g;
+        uint32_t packed = 0;
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const int j = x - d0 - k;   // right pixel
-        const bool ok = d0 + k < D && j >= 0;
-        // (index 0 where there is no candidate: every address stays in the row)
-        const uint64_t b = srt[ok ? (j & 3) * Q + (j >> 2) : 0];
-        const uint32_t c = ok ? (uint32_t)__popcll(a ^ b) : (uint32_t)cmax;
-        packed |= c << (8 * k);
+        for (int k = 0; k < 4; k++) {
+          const int j = x - d0 - k;   // right pixel
+          const bool ok = d0 + k < D && j >= 0;
+          // (index 0 where there is no candidate: every address stays in the row)
+          const uint64_t b = srt[ok ? (j & 3) * Q + (j >> 2) : 0];
+          const uint32_t c = ok ? (uint32_t)__popcll(a ^ b) : (uint32_t)cmax;
+          packed |= c << (8 * k);
+        }
+        row[g] = packed;
       }
-      row[g] = packed;
+    }
+    __syncthreads();
+    // left-reference row: the rows of the band; right-reference row:
+    // C_R(x, d) = band[x + d][d], or cmax past the edge
+    uint32_t* dl = reinterpret_cast<uint32_t*>(CL + (size_t)y * W * Dp);
+    uint32_t* dr = reinterpret_cast<uint32_t*>(CR + (size_t)y * W * Dp);
+    for (int x = warp; x < W; x += nw) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(band + x * Ds);
+      for (int g = lane; g < groups; g += 32) {
+        dl[x * groups + g] = src[g];
+        const int d0 = 4 * g;
+        uint32_t packed = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const int xl = x + d0 + k;
+          const uint32_t v = band[xl < W ? xl * Ds + d0 + k : 0];
+          const uint32_t c = xl < W ? v : (uint32_t)cmax;
+          packed |= c << (8 * k);
+        }
+        dr[x * groups + g] = packed;
+      }
     }
   }
-  __syncthreads();
-  // left-reference row: the rows of the band, 4 bytes per lane
-  uint32_t* dl = reinterpret_cast<uint32_t*>(CL + (size_t)y * W * Dp);
-  uint32_t* dr = reinterpret_cast<uint32_t*>(CR + (size_t)y * W * Dp);
-  for (int x = warp; x < W; x += nw) {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(band + x * Ds);
-    for (int g = lane; g < groups; g += 32) {
-      dl[x * groups + g] = src[g];
-      // right-reference row: C_R(x, d) = band[x + d][d], or cmax past the edge
-      const int d0 = 4 * g;
-      uint32_t packed = 0;
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const int xl = x + d0 + k;
-        const uint32_t v = band[xl < W ? xl * Ds + d0 + k : 0];
-        const uint32_t c = xl < W ? v : (uint32_t)cmax;
-        packed |= c << (8 * k);
-      }
-      dr[x * groups + g] = packed;
-    }
-  }
+  cp_async_wait<0>();
 }
 
 // Rows too wide for one CTA's shared memory (W x Dp > ~200 KB): each
@@ -936,7 +951,10 @@ cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int 
                                        227 * 1024);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  cost_pair_kernel<<<H, 1024, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, CR);
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  cost_pair_kernel<<<std::min(H, sms), 1024, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, CR);
   return cudaGetLastError();
 }
 
