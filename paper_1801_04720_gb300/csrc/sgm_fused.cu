@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     }
     p = lo;
   }
-  const PassDesc& pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];
+  const PassDesc pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];   // by value: fields in registers
   const int W = pd.W, H = pd.H, Dp = pd.Dp;
   const int nrb = (H + kHlineRows - 1) / kHlineRows;
   const int rem = blockIdx.x - (a.block_prefix ? a.block_prefix[p] : p * a.uniform_blocks);
@@ -250,16 +250,18 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
   const bool row_ok = r0 < nrows;
   const int d0 = q * DC;
   const bool live = d0 < Dp;                 // chunks past the padded depth hold no data
+  const bool io = live && row_ok;
+  const bool two = r1 != r0;
   const int D = pd.D;
   const bool pad = d0 + DC > D;
+  const bool q_first = q == 0, q_last = q == CHUNKS - 1;
   const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
   const int CW = max(1, kHlineTileBytes / (kHlineRows * Dp));   // columns per chunk
   const int nchunks = (W + CW - 1) / CW;
-  uint8_t* buf[2] = {hsmem, hsmem + kHlineTileBytes};
   auto chunk_x0 = [&](int c) { return dir == 0 ? c * CW : max(0, W - (c + 1) * CW); };
   auto chunk_w = [&](int c) { return dir == 0 ? min(CW, W - c * CW) : (W - c * CW) - chunk_x0(c); };
   auto issue = [&](int c) {                  // one thread: all rows of chunk c
-    uint8_t* dst = buf[c & 1];
+    uint8_t* dst = hsmem + (c & 1) * kHlineTileBytes;
     const int xs = chunk_x0(c), cw = chunk_w(c);
     const unsigned bytes = (unsigned)(cw * Dp);
     fence_proxy_async();
@@ -279,7 +281,40 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
 #pragma unroll
   for (int i = 0; i < DC; i++) L[i] = 0;
   uint32_t m = 0;
-  int s = 0;                                 // step along the line
+  // one step along the line: costs from the tile, the update, the outputs.
+  // (A line's first step has L = 0 and m = 0, so its update is C whatever
+  // the end values at d = 0 and d = Dp-1.)
+  const int step = dir == 0 ? Dp : -Dp;
+  auto line_step = [&](const uint8_t*& ta, const uint8_t*& tb, uint8_t*& oa, uint8_t*& ob, const uint32_t* Lp,
+                       uint32_t* Ln) {
+    V va = ByteVec<DC>::zero(), vb = va;
+    if (io) {
+      va = *reinterpret_cast<const V*>(ta);
+      vb = *reinterpret_cast<const V*>(tb);
+    }
+    ta += step;
+    tb += step;
+    bytes_to_pairs<DC>(va, vb, Cr);
+    if (pad) {
+#pragma unroll
+      for (int i = 0; i < DC; i++)
+        if (d0 + i >= D) Cr[i] = kPadCost2;
+    }
+    uint32_t left = __shfl_up_sync(0xffffffffu, Lp[DC - 1], 1, CHUNKS);
+    uint32_t right = __shfl_down_sync(0xffffffffu, Lp[0], 1, CHUNKS);
+    if (q_first) left = kInf2;
+    if (q_last) right = kInf2;
+    sgm_update<DC>(Lp, Cr, left, right, m, p1x2, p2x2, Ln);
+    m = group_min2<CHUNKS>(tree_min<DC>(Ln));
+    if (io) {
+      V wa, wb;
+      pairs_to_bytes<DC>(Ln, wa, wb);
+      __stcs(reinterpret_cast<V*>(oa), wa);
+      if (two) __stcs(reinterpret_cast<V*>(ob), wb);
+    }
+    oa += step;
+    ob += step;
+  };
   for (int c = 0; c < nchunks; c++) {
     if (t == 0 && c + 1 < nchunks) issue(c + 1);
     // bounded wait for chunk c
@@ -293,36 +328,23 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
       }
     }
     if (s_fail) break;
-    const uint8_t* tile = buf[c & 1];
     const int xs = chunk_x0(c), cw = chunk_w(c);
-    for (int u = 0; u < cw; u++, s++) {
-      const int cx = dir == 0 ? u : cw - 1 - u;
-      const int x = xs + cx;
-      V va = ByteVec<DC>::zero(), vb = va;
-      if (live && row_ok) {
-        va = *reinterpret_cast<const V*>(tile + ((size_t)r0 * CW + cx) * Dp + d0);
-        vb = *reinterpret_cast<const V*>(tile + ((size_t)r1 * CW + cx) * Dp + d0);
-      }
-      bytes_to_pairs<DC>(va, vb, Cr);
-      if (pad) {
-#pragma unroll
-        for (int i = 0; i < DC; i++)
-          if (d0 + i >= D) Cr[i] = kPadCost2;
-      }
-      uint32_t left = __shfl_up_sync(0xffffffffu, L[DC - 1], 1, CHUNKS);
-      uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, CHUNKS);
-      if (q == 0) left = (s == 0) ? 0u : kInf2;
-      if (q == CHUNKS - 1) right = (s == 0) ? 0u : kInf2;
-      sgm_update<DC>(L, Cr, left, right, m, p1x2, p2x2, N);
-      m = group_min2<CHUNKS>(tree_min<DC>(N));
+    const int cx0 = dir == 0 ? 0 : cw - 1;   // first column of the walk in this chunk
+    const uint8_t* tile = hsmem + (c & 1) * kHlineTileBytes;
+    const uint8_t* ta = tile + (r0 * CW + cx0) * Dp + d0;
+    const uint8_t* tb = tile + (r1 * CW + cx0) * Dp + d0;
+    uint8_t* oa = out + ((size_t)(ybase + r0) * W + xs + cx0) * Dp + d0;
+    uint8_t* ob = out + ((size_t)(ybase + r1) * W + xs + cx0) * Dp + d0;
+    int u = 0;
+    // two steps per trip: the states alternate between L and N (no copies)
+    for (; u + 1 < cw; u += 2) {
+      line_step(ta, tb, oa, ob, L, N);
+      line_step(ta, tb, oa, ob, N, L);
+    }
+    if (u < cw) {
+      line_step(ta, tb, oa, ob, L, N);
 #pragma unroll
       for (int i = 0; i < DC; i++) L[i] = N[i];
-      if (live && row_ok) {
-        V oa, ob;
-        pairs_to_bytes<DC>(N, oa, ob);
-        __stcs(reinterpret_cast<V*>(out + ((size_t)(ybase + r0) * W + x) * Dp + d0), oa);
-        if (r1 != r0) __stcs(reinterpret_cast<V*>(out + ((size_t)(ybase + r1) * W + x) * Dp + d0), ob);
-      }
     }
     __syncthreads();   // buffer c&1 is free for chunk c+2
   }
