@@ -994,7 +994,13 @@ static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   count_launches(1);
-  const Shape sh = shape_for(a.Dmax, a.builtin_shape == 0);
+  // the horizontal volumes do not depend on the sweeps' shape: 8 disparities
+  // per thread (shortest serial step) wherever 16 chunks cover D
+  Shape sh;
+  sh.dc = a.Dmax <= 128 ? 8 : 16;
+  sh.chunks = sh.dc == 8 ? 2 : 4;
+  while (sh.chunks * sh.dc < a.Dmax) sh.chunks <<= 1;
+  sh.halo = 0;
   if (sh.dc == 16) {
     switch (sh.chunks) {
       case 4: return hline_dispatch<16, 4>(a, s);
