@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--learned-eval", type=int, default=200,
                     help="held-out scenes for the learned path's false-accept rate "
                          "(0 = timing only, -1 = skip the learned path)")
+    ap.add_argument("--shape", default=None,
+                    help="sweep shape DCxHALO for the frame's disparity class instead of the "
+                         "autotuner (e.g. 16x16, as in profiling runs)")
     ap.add_argument("--profile", action="store_true",
                     help="short run for ncu: no clock-sampling load phase, no e2e, no CPU baseline")
     args = ap.parse_args()
@@ -182,7 +185,11 @@ def run_ours(args, world, rank, local):
     _lib.load()
     dev = torch.device("cuda", local)
     tuned = None
-    if not args.no_autotune:
+    if args.shape:
+        dc, halo = (int(v) for v in args.shape.lower().split("x"))
+        _lib.sf_set_sweep_shape(65, 128, dc, halo)
+        tuned = {"classes": [{"lo": 65, "hi": 128, "dc": dc, "halo": halo, "forced": True}]}
+    elif not args.no_autotune:
         from paper_1801_04720_gb300 import autotune
         tuned = autotune.load_or_tune(W=W_IMG, H=H_IMG, classes=[(65, 128)])
     q = synth.automotive(seed=args.seed + rank)

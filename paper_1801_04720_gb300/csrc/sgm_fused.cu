@@ -91,15 +91,18 @@ __global__ void __launch_bounds__(1024, 1)
     for (int x = warp; x < W; x += nw) {
       const uint64_t a = sl[x];
       uint32_t* row = reinterpret_cast<uint32_t*>(band + x * Ds);
+      // right pixel j = x - 4g - k sits at srt[(x-k) & 3][((x-k) >> 2) - g]
+      int base[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) base[k] = ((x - k) & 3) * Q + ((x - k) >> 2);
       for (int g = lane; g < groups; g += 32) {
         const int d0 = 4 * g;
         uint32_t packed = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-          const int j = x - d0 - k;   // right pixel
-          const bool ok = d0 + k < D && j >= 0;
+          const bool ok = d0 + k < D && d0 + k <= x;
           // (index 0 where there is no candidate: every address stays in the row)
-          const uint64_t b = srt[ok ? (j & 3) * Q + (j >> 2) : 0];
+          const uint64_t b = srt[ok ? base[k] - g : 0];
           const uint32_t c = ok ? (uint32_t)__popcll(a ^ b) : (uint32_t)cmax;
           packed |= c << (8 * k);
         }
@@ -113,16 +116,17 @@ __global__ void __launch_bounds__(1024, 1)
     uint32_t* dr = reinterpret_cast<uint32_t*>(CR + (size_t)y * W * Dp);
     for (int x = warp; x < W; x += nw) {
       const uint32_t* src = reinterpret_cast<const uint32_t*>(band + x * Ds);
+      const int diag = x * Ds;   // band[x + d][d] = band[diag + d (Ds + 1)]
       for (int g = lane; g < groups; g += 32) {
         dl[x * groups + g] = src[g];
         const int d0 = 4 * g;
+        const int o0 = diag + d0 * (Ds + 1);
         uint32_t packed = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-          const int xl = x + d0 + k;
-          const uint32_t v = band[xl < W ? xl * Ds + d0 + k : 0];
-          const uint32_t c = xl < W ? v : (uint32_t)cmax;
-          packed |= c << (8 * k);
+          const bool in = x + d0 + k < W;
+          const uint32_t v = band[in ? o0 + k * (Ds + 1) : 0];
+          packed |= (in ? v : (uint32_t)cmax) << (8 * k);
         }
         dr[x * groups + g] = packed;
       }
