@@ -160,9 +160,10 @@ def bytes_model(stage, N, D, passes=4):
     return 3 * N * D
 
 
-def measured_traffic(stage):
+def measured_traffic(stage, shape=None):
     """DRAM bytes per launch of `stage` from the committed ncu capture, or None
-    when there is none or the kernel sources changed since it was taken."""
+    when there is none, the kernel sources changed since it was taken, or it
+    was taken with another sweep shape ("DCxHALO") than the one timed."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -170,7 +171,11 @@ def measured_traffic(stage):
         h = hashlib.sha256()
         for src in rec["sources"]:
             h.update(open(os.path.join(ROOT, src), "rb").read())
-        return rec["bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        if rec.get("shape", "any") != "any" and rec.get("shape") != shape:
+            return None
+        return rec["bytes_per_launch"]
     except (OSError, ValueError, KeyError, TypeError, AttributeError):
         return None
 
@@ -257,7 +262,12 @@ def run_ours(args, world, rank, local):
     hbm_peak, peak_kind = peaks()
     algo_bytes = bytes_model(dominant, N, D_MAX)
     achieved = algo_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = measured_traffic(dominant)
+    shape_now = None
+    if tuned and tuned.get("classes"):
+        shape_now = f'{tuned["classes"][0]["dc"]}x{tuned["classes"][0]["halo"]}'
+    elif args.no_autotune:
+        shape_now = "8x16"   # built-in rule for D = 128
+    traffic = measured_traffic(dominant, shape_now)
 
     e2e = None
     if not args.no_e2e:
