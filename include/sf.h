@@ -430,8 +430,8 @@ sf_status sf_confnet_train_step(float* params, float* adam_m, float* adam_v, con
 sf_status sf_confnet_adam(float* params, float* adam_m, float* adam_v, const float* grad,
                           const sf_confnet_hparams* hp, void* stream);
 
-/* Workspace bytes of sf_sgm_learned (npairs = 1) or sf_scene_flow_learned
- * (npairs = 2). */
+/* Workspace bytes of sf_sgm_learned (npairs = 1), sf_scene_flow_learned
+ * (npairs = 2) or sf_scene_flow_learned_frames (npairs = 2 n); npairs <= 4. */
 size_t sf_learned_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p, int32_t npairs);
 
 /* Stereo with learned confidence: census, the left-reference cost, the eight
@@ -454,6 +454,32 @@ sf_status sf_scene_flow_learned(const uint8_t* left_t, const uint8_t* right_t, c
                                 const void* packed, float threshold, float* s4_out, float* motion_out,
                                 float* point_out, uint8_t* valid_out, float* D0_out, float* D1_out,
                                 void* workspace, size_t ws_bytes, void* stream);
+
+/* One frame of sf_scene_flow_learned_frames: the four images (same pitch
+ * and size for every frame), the flow and the outputs, as in
+ * sf_scene_flow_learned. */
+typedef struct {
+  const uint8_t* left_t;
+  const uint8_t* right_t;
+  const uint8_t* left_t1;
+  const uint8_t* right_t1;
+  const float* flow;
+  float* s4_out;
+  float* motion_out;
+  float* point_out;
+  uint8_t* valid_out;
+  float* D0_out;
+  float* D1_out;
+} sf_learned_frame;
+
+/* sf_scene_flow_learned for n frames of one size (n = 1 or 2): their 2n
+ * left passes share the sweep launches, so two frames keep as many SMs busy
+ * as the four passes of one plain frame.  Workspace of
+ * sf_learned_workspace_size(W, H, p, 2 n). */
+sf_status sf_scene_flow_learned_frames(const sf_learned_frame* frames, int32_t n, int32_t pitch, int32_t W,
+                                       int32_t H, const sf_sgm_params* p, const sf_camera* cam,
+                                       const void* packed, float threshold, void* workspace, size_t ws_bytes,
+                                       void* stream);
 
 #ifdef __cplusplus
 }

@@ -32,7 +32,7 @@ EXPORTED = [
     "sf_sgm_aggregate_noalloc", "sf_confnet_param_count", "sf_confnet_packed_bytes",
     "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
     "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
-    "sf_scene_flow_learned", "sf_debug_set",
+    "sf_scene_flow_learned", "sf_scene_flow_learned_frames", "sf_debug_set",
 ]
 
 SF_DEBUG_SPIN_LIMIT = 1
@@ -136,6 +136,8 @@ def load(path: str = LIB_PATH):
             "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
             "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
             "sf_debug_set": (i32, [i32, ctypes.c_int64]),
+            "sf_scene_flow_learned_frames": (i32, [P, i32, i32, i32, i32, PP, PC, P, ctypes.c_float, P, sz,
+                                                   P]),
             "sf_confnet_param_count": (i32, []),
             "sf_confnet_packed_bytes": (sz, []),
             "sf_confnet_pack": (i32, [P, P, P]),
@@ -549,3 +551,30 @@ def sf_scene_flow_learned(images, flow, p: SgmParams, cam: Camera, packed, thres
                                         _ptr(out["D0"]), _ptr(out["D1"]), _ptr(ws), ws.numel(),
                                         _stream(stream)))
     return out
+
+
+class LearnedFrame(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("left_t", "right_t", "left_t1", "right_t1", "flow",
+                                                 "s4_out", "motion_out", "point_out", "valid_out",
+                                                 "D0_out", "D1_out")]
+
+
+def sf_scene_flow_learned_frames(scenes, p: SgmParams, cam: Camera, packed, threshold, ws=None,
+                                 outs=None, stream=None):
+    """scenes: list of (images, flow) of one size; returns the outputs per frame."""
+    H, W = scenes[0][0][0].shape
+    dev = scenes[0][0][0].device
+    n = len(scenes)
+    if ws is None:
+        ws = learned_workspace(W, H, p, 2 * n, dev)
+    if outs is None:
+        outs = [alloc_scene_flow_outputs(W, H, dev) for _ in range(n)]
+    arr = (LearnedFrame * n)()
+    for k, ((imgs, flow), o) in enumerate(zip(scenes, outs)):
+        arr[k] = LearnedFrame(*[_ptr(v) for v in (imgs[0], imgs[1], imgs[2], imgs[3], flow, o["s4"],
+                                                  o["motion"], o["point"], o["valid"], o["D0"], o["D1"])])
+    _check("sf_scene_flow_learned_frames",
+           load().sf_scene_flow_learned_frames(arr, n, W, W, H, ctypes.byref(p), ctypes.byref(cam),
+                                               _ptr(packed), float(threshold), _ptr(ws), ws.numel(),
+                                               _stream(stream)))
+    return outs

@@ -1100,7 +1100,7 @@ struct LearnedPair {
 
 struct LearnedPlan {
   size_t err = 0, counters = 0, control_bytes = 0, total = 0;
-  LearnedPair pr[2];
+  LearnedPair pr[fused::kMaxPass];
   LearnedPlan(int W, int H, int D, int npairs) {
     const size_t N = (size_t)W * H;
     const int J = (W + fused::kTW - 1) / fused::kTW;
@@ -1157,7 +1157,7 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
   const int D = p->D, Dp = fused::padded_d(D);
   const int J = (W + fused::kTW - 1) / fused::kTW;
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
-  fused::PassDesc d[2];
+  fused::PassDesc d[fused::kMaxPass];
   for (int k = 0; k < npairs; k++) {
     const LearnedPair& b = plan.pr[k];
     uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b.census_l);
@@ -1309,7 +1309,7 @@ sf_status sf_confnet_adam(float* params, float* adam_m, float* adam_v, const flo
 
 size_t sf_learned_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p, int32_t npairs) {
   if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
-  if (npairs != 1 && npairs != 2) return 0;
+  if (npairs < 1 || npairs > fused::kMaxPass) return 0;
   return LearnedPlan(W, H, p->D, npairs).total;
 }
 
@@ -1328,36 +1328,60 @@ sf_status sf_sgm_learned(const uint8_t* left, const uint8_t* right, int32_t W, i
                            &valid_out, &disp_out, &features_out, (uint8_t*)workspace, (cudaStream_t)stream);
 }
 
+sf_status sf_scene_flow_learned_frames(const sf_learned_frame* frames, int32_t n, int32_t pitch, int32_t W,
+                                       int32_t H, const sf_sgm_params* p, const sf_camera* cam,
+                                       const void* packed, float threshold, void* workspace, size_t ws_bytes,
+                                       void* stream) {
+  sf_status st = check_learned(W, H, p);
+  if (st != SF_OK) return st;
+  if (!frames || n < 1 || 2 * n > fused::kMaxPass) return SF_ERR_INVALID_ARG;
+  if (!cam || !packed || !workspace || pitch < W) return SF_ERR_INVALID_ARG;
+  if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
+  for (int i = 0; i < n; i++) {
+    const sf_learned_frame& f = frames[i];
+    if (!f.left_t || !f.right_t || !f.left_t1 || !f.right_t1 || !f.flow || !f.s4_out || !f.valid_out)
+      return SF_ERR_INVALID_ARG;
+    if (!aligned(f.flow, 8) || !aligned(f.s4_out, 16) || !aligned(f.motion_out, 4) ||
+        !aligned(f.point_out, 4) || !aligned(f.D0_out, 4) || !aligned(f.D1_out, 4))
+      return SF_ERR_INVALID_ARG;
+  }
+  const LearnedPlan plan(W, H, p->D, 2 * n);
+  if (ws_bytes < plan.total || !aligned(workspace, 256) || !aligned(packed, 16)) return SF_ERR_INVALID_ARG;
+  uint8_t* ws = (uint8_t*)workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint8_t* L[fused::kMaxPass];
+  const uint8_t* R[fused::kMaxPass];
+  float* disp[fused::kMaxPass];
+  for (int i = 0; i < n; i++) {
+    const sf_learned_frame& f = frames[i];
+    L[2 * i] = f.left_t;
+    R[2 * i] = f.right_t;
+    L[2 * i + 1] = f.left_t1;
+    R[2 * i + 1] = f.right_t1;
+    disp[2 * i] = f.D0_out ? f.D0_out : reinterpret_cast<float*>(ws + plan.pr[2 * i].disp);
+    disp[2 * i + 1] = f.D1_out ? f.D1_out : reinterpret_cast<float*>(ws + plan.pr[2 * i + 1].disp);
+  }
+  if ((st = run_learned_pairs(2 * n, L, R, W, H, pitch, p, packed, threshold, nullptr, nullptr, nullptr, disp,
+                              nullptr, ws, s)) != SF_OK)
+    return st;
+  for (int i = 0; i < n; i++) {
+    const sf_learned_frame& f = frames[i];
+    SF_TRY_CUDA(launch_combine(disp[2 * i], disp[2 * i + 1], f.flow, W, H, cam->f, cam->B, cam->cx, cam->cy,
+                               f.s4_out, f.motion_out, f.point_out, f.valid_out, s));
+  }
+  return SF_OK;
+}
+
 sf_status sf_scene_flow_learned(const uint8_t* left_t, const uint8_t* right_t, const uint8_t* left_t1,
                                 const uint8_t* right_t1, int32_t pitch, const float* flow, int32_t W,
                                 int32_t H, const sf_sgm_params* p, const sf_camera* cam,
                                 const void* packed, float threshold, float* s4_out, float* motion_out,
                                 float* point_out, uint8_t* valid_out, float* D0_out, float* D1_out,
                                 void* workspace, size_t ws_bytes, void* stream) {
-  sf_status st = check_learned(W, H, p);
-  if (st != SF_OK) return st;
-  if (!left_t || !right_t || !left_t1 || !right_t1 || !flow || !cam || !s4_out || !valid_out || !packed ||
-      !workspace || pitch < W)
-    return SF_ERR_INVALID_ARG;
-  if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
-  const LearnedPlan plan(W, H, p->D, 2);
-  if (ws_bytes < plan.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
-  if (!aligned(packed, 16) || !aligned(flow, 8) || !aligned(s4_out, 16) || !aligned(motion_out, 4) ||
-      !aligned(point_out, 4) || !aligned(D0_out, 4) || !aligned(D1_out, 4))
-    return SF_ERR_INVALID_ARG;
-  uint8_t* ws = (uint8_t*)workspace;
-  cudaStream_t s = (cudaStream_t)stream;
-  float* D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + plan.pr[0].disp);
-  float* D1 = D1_out ? D1_out : reinterpret_cast<float*>(ws + plan.pr[1].disp);
-  const uint8_t* L[2] = {left_t, left_t1};
-  const uint8_t* R[2] = {right_t, right_t1};
-  float* disp[2] = {D0, D1};
-  if ((st = run_learned_pairs(2, L, R, W, H, pitch, p, packed, threshold, nullptr, nullptr, nullptr, disp,
-                              nullptr, ws, s)) != SF_OK)
-    return st;
-  SF_TRY_CUDA(launch_combine(D0, D1, flow, W, H, cam->f, cam->B, cam->cx, cam->cy, s4_out, motion_out,
-                             point_out, valid_out, s));
-  return SF_OK;
+  const sf_learned_frame f = {left_t, right_t, left_t1, right_t1, flow, s4_out, motion_out, point_out,
+                              valid_out, D0_out, D1_out};
+  return sf_scene_flow_learned_frames(&f, 1, pitch, W, H, p, cam, packed, threshold, workspace, ws_bytes,
+                                      stream);
 }
 
 }  // extern "C"

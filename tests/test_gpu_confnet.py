@@ -295,3 +295,21 @@ def test_learned_path_rejects_partial_path_masks(sf):
     with pytest.raises(sf.SFError):
         sf.sf_sgm_learned(to_dev(q.left_t), to_dev(q.right_t), p, packed=None)
     torch.cuda.synchronize()
+
+
+def test_two_frames_per_launch_equal_single_frames(sf):
+    import torch
+    theta = synth.confnet_init(5, LAYERS)
+    packed = sf.confnet_pack(torch.from_numpy(theta).cuda())
+    quads = [synth.fronto_planes(W=130, H=41, D=32, disparities=(2, 10, 27), seed=s) for s in (31, 32)]
+    cam = sf.camera(quads[0].camera.f, quads[0].camera.B, quads[0].camera.cx, quads[0].camera.cy)
+    p = sf.params(D=32)
+    scenes = [([to_dev(im) for im in q.images()], to_dev(q.flow)) for q in quads]
+    both = sf.sf_scene_flow_learned_frames(scenes, p, cam, packed, 0.4)
+    torch.cuda.synchronize()
+    for (imgs, flow), o in zip(scenes, both):
+        one = sf.sf_scene_flow_learned(imgs, flow, p, cam, packed, 0.4)
+        torch.cuda.synchronize()
+        for k in ("s4", "motion", "point", "valid", "D0", "D1"):
+            a, b = to_np(o[k]), to_np(one[k])
+            assert np.array_equal(np.nan_to_num(a, nan=-3.0), np.nan_to_num(b, nan=-3.0)), k
