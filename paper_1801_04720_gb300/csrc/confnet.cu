@@ -45,11 +45,8 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int kMaxPerLane = SF_MAX_DISPARITY / 32;
 
-__device__ __forceinline__ uint32_t warp_min(uint32_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFullMask, v, o));
-  return v;
-}
+// minimum over the warp (every lane gets it): one warp-reduction instruction
+__device__ __forceinline__ uint32_t warp_min(uint32_t v) { return __reduce_min_sync(kFullMask, v); }
 
 // One pixel's curve, spread over the warp: lane l holds d = l + 32 k.
 struct Curve {
@@ -171,53 +168,24 @@ __global__ void __launch_bounds__(256)
   if (in_b) finish_pixel(a, cb, xb, pb, lane, 1);
 }
 
-// Vector form (D % 4 == 0): one warp per pixel, lane l holding disparities
-// 4l .. 4l+3 (+128 for a second chunk): 8-byte loads of S, 4-byte loads of
-// the horizontal paths, 16-byte loads of the partial-sum words.
+// Vector form (D % 4 == 0): one warp per column pair (x, x + 16) of a
+// 32-column strip row (the pair shares the words of the down sweep's partial
+// sum); lane l holds disparities 4l .. 4l+3 (+128 for a second chunk) of
+// both columns: 8-byte loads of S, 4-byte loads of the horizontal paths,
+// 16-byte loads of the partial-sum words.
+struct VecCurve {
+  uint32_t ks, kh, kd, ku;
+};
+
 template <int NCH>
-__global__ void __launch_bounds__(256)
-    features_vec_kernel(FeatureArgs a) {
-  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (warp >= a.W * a.H) return;
-  const int y = warp / a.W, x = warp - y * a.W;
-  const size_t pix = (size_t)y * a.W + x;
-  const int j = x >> 5, c = x & 31, pr = c & 15, hi = c >> 4;
-  const uint32_t* sd = a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape;
-  uint32_t sv[4 * NCH];
-  uint32_t ks = 0xffffffffu, kh = 0xffffffffu, kd = 0xffffffffu, ku = 0xffffffffu;
-#pragma unroll
-  for (int ch = 0; ch < NCH; ch++) {
-    const int d0 = 128 * ch + 4 * lane;
-    if (d0 < a.D) {
-      const uint2 s4 = *reinterpret_cast<const uint2*>(a.S + pix * a.D + d0);
-      const uint32_t hf4 = *reinterpret_cast<const uint32_t*>(a.hfwd + pix * a.Dp + d0);
-      const uint32_t hb4 = *reinterpret_cast<const uint32_t*>(a.hbwd + pix * a.Dp + d0);
-      const uint4 w4 = *reinterpret_cast<const uint4*>(sd + d0);
-      const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
-      const uint32_t ss[4] = {s4.x & 0xffffu, s4.x >> 16, s4.y & 0xffffu, s4.y >> 16};
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const uint32_t d = (uint32_t)(d0 + e);
-        const uint32_t gh = ((hf4 >> (8 * e)) & 0xffu) + ((hb4 >> (8 * e)) & 0xffu);
-        const uint32_t gd = hi ? (ww[e] >> 16) : (ww[e] & 0xffffu);
-        sv[4 * ch + e] = ss[e];
-        ks = min(ks, (ss[e] << 8) | d);
-        kh = min(kh, (gh << 8) | d);
-        kd = min(kd, (gd << 8) | d);
-        ku = min(ku, ((ss[e] - gh - gd) << 8) | d);
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < 4; e++) sv[4 * ch + e] = 0xffffffffu;
-    }
-  }
-  ks = warp_min(ks);
-  kh = warp_min(kh);
-  kd = warp_min(kd);
-  ku = warp_min(ku);
-  const int ds = (int)(ks & 0xffu);
-  const uint32_t s0 = ks >> 8;
+__device__ __forceinline__ void vec_finish(const FeatureArgs& a, const uint32_t* sv, VecCurve c, int x,
+                                           size_t pix, int lane, int out_lane) {
+  c.ks = warp_min(c.ks);
+  c.kh = warp_min(c.kh);
+  c.kd = warp_min(c.kd);
+  c.ku = warp_min(c.ku);
+  const int ds = (int)(c.ks & 0xffu);
+  const uint32_t s0 = c.ks >> 8;
   uint32_t far = 0xffffffffu, vm = 0u, vp = 0u;
 #pragma unroll
   for (int ch = 0; ch < NCH; ch++) {
@@ -234,7 +202,7 @@ __global__ void __launch_bounds__(256)
   far = warp_min(far);
   vm = __shfl_sync(kFullMask, vm, ((ds + 127) >> 2) & 31);   // lane of d* - 1
   vp = __shfl_sync(kFullMask, vp, ((ds + 1) >> 2) & 31);     // lane of d* + 1
-  if (lane != 0) return;
+  if (lane != out_lane) return;
   const int cstar = a.cost[pix * a.Dp + ds];
   const uint32_t s2 = far == 0xffffffffu ? s0 : far;
   int curv = 0, rise = 0;
@@ -251,8 +219,8 @@ __global__ void __launch_bounds__(256)
       rise = min(am, bp);
     }
   }
-  const int dis = min(abs((int)(kh & 0xffu) - ds), 16) + min(abs((int)(kd & 0xffu) - ds), 16) +
-                  min(abs((int)(ku & 0xffu) - ds), 16);
+  const int dis = min(abs((int)(c.kh & 0xffu) - ds), 16) + min(abs((int)(c.kd & 0xffu) - ds), 16) +
+                  min(abs((int)(c.ku & 0xffu) - ds), 16);
   const int margin = min(max(x - ds, 0), 64);
   const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
                        (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
@@ -272,6 +240,69 @@ __global__ void __launch_bounds__(256)
     v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
   }
   a.dsub[pix] = v;
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(256)
+    features_vec_kernel(FeatureArgs a) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int per_row = a.J * 16;
+  if (warp >= a.H * per_row) return;
+  const int y = warp / per_row, r = warp - y * per_row;
+  const int j = r >> 4, pr = r & 15;
+  const int xa = j * 32 + pr, xb = xa + 16;
+  const bool in_a = xa < a.W, in_b = xb < a.W;
+  const size_t pa = (size_t)y * a.W + xa, pb = (size_t)y * a.W + xb;
+  const uint32_t* sd = a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape;
+  uint32_t sa[4 * NCH], sb[4 * NCH];
+  VecCurve ca = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu}, cb = ca;
+#pragma unroll
+  for (int ch = 0; ch < NCH; ch++) {
+    const int d0 = 128 * ch + 4 * lane;
+    uint2 s4a = make_uint2(0xffffffffu, 0xffffffffu), s4b = s4a;
+    uint32_t hfa = 0, hba = 0, hfb = 0, hbb = 0;
+    uint4 w4 = make_uint4(0, 0, 0, 0);
+    const bool live = d0 < a.D;
+    if (live) {
+      w4 = *reinterpret_cast<const uint4*>(sd + d0);
+      if (in_a) {
+        s4a = *reinterpret_cast<const uint2*>(a.S + pa * a.D + d0);
+        hfa = *reinterpret_cast<const uint32_t*>(a.hfwd + pa * a.Dp + d0);
+        hba = *reinterpret_cast<const uint32_t*>(a.hbwd + pa * a.Dp + d0);
+      }
+      if (in_b) {
+        s4b = *reinterpret_cast<const uint2*>(a.S + pb * a.D + d0);
+        hfb = *reinterpret_cast<const uint32_t*>(a.hfwd + pb * a.Dp + d0);
+        hbb = *reinterpret_cast<const uint32_t*>(a.hbwd + pb * a.Dp + d0);
+      }
+    }
+    const uint32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+    const uint32_t ssa[4] = {s4a.x & 0xffffu, s4a.x >> 16, s4a.y & 0xffffu, s4a.y >> 16};
+    const uint32_t ssb[4] = {s4b.x & 0xffffu, s4b.x >> 16, s4b.y & 0xffffu, s4b.y >> 16};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const uint32_t d = (uint32_t)(d0 + e);
+      sa[4 * ch + e] = live ? ssa[e] : 0xffffffffu;
+      sb[4 * ch + e] = live ? ssb[e] : 0xffffffffu;
+      if (live) {
+        const uint32_t gha = ((hfa >> (8 * e)) & 0xffu) + ((hba >> (8 * e)) & 0xffu);
+        const uint32_t gda = ww[e] & 0xffffu;
+        ca.ks = min(ca.ks, (ssa[e] << 8) | d);
+        ca.kh = min(ca.kh, (gha << 8) | d);
+        ca.kd = min(ca.kd, (gda << 8) | d);
+        ca.ku = min(ca.ku, ((ssa[e] - gha - gda) << 8) | d);
+        const uint32_t ghb = ((hfb >> (8 * e)) & 0xffu) + ((hbb >> (8 * e)) & 0xffu);
+        const uint32_t gdb = ww[e] >> 16;
+        cb.ks = min(cb.ks, (ssb[e] << 8) | d);
+        cb.kh = min(cb.kh, (ghb << 8) | d);
+        cb.kd = min(cb.kd, (gdb << 8) | d);
+        cb.ku = min(cb.ku, ((ssb[e] - ghb - gdb) << 8) | d);
+      }
+    }
+  }
+  if (in_a) vec_finish<NCH>(a, sa, ca, xa, pa, lane, 0);
+  if (in_b) vec_finish<NCH>(a, sb, cb, xb, pb, lane, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,16 +517,39 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   const uint32_t w2_base = w_base + kW1Elems * 2, w3_base = w2_base + kW2Elems * 2;
   const uint32_t w4_base = w3_base + kW2Elems * 2;
 
-  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int X0 = (tile % tiles_x) * kTX, Y0 = (tile / tiles_x) * kTY;
-    // ---- features of region 0 (origin X0-4, Y0-4), zero outside the image ----
+  // features of a tile's region 0 (origin X0-4, Y0-4; zeros outside the
+  // image) by asynchronous copies, so that the next tile's arrive while this
+  // tile's layers 2-4 run
+  auto fetch_features = [&](int tl) {
+    const int X0 = (tl % tiles_x) * kTX, Y0 = (tl / tiles_x) * kTY;
     for (int i = tid; i < region_rows(0) * kP; i += kThreads) {
       const int gy = Y0 - 4 + i / kP, gx = X0 - 4 + i % kP;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-        v = reinterpret_cast<const uint4*>(a.feat)[(size_t)gy * a.W + gx];
-      reinterpret_cast<uint4*>(feat_s)[i] = v;
+      const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+      const void* src = in ? static_cast<const void*>(reinterpret_cast<const uint4*>(a.feat) + (size_t)gy * a.W + gx)
+                           : a.feat;
+      const unsigned d = smem_u32(feat_s + 16 * i);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(in ? 16 : 0)
+                   : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // descriptors of the operands at M tile 0; a tap, an input plane or an M
+  // tile adds to the start-address field (16-byte units, no carry below 256 KB)
+  uint64_t ad1[5], bd1[5];
+#pragma unroll
+  for (int j = 0; j < 5; j++) {
+    const int o0 = tap_off(2 * j), o1 = tap_off(2 * j + 1);
+    ad1[j] = mat_desc(smem_u32(feat_s) + 16u * (uint32_t)o0, 16u * (uint32_t)(o1 - o0), 128u);
+    bd1[j] = mat_desc(w_base + (uint32_t)j * 2u * kC * 16u, kC * 16u, 128u);
+  }
+  const uint64_t ad2 = mat_desc(smem_u32(bufx), kPlane1, 128u), bd2 = mat_desc(w2_base, kC * 16u, 128u);
+  const uint64_t ad3 = mat_desc(smem_u32(bufy), kPlane2, 128u), bd3 = mat_desc(w3_base, kC * 16u, 128u);
+  const uint64_t ad4 = mat_desc(smem_u32(bufx), kPlane3, 128u), bd4 = mat_desc(w4_base, 16u * 16u, 128u);
+
+  if (blockIdx.x < ntiles) fetch_features(blockIdx.x);
+  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int X0 = (tile % tiles_x) * kTX, Y0 = (tile / tiles_x) * kTY;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -510,27 +564,23 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
       if (tid == 0) {
         fence_after();
         if (layer == 0) {
-          const uint32_t ab = smem_u32(feat_s);
           for (int mt = 0; mt < nm; mt++) {
-            for (int j = 0; j < 5; j++) {
-              const int o0 = tap_off(2 * j), o1 = tap_off(2 * j + 1);
-              const uint64_t ad = mat_desc(ab + 16u * (uint32_t)(128 * mt + o0), 16u * (uint32_t)(o1 - o0), 128u);
-              const uint64_t bd = mat_desc(w_base + (uint32_t)j * 2u * kC * 16u, kC * 16u, 128u);
-              mma_bf16(tmem + (uint32_t)(kC * mt), ad, bd, idesc, j > 0);
-            }
+#pragma unroll
+            for (int j = 0; j < 5; j++)
+              mma_bf16(tmem + (uint32_t)(kC * mt), ad1[j] + 128u * mt, bd1[j], idesc, j > 0);
           }
         } else {
-          const uint32_t ab = smem_u32(layer == 2 ? bufy : bufx);
-          const uint32_t plane = layer == 1 ? kPlane1 : layer == 2 ? kPlane2 : kPlane3;
-          const uint32_t wb = layer == 1 ? w2_base : layer == 2 ? w3_base : w4_base;
+          const uint64_t ab = layer == 1 ? ad2 : layer == 2 ? ad3 : ad4;
+          const uint64_t bb = layer == 1 ? bd2 : layer == 2 ? bd3 : bd4;
+          const uint32_t plane16 = (layer == 1 ? kPlane1 : layer == 2 ? kPlane2 : kPlane3) / 16;
           for (int mt = 0; mt < nm; mt++) {
+            const uint64_t am = ab + 128u * mt;
+#pragma unroll
             for (int t = 0; t < 9; t++) {
-              for (int s = 0; s < 2; s++) {
-                const uint64_t ad =
-                    mat_desc(ab + 2u * s * plane + 16u * (uint32_t)(128 * mt + tap_off(t)), plane, 128u);
-                const uint64_t bd = mat_desc(wb + (uint32_t)(2 * t + s) * 2u * N * 16u, (uint32_t)N * 16u, 128u);
-                mma_bf16(tmem + (uint32_t)(N * mt), ad, bd, idesc, (t | s) != 0);
-              }
+#pragma unroll
+              for (int s = 0; s < 2; s++)
+                mma_bf16(tmem + (uint32_t)(N * mt), am + 2u * s * plane16 + (uint32_t)tap_off(t),
+                         bb + (uint32_t)(2 * t + s) * 2u * N, idesc, (t | s) != 0);
             }
           }
         }
@@ -547,6 +597,8 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
       }
       phase ^= 1u;
       failed = __syncthreads_or(timed_out) != 0;
+      // layer 1 has read the features: the next tile's may come in
+      if (layer == 0 && !failed && tile + (int)gridDim.x < ntiles) fetch_features(tile + gridDim.x);
       if (failed) {
         if (tid == 0) atomicExch(a.err, 1);
         break;
@@ -602,6 +654,7 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
       __syncthreads();
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy left in flight
   fence_before();
   __syncthreads();
   fence_after();
@@ -829,7 +882,7 @@ __global__ void adam_kernel(float* th, float* m, float* v, const float* g, int n
 cudaError_t launch_features(const FeatureArgs& a, cudaStream_t s) {
   count_launches(1);
   if (a.D % 4 == 0) {
-    const size_t threads = (size_t)a.W * a.H * 32;
+    const size_t threads = (size_t)a.J * 16 * a.H * 32;
     if (a.D <= 128)
       features_vec_kernel<1><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
     else
