@@ -421,6 +421,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// one lane of a converged warp (the warp's loop values stay uniform)
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n .reg .pred P;\n elect.sync _|P, 0xffffffff;\n selp.b32 %0, 1, 0, P;\n}\n"
+      : "=r"(pred));
+  return pred != 0;
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -560,14 +569,15 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
       const int nm = out_rows * kP / 128;
       const int N = layer == 3 ? 16 : kC;
       const uint32_t idesc = instr_desc(N);
-      // ---- issue: one thread, all M tiles of the layer ----
-      if (tid == 0) {
+      // ---- issue: warp 0 walks the MMAs of all M tiles (warp-uniform
+      // descriptors), one elected lane issues each ----
+      if (warp == 0) {
         fence_after();
         if (layer == 0) {
           for (int mt = 0; mt < nm; mt++) {
 #pragma unroll
             for (int j = 0; j < 5; j++)
-              mma_bf16(tmem + (uint32_t)(kC * mt), ad1[j] + 128u * mt, bd1[j], idesc, j > 0);
+              if (elect_one()) mma_bf16(tmem + (uint32_t)(kC * mt), ad1[j] + 128u * mt, bd1[j], idesc, j > 0);
           }
         } else {
           const uint64_t ab = layer == 1 ? ad2 : layer == 2 ? ad3 : ad4;
@@ -579,12 +589,14 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
             for (int t = 0; t < 9; t++) {
 #pragma unroll
               for (int s = 0; s < 2; s++)
-                mma_bf16(tmem + (uint32_t)(N * mt), am + 2u * s * plane16 + (uint32_t)tap_off(t),
-                         bb + (uint32_t)(2 * t + s) * 2u * N, idesc, (t | s) != 0);
+                if (elect_one())
+                  mma_bf16(tmem + (uint32_t)(N * mt), am + 2u * s * plane16 + (uint32_t)tap_off(t),
+                           bb + (uint32_t)(2 * t + s) * 2u * N, idesc, (t | s) != 0);
             }
           }
         }
-        mma_commit(barp);
+        if (elect_one()) mma_commit(barp);
+        __syncwarp();
       }
       // ---- wait for the layer's accumulators (bounded) ----
       long long spins = 0;
