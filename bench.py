@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--learned-eval", type=int, default=200,
                     help="held-out scenes for the learned path's false-accept rate "
                          "(0 = timing only, -1 = skip the learned path)")
+    ap.add_argument("--stream", type=int, default=2,
+                    help="frames of the 2048x1024, D=256 stream recipe to time (0 = skip)")
     ap.add_argument("--shape", default=None,
                     help="sweep shape DCxHALO for the frame's disparity class instead of the "
                          "autotuner (e.g. 16x16, as in profiling runs)")
@@ -50,6 +52,7 @@ def parse():
         args.batch = 0
         args.no_autotune = True
         args.learned_eval = -1
+        args.stream = 0
     return args
 
 
@@ -316,6 +319,8 @@ def run_ours(args, world, rank, local):
     if args.learned_eval >= 0:
         result["learned"] = run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush,
                                         result["value"])
+    if args.stream > 0:
+        result["stream"] = run_stream(args, dev, _lib, torch, flush)
     return result, q
 
 
@@ -443,13 +448,88 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
            "automotive_frame": {k: round(v, 5) for k, v in frame_rates.items()}}
     n_eval = min(args.learned_eval, len(train_confnet.EVAL_SEEDS))
     if n_eval > 0:
-        seeds = list(train_confnet.EVAL_SEEDS)[:n_eval]
-        pairs = train_confnet.render_pairs(seeds, W, H, D_MAX)
-        ev = train_confnet.rates(train_confnet.decisions(_lib, packed, pairs, D_MAX), thr)
-        res["eval"] = {"scenes": n_eval, "seeds": [seeds[0], seeds[-1]],
-                       "recipe": "fronto-parallel plane recipe at 1242x375, D=128",
-                       **{k: round(v, 5) for k, v in ev.items()}}
+        # held-out scenes of both training recipes (never trained or calibrated on)
+        res["eval"] = {}
+        for name, all_seeds, n, recipe in (
+                ("planes", train_confnet.EVAL_SEEDS, n_eval,
+                 "fronto-parallel plane recipe at 1242x375, D=128, pair at t"),
+                ("automotive", train_confnet.AUTO_EVAL_SEEDS, min(max(n_eval // 4, 1), len(train_confnet.AUTO_EVAL_SEEDS)),
+                 "automotive recipe at 1242x375, D=128, pairs at t and t+1")):
+            seeds = list(all_seeds)[:n]
+            pairs = train_confnet.render_pairs(seeds, W, H, D_MAX, recipe=name)
+            ev = train_confnet.rates(train_confnet.decisions(_lib, packed, pairs, D_MAX), thr)
+            res["eval"][name] = {"scenes": n, "pairs": len(pairs), "seeds": [seeds[0], seeds[-1]],
+                                 "recipe": recipe, **{k: round(v, 5) for k, v in ev.items()}}
     return res
+
+
+def _stream_frame(k):
+    from paper_1801_04720_gb300 import synth
+    return synth.automotive(seed=k, W=2048, H=1024, D=256, n_segments=40)
+
+
+def run_stream(args, dev, _lib, torch, flush):
+    """The large-stream configuration: 2048x1024 quadruples, D = 256 (40
+    moving segments), plain path per frame and the learned path two frames
+    per launch, the plain check judging the learned one.  The frames are
+    rendered on the host in spawned workers; each timed step reuses them."""
+    import multiprocessing as mp
+    from paper_1801_04720_gb300 import train_confnet
+    n = max(2, args.stream - args.stream % 2)
+    with mp.get_context("spawn").Pool(min(n, 8)) as pool:
+        frames = pool.map(_stream_frame, range(n))
+    H, W = frames[0].shape
+    D = frames[0].D
+    p = _lib.params(D=D)
+    cam = _lib.camera(frames[0].camera.f, frames[0].camera.B, frames[0].camera.cx, frames[0].camera.cy)
+    dimgs = [[torch.from_numpy(im).to(dev) for im in q.images()] for q in frames]
+    dflow = [torch.from_numpy(q.flow).to(dev) for q in frames]
+    ws = _lib.workspace(W, H, p, dev)
+    out = _lib.alloc_scene_flow_outputs(W, H, dev)
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 8))
+
+    def timed(fn, k_of):
+        for k in range(2):
+            fn(k_of(k))
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k_of(k))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.mean(ms)
+
+    ms_plain = timed(lambda k: _lib.sf_scene_flow(dimgs[k], dflow[k], p, cam, ws=ws, out=out, stream=stream),
+                     lambda k: k % n)
+    theta, meta = train_confnet.load()
+    packed = _lib.confnet_pack(torch.from_numpy(theta).to(dev))
+    thr = float(meta["threshold"])
+    ws2 = _lib.learned_workspace(W, H, p, 4, dev)
+    outs2 = [_lib.alloc_scene_flow_outputs(W, H, dev) for _ in range(2)]
+    ms_learned = timed(lambda k: _lib.sf_scene_flow_learned_frames(
+        [(dimgs[2 * k], dflow[2 * k]), (dimgs[2 * k + 1], dflow[2 * k + 1])], p, cam, packed, thr,
+        ws=ws2, outs=outs2, stream=stream), lambda k: k % (n // 2))
+    dec = []
+    ws1 = _lib.learned_workspace(W, H, p, 1, dev)
+    for k in range(n):
+        plain = _lib.sf_sgm_full(dimgs[k][0], dimgs[k][1], p, ws=ws)
+        lo = _lib.sf_sgm_learned(dimgs[k][0], dimgs[k][1], p, packed=packed, threshold=thr, ws=ws1)
+        dec.append((lo["prob"], lo["dint"], plain["valid"]))
+    rates = train_confnet.rates(dec, thr)
+    N = W * H
+    return {"workload": f"automotive stream {W}x{H} D={D}, 40 moving segments, {n} frames rendered",
+            "plain": {"value": round(1000.0 / ms_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain, 3),
+                      "Gcost_entries_per_s": round(4 * N * D / (ms_plain * 1e-3) / 1e9, 1)},
+            "learned_two_frames_per_launch": {"value": round(2000.0 / ms_learned, 2), "unit": "frames/s",
+                                              "ms_per_step": round(ms_learned, 3)},
+            "learned_vs_plain_check": {k: round(v, 5) for k, v in rates.items()},
+            "parity": "frame 0 of this recipe against the oracle in tests/test_gpu_fullsize.py "
+                      "(integers bit-exact); the oracle is not timed here"}
 
 
 def cpu_baseline(q):

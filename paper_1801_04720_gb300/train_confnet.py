@@ -1,6 +1,9 @@
 """Training, calibration and evaluation of the learned confidence network.
 
-Labels come from the plain method itself: a pixel of the left pass is a
+Two scene recipes feed it: the fronto-parallel plane recipe and the
+automotive recipe (slanted moving segments over a ground plane and a far
+wall), both at 1242x375, D = 128; from the automotive recipe both stereo
+pairs of a quadruple are used.  Labels come from the plain method itself: a pixel of the left pass is a
 positive when the left-right check (Sec. 3.1, tolerance 1 px) keeps it and a
 negative when the check removes it; pixels with x - d* < 0 are left out (the
 learned path rejects them by rule).  Every step runs through libsf: the
@@ -25,24 +28,35 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "confnet_weights.npz")
 LAYERS = [(8, 32), (32, 32), (32, 32), (32, 1)]
+# plane recipe (one pair per seed)
 TRAIN_SEEDS = range(0, 2000)
 CALIB_SEEDS = range(5000, 5100)
 EVAL_SEEDS = range(10000, 10200)
+# automotive recipe (two pairs per seed); disjoint from the seeds the bench renders
+AUTO_TRAIN_SEEDS = range(20000, 20600)
+AUTO_CALIB_SEEDS = range(25000, 25040)
+AUTO_EVAL_SEEDS = range(30000, 30050)
 
 
 def _render(args):
     from paper_1801_04720_gb300 import synth
-    seed, W, H, D = args
+    seed, W, H, D, recipe = args
+    if recipe == "automotive":
+        q = synth.automotive(seed=seed, W=W, H=H, D=D)
+        return [(q.left_t, q.right_t), (q.left_t1, q.right_t1)]
     q = synth.confidence_recipe(seed, W=W, H=H, D=D)
-    return q.left_t, q.right_t
+    return [(q.left_t, q.right_t)]
 
 
-def render_pairs(seeds, W, H, D, workers=8):
-    """Left/right images at t of the confidence recipe, rendered on the host
-    in spawned worker processes."""
+def render_pairs(seeds, W, H, D, recipe="planes", workers=None):
+    """Stereo pairs of a recipe ("planes": the left/right images at t;
+    "automotive": both pairs of each quadruple), rendered on the host in
+    spawned worker processes."""
+    workers = workers or min(16, os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
     with ctx.Pool(workers) as pool:
-        return pool.map(_render, [(s, W, H, D) for s in seeds], chunksize=4)
+        per_seed = pool.map(_render, [(s, W, H, D, recipe) for s in seeds], chunksize=2)
+    return [pair for pairs in per_seed for pair in pairs]
 
 
 def label_pass(_lib, left, right, p, p_plain, ws_l, ws_p):
@@ -152,23 +166,30 @@ def calibrate(dec, target=0.01):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--scenes", type=int, default=len(TRAIN_SEEDS))
+    ap.add_argument("--auto-scenes", type=int, default=len(AUTO_TRAIN_SEEDS))
     ap.add_argument("--eval", type=int, default=len(EVAL_SEEDS))
+    ap.add_argument("--auto-eval", type=int, default=len(AUTO_EVAL_SEEDS))
     ap.add_argument("--epochs", type=int, default=12)
     ap.add_argument("--W", type=int, default=1242)
     ap.add_argument("--H", type=int, default=375)
     ap.add_argument("--D", type=int, default=128)
     ap.add_argument("--target", type=float, default=0.008,
-                    help="false-accept rate the threshold is calibrated to (held-out scenes)")
+                    help="false-accept rate the threshold is calibrated to, on the held-out "
+                         "scenes of each recipe")
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     args = ap.parse_args(argv)
     import torch
     from paper_1801_04720_gb300 import _lib, build
     t0 = time.time()
-    train_pairs = render_pairs(list(TRAIN_SEEDS)[:args.scenes], args.W, args.H, args.D)
-    calib_pairs = render_pairs(list(CALIB_SEEDS), args.W, args.H, args.D)
-    eval_pairs = render_pairs(list(EVAL_SEEDS)[:args.eval], args.W, args.H, args.D)
-    print(f"rendered {len(train_pairs)} + {len(calib_pairs)} + {len(eval_pairs)} scenes "
-          f"in {time.time() - t0:.1f} s")
+    size = (args.W, args.H, args.D)
+    train_pairs = (render_pairs(list(TRAIN_SEEDS)[:args.scenes], *size)
+                   + render_pairs(list(AUTO_TRAIN_SEEDS)[:args.auto_scenes], *size, recipe="automotive"))
+    calib = {"planes": render_pairs(list(CALIB_SEEDS), *size),
+             "automotive": render_pairs(list(AUTO_CALIB_SEEDS), *size, recipe="automotive")}
+    evals = {"planes": (list(EVAL_SEEDS)[:args.eval], render_pairs(list(EVAL_SEEDS)[:args.eval], *size)),
+             "automotive": (list(AUTO_EVAL_SEEDS)[:args.auto_eval],
+                            render_pairs(list(AUTO_EVAL_SEEDS)[:args.auto_eval], *size, recipe="automotive"))}
+    print(f"rendered {len(train_pairs)} training pairs in {time.time() - t0:.1f} s")
     build.build()
     _lib.load()
     t1 = time.time()
@@ -179,12 +200,17 @@ def main(argv=None):
     torch.cuda.synchronize()
     print(f"trained in {time.time() - t2:.1f} s")
     packed = _lib.confnet_pack(params)
-    threshold = calibrate(decisions(_lib, packed, calib_pairs, args.D), target=args.target)
-    ev = rates(decisions(_lib, packed, eval_pairs, args.D), threshold)
-    meta = {"threshold": threshold, "calibration_target": args.target, "eval": ev, "train_scenes": len(train_pairs),
-            "calib_seeds": [CALIB_SEEDS.start, CALIB_SEEDS.stop - 1],
-            "eval_seeds": [EVAL_SEEDS.start, EVAL_SEEDS.start + len(eval_pairs) - 1],
-            "size": [args.W, args.H, args.D], "epochs": args.epochs}
+    # the threshold keeps the false-accept rate within the target on each recipe
+    threshold = max(calibrate(decisions(_lib, packed, pairs, args.D), target=args.target)
+                    for pairs in calib.values())
+    ev = {name: {"seeds": [seeds[0], seeds[-1]], "pairs": len(pairs),
+                 **rates(decisions(_lib, packed, pairs, args.D), threshold)}
+          for name, (seeds, pairs) in evals.items() if seeds}
+    meta = {"threshold": threshold, "calibration_target": args.target, "eval": ev,
+            "train_pairs": len(train_pairs),
+            "calib_seeds": {"planes": [CALIB_SEEDS.start, CALIB_SEEDS.stop - 1],
+                            "automotive": [AUTO_CALIB_SEEDS.start, AUTO_CALIB_SEEDS.stop - 1]},
+            "size": list(size), "epochs": args.epochs}
     print(json.dumps(meta))
     np.savez(args.out, params=params.cpu().numpy(), meta=json.dumps(meta))
     return meta
