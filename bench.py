@@ -438,6 +438,9 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
     plain = _lib.sf_sgm_full(imgs[0], imgs[1], p)
     lo = _lib.sf_sgm_learned(imgs[0], imgs[1], p, packed=packed, threshold=thr)
     frame_rates = train_confnet.rates([(lo["prob"], lo["dint"], plain["valid"])], thr)
+    gt = [torch.from_numpy(q.gt_disp0).to(dev)]
+    frame_gt = {"plain_check": train_confnet.accuracy([plain["disp"]], gt),
+                "learned": train_confnet.accuracy([lo["disp"]], gt)}
     res = {"metric": "scene-flow frames/s, learned confidence in place of the L-R check",
            "value": round(replica_rate(ms, world), 2), "unit": "frames/s", "ms_per_step": round(ms, 4),
            "vs_plain": round(replica_rate(ms, world) / plain_fps, 3), "threshold": thr,
@@ -445,7 +448,9 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
                                      "ms_per_step": round(ms2, 4),
                                      "vs_plain": round(replica_rate(ms2, world, 2) / plain_fps, 3)},
            "gpu_launches": int(launches), "stages_ms_per_step": stages,
-           "automotive_frame": {k: round(v, 5) for k, v in frame_rates.items()}}
+           "automotive_frame": {k: round(v, 5) for k, v in frame_rates.items()},
+           "automotive_frame_vs_ground_truth": {k: {kk: round(vv, 5) for kk, vv in v.items()}
+                                                for k, v in frame_gt.items()}}
     n_eval = min(args.learned_eval, len(train_confnet.EVAL_SEEDS))
     if n_eval > 0:
         # held-out scenes of both training recipes (never trained or calibrated on)
@@ -514,13 +519,17 @@ def run_stream(args, dev, _lib, torch, flush):
     ms_learned = timed(lambda k: _lib.sf_scene_flow_learned_frames(
         [(dimgs[2 * k], dflow[2 * k]), (dimgs[2 * k + 1], dflow[2 * k + 1])], p, cam, packed, thr,
         ws=ws2, outs=outs2, stream=stream), lambda k: k % (n // 2))
-    dec = []
+    dec, dp, dl, gts = [], [], [], []
     ws1 = _lib.learned_workspace(W, H, p, 1, dev)
     for k in range(n):
         plain = _lib.sf_sgm_full(dimgs[k][0], dimgs[k][1], p, ws=ws)
         lo = _lib.sf_sgm_learned(dimgs[k][0], dimgs[k][1], p, packed=packed, threshold=thr, ws=ws1)
         dec.append((lo["prob"], lo["dint"], plain["valid"]))
+        dp.append(plain["disp"])
+        dl.append(lo["disp"])
+        gts.append(torch.from_numpy(frames[k].gt_disp0).to(dev))
     rates = train_confnet.rates(dec, thr)
+    vs_gt = {"plain_check": train_confnet.accuracy(dp, gts), "learned": train_confnet.accuracy(dl, gts)}
     N = W * H
     return {"workload": f"automotive stream {W}x{H} D={D}, 40 moving segments, {n} frames rendered",
             "plain": {"value": round(1000.0 / ms_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain, 3),
@@ -528,6 +537,7 @@ def run_stream(args, dev, _lib, torch, flush):
             "learned_two_frames_per_launch": {"value": round(2000.0 / ms_learned, 2), "unit": "frames/s",
                                               "ms_per_step": round(ms_learned, 3)},
             "learned_vs_plain_check": {k: round(v, 5) for k, v in rates.items()},
+            "vs_ground_truth": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in vs_gt.items()},
             "parity": "frame 0 of this recipe against the oracle in tests/test_gpu_fullsize.py "
                       "(integers bit-exact); the oracle is not timed here"}
 

@@ -372,7 +372,10 @@ sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const 
  *   4  d* / 128
  *   5  clamp(x - d*, 0, 64) / 64
  *   6  C(d*) / 64
- *   7  min(S(d*-1), S(d*+1)) - S0 (the one neighbour at an end) / 256
+ *   7  visibility margin / 16: with u(x) = x - d*(x) the right-image column
+ *      pixel x matches and m(x) the minimum of u over the pixels right of x
+ *      in the same row, clamp(m(x) - u(x), -16, 16); 16 for the last pixel
+ *      (<= 0: a pixel to the right covers x's match, x is occluded)
  * Each is an integer over a power of two, rounded once to bfloat16.
  *
  * Network: z1 = b1 + conv3x3(f, W1), a1 = bf16(relu(z1)); a2, a3 likewise

@@ -88,8 +88,9 @@ def features(S: np.ndarray, L: list[np.ndarray], cost: np.ndarray) -> tuple[np.n
       f4 = d* / 128
       f5 = clamp(x - d*, 0, 64) / 64
       f6 = C(d*) / 64
-      f7 = rise / 256: min(S(d*-1), S(d*+1)) - S0 inside, S(nb) - S0 at an
-           end, 0 if D = 1."""
+      f7 = visibility margin / 16 (see visibility_margin): how far the
+           pixel's match in the right image lies left of every match of the
+           pixels to its right in the same row."""
     S = np.asarray(S, dtype=np.int64)
     H, W, D = S.shape
     ds = _first_argmin(S)
@@ -102,21 +103,42 @@ def features(S: np.ndarray, L: list[np.ndarray], cost: np.ndarray) -> tuple[np.n
             far = [int(s[k]) for k in range(D) if abs(k - d) >= 2]
             s2 = min(far) if far else s0
             if D == 1:
-                curv, rise = 0, 0
+                curv = 0
             elif d == 0:
-                curv, rise = 2 * (int(s[1]) - s0), int(s[1]) - s0
+                curv = 2 * (int(s[1]) - s0)
             elif d == D - 1:
-                curv, rise = 2 * (int(s[D - 2]) - s0), int(s[D - 2]) - s0
+                curv = 2 * (int(s[D - 2]) - s0)
             else:
                 curv = int(s[d - 1]) + int(s[d + 1]) - 2 * s0
-                rise = min(int(s[d - 1]), int(s[d + 1])) - s0
             dis = 0
             for g in (GROUP_H, GROUP_DOWN, GROUP_UP):
                 sg = sum(np.asarray(L[r][y, x], dtype=np.int64) for r in g)
                 dis += min(abs(int(np.argmin(sg)) - d), 16)
             feat[y, x] = [s0 / 1024, (s2 - s0) / 256, curv / 256, dis / 16, d / 128,
-                          min(max(x - d, 0), 64) / 64, int(cost[y, x, d]) / 64, rise / 256]
+                          min(max(x - d, 0), 64) / 64, int(cost[y, x, d]) / 64, 0.0]
+    feat[:, :, 7] = visibility_margin(ds) / 16
     return bf16(feat), ds
+
+
+def visibility_margin(ds: np.ndarray) -> np.ndarray:
+    """Occlusion test on the left winners alone (the uniqueness reading of the
+    left-right check of Sec. 3.1).  Pixel x of a row matches right-image
+    column u(x) = x - d*(x).  A pixel x' > x whose match lies at or left of
+    u(x) hides x from the right camera, so with m(x) = min over x' > x of
+    u(x') the margin is v(x) = m(x) - u(x), clamped to [-16, 16]; v <= 0 means
+    occluded, v = 1 on a fronto-parallel surface, and the last pixel of a row
+    (no x' > x) gets 16.  Returns int [H][W]."""
+    ds = np.asarray(ds, dtype=np.int64)
+    H, W = ds.shape
+    v = np.full((H, W), 16, dtype=np.int64)
+    for y in range(H):
+        m = None                       # min of u(x') over the pixels right of x
+        for x in range(W - 1, -1, -1):
+            u = x - int(ds[y, x])
+            if m is not None:
+                v[y, x] = min(max(m - u, -16), 16)
+            m = u if m is None else min(m, u)
+    return v
 
 
 def _conv3x3(a: np.ndarray, w: np.ndarray) -> np.ndarray:

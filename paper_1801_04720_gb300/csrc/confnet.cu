@@ -4,14 +4,16 @@
 // which needs a second SGM pass with the right image as reference.  This
 // path predicts that check's outcome from the left pass alone:
 //
-//   1. features_kernel: eight channels per pixel of the left pass's
+//   1. features_kernel: seven channels per pixel of the left pass's
 //      aggregated cost curve S (best cost, margin to the best cost outside
 //      the winner's neighbourhood, curvature, disagreement of the three path
 //      groups, winner, distance to the left border, matching cost at the
-//      winner, smaller neighbour rise), each an integer over a power of two,
-//      stored as bfloat16 [H][W][8].  The winner and its parabolic subpixel
-//      value come out of the same pass, computed exactly like the plain
-//      select.
+//      winner), each an integer over a power of two, stored as bfloat16
+//      [H][W][8].  The winner and its parabolic subpixel value come out of
+//      the same pass, computed exactly like the plain select.  Then
+//      visibility_kernel fills channel 7 from the winners of each row: the
+//      occlusion test that the left-right check performs, read off the left
+//      disparities alone.
 //   2. infer_kernel: a 4-layer 3x3 network (8 -> 32 -> 32 -> 32 -> 1, ReLU,
 //      sigmoid), bfloat16 weights and activations, fp32 accumulation on the
 //      5th-generation tensor cores: tcgen05.mma with operands in shared
@@ -81,19 +83,14 @@ __device__ __forceinline__ void finish_pixel(const FeatureArgs& a, Curve& c, int
   if (lane != out_lane) return;
   const int cstar = a.cost[pix * a.Dp + ds];
   const uint32_t s2 = far == 0xffffffffu ? s0 : far;
-  int curv = 0, rise = 0;
+  int curv = 0;
   if (a.D > 1) {
-    if (ds == 0) {
+    if (ds == 0)
       curv = 2 * ((int)vp - (int)s0);
-      rise = (int)vp - (int)s0;
-    } else if (ds == a.D - 1) {
+    else if (ds == a.D - 1)
       curv = 2 * ((int)vm - (int)s0);
-      rise = (int)vm - (int)s0;
-    } else {
-      const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
-      curv = am + bp;
-      rise = min(am, bp);
-    }
+    else
+      curv = (int)vm + (int)vp - 2 * (int)s0;
   }
   const int gh_d = (int)(c.kh & 0xffu), gd_d = (int)(c.kd & 0xffu), gu_d = (int)(c.ku & 0xffu);
   const int dis = min(abs(gh_d - ds), 16) + min(abs(gd_d - ds), 16) + min(abs(gu_d - ds), 16);
@@ -102,7 +99,7 @@ __device__ __forceinline__ void finish_pixel(const FeatureArgs& a, Curve& c, int
   const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
                        (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
                        (float)ds * (1.0f / 128.0f),   (float)margin * (1.0f / 64.0f),
-                       (float)cstar * (1.0f / 64.0f), (float)rise * (1.0f / 256.0f)};
+                       (float)cstar * (1.0f / 64.0f), 0.0f};   // channel 7: visibility_kernel
   uint32_t packed[4];
 #pragma unroll
   for (int i = 0; i < 4; i++) {
@@ -205,19 +202,14 @@ __device__ __forceinline__ void vec_finish(const FeatureArgs& a, const uint32_t*
   if (lane != out_lane) return;
   const int cstar = a.cost[pix * a.Dp + ds];
   const uint32_t s2 = far == 0xffffffffu ? s0 : far;
-  int curv = 0, rise = 0;
+  int curv = 0;
   if (a.D > 1) {
-    if (ds == 0) {
+    if (ds == 0)
       curv = 2 * ((int)vp - (int)s0);
-      rise = (int)vp - (int)s0;
-    } else if (ds == a.D - 1) {
+    else if (ds == a.D - 1)
       curv = 2 * ((int)vm - (int)s0);
-      rise = (int)vm - (int)s0;
-    } else {
-      const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
-      curv = am + bp;
-      rise = min(am, bp);
-    }
+    else
+      curv = (int)vm + (int)vp - 2 * (int)s0;
   }
   const int dis = min(abs((int)(c.kh & 0xffu) - ds), 16) + min(abs((int)(c.kd & 0xffu) - ds), 16) +
                   min(abs((int)(c.ku & 0xffu) - ds), 16);
@@ -225,7 +217,7 @@ __device__ __forceinline__ void vec_finish(const FeatureArgs& a, const uint32_t*
   const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
                        (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
                        (float)ds * (1.0f / 128.0f),   (float)margin * (1.0f / 64.0f),
-                       (float)cstar * (1.0f / 64.0f), (float)rise * (1.0f / 256.0f)};
+                       (float)cstar * (1.0f / 64.0f), 0.0f};   // channel 7: visibility_kernel
   uint32_t packed[4];
 #pragma unroll
   for (int i = 0; i < 4; i++) {
@@ -888,11 +880,47 @@ __global__ void adam_kernel(float* th, float* m, float* v, const float* g, int n
 
 }  // namespace
 
+// Channel 7, the visibility margin: pixel x of a row matches right-image
+// column u(x) = x - d*(x); with m(x) the minimum of u over the pixels right of
+// x, v = clamp(m - u, -16, 16) (16 for the last pixel), stored as v / 16.
+// One block per row: each thread takes a contiguous segment, the minima of
+// the segments to its right come from a block-wide suffix scan, then the
+// thread walks its segment right to left.
+constexpr int kVisThreads = 256;
+
+__global__ void __launch_bounds__(kVisThreads)
+    visibility_kernel(const int16_t* __restrict__ dint, uint16_t* __restrict__ feat, int W) {
+  __shared__ int warp_suffix[kVisThreads / 32];
+  constexpr int kNone = 0x7fffffff;
+  const int y = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  const int seg = (W + kVisThreads - 1) / kVisThreads;
+  const int x0 = min(t * seg, W), x1 = min(x0 + seg, W);
+  const int16_t* row = dint + (size_t)y * W;
+  int tot = kNone;
+  for (int x = x0; x < x1; x++) tot = min(tot, x - (int)row[x]);
+  // inclusive suffix minimum over the lanes >= lane of this warp
+  int incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) incl = min(incl, __shfl_down_sync(kFullMask, incl, o));
+  if (lane == 0) warp_suffix[wp] = incl;
+  __syncthreads();
+  int m = __shfl_down_sync(kFullMask, incl, 1);
+  if (lane == 31) m = kNone;
+  for (int w = wp + 1; w < kVisThreads / 32; w++) m = min(m, warp_suffix[w]);
+  uint16_t* f = feat + (size_t)y * W * kF + 7;
+  for (int x = x1 - 1; x >= x0; x--) {
+    const int u = x - (int)row[x];
+    const int v = m == kNone ? 16 : max(min(m - u, 16), -16);
+    f[(size_t)x * kF] = __bfloat16_as_ushort(__float2bfloat16_rn((float)v * (1.0f / 16.0f)));
+    m = min(m, u);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_features(const FeatureArgs& a, cudaStream_t s) {
-  count_launches(1);
+  count_launches(2);
   if (a.D % 4 == 0) {
     const size_t threads = (size_t)a.J * 16 * a.H * 32;
     if (a.D <= 128)
@@ -903,6 +931,7 @@ cudaError_t launch_features(const FeatureArgs& a, cudaStream_t s) {
     const size_t threads = (size_t)a.J * 16 * a.H * 32;
     features_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
   }
+  visibility_kernel<<<(unsigned)a.H, kVisThreads, 0, s>>>(a.dint, a.feat, a.W);
   return cudaGetLastError();
 }
 

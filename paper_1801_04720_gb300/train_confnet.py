@@ -155,6 +155,20 @@ def rates(dec, threshold):
             "accepted": acc / max(tot, 1), "plain_kept": pos / max(tot, 1)}
 
 
+def accuracy(disps, gts, tau=3.0):
+    """Density (fraction of pixels with a disparity, i.e. not NaN) and the
+    fraction of those more than `tau` px from the ground truth, over pairs of
+    (disparity map, ground-truth disparity) device tensors."""
+    import torch
+    kept = bad = tot = 0
+    for disp, gt in zip(disps, gts):
+        m = ~torch.isnan(disp)
+        kept += int(m.sum())
+        bad += int(((disp - gt).abs() > tau)[m].sum())
+        tot += disp.numel()
+    return {"density": kept / max(tot, 1), f"bad_{tau:g}px": bad / max(kept, 1)}
+
+
 def calibrate(dec, target=0.01):
     """Smallest threshold on a grid whose false-accept rate is <= target."""
     for t in np.linspace(0.05, 0.995, 190):

@@ -10,6 +10,7 @@ import pytest
 from oracle import confnet_oracle as co
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "confnet_features.txt")
+VISIBILITY = os.path.join(os.path.dirname(__file__), "golden", "visibility_margin.txt")
 
 
 def test_bf16_matches_library_conversion():
@@ -66,8 +67,59 @@ def test_features_hand_cases(case):
     cost[0, x, d_star] = c
     feat, ds = co.features(S, vols, cost)
     assert int(ds[0, x]) == d_star
-    scales = [1024, 256, 256, 16, 128, 64, 64, 256]
+    scales = [1024, 256, 256, 16, 128, 64, 64, 16]
     assert list(feat[0, x]) == [float(co.bf16(e / s)) for e, s in zip(exp, scales)]
+
+
+def _visibility_cases():
+    cases = []
+    for line in open(VISIBILITY):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, row, exp = (p.strip() for p in line.split("|"))
+        cases.append((name, [int(v) for v in row.split()], [int(v) for v in exp.split()]))
+    return cases
+
+
+@pytest.mark.parametrize("case", _visibility_cases(), ids=lambda c: c[0])
+def test_visibility_margin_hand_rows(case):
+    _, row, exp = case
+    assert len(row) == len(exp)
+    assert list(co.visibility_margin(np.array([row]))[0]) == exp
+
+
+@pytest.mark.parametrize("case", _visibility_cases(), ids=lambda c: c[0])
+def test_visibility_margin_through_features(case):
+    """Channel 7 of the features on cost curves whose single minimum sits at
+    the row's winners (in L0 only), and rows stacked: each row on its own."""
+    _, row, exp = case
+    W, D = len(row), max(row) + 2
+    vols = [np.zeros((2, W, D), dtype=np.int64) for _ in range(8)]
+    for y, shift in ((0, 0), (1, 1)):
+        for x, d in enumerate(row):
+            dd = min(d + shift, D - 1) if y == 1 else d
+            vols[0][y, x] = 50 + 3 * np.abs(np.arange(D) - dd)
+    feat, ds = co.features(sum(vols), vols, np.zeros((2, W, D), dtype=np.uint8))
+    assert list(ds[0]) == row
+    assert list(feat[0, :, 7]) == [float(co.bf16(e / 16)) for e in exp]
+    assert np.array_equal(feat[1, :, 7], co.bf16(co.visibility_margin(ds[1:2])[0] / 16))
+
+
+def test_visibility_margin_step_closed_form():
+    """A foreground step of height J at column x0 hides the J background
+    pixels left of it: v(x) = (x0 - d_f) - (x - d_b) there, 1 elsewhere."""
+    for d_b, d_f, x0, W in ((3, 7, 20, 40), (0, 12, 30, 50), (5, 6, 10, 16)):
+        row = np.array([[d_b] * x0 + [d_f] * (W - x0)])
+        v = co.visibility_margin(row)[0]
+        J = d_f - d_b
+        for x in range(W):
+            if x == W - 1:
+                want = 16
+            elif x0 - J <= x < x0:
+                want = max((x0 - d_f) - (x - d_b), -16)
+            else:
+                want = 1
+            assert v[x] == want, (d_b, d_f, x0, x)
 
 
 def test_single_tap_network_routes_one_value():
