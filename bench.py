@@ -284,17 +284,45 @@ def run_ours(args, world, rank, local):
                  "valid": torch.empty((H, W), dtype=torch.uint8).pin_memory()}
         for _ in range(3):
             _lib.sf_scene_flow_host(h_imgs, h_flow, p, cam, ws_h, h_out, stream=stream)
-        e_ms = []
+        # latency of one synchronous call (L2 flushed before each)
+        lat = []
         for k in range(args.steps):
             flush.fill_(k & 0xFF)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             _lib.sf_scene_flow_host(h_imgs, h_flow, p, cam, ws_h, h_out, stream=stream)
-            e_ms.append((time.perf_counter() - t0) * 1e3)
-        e_mean = max_over_ranks(statistics.mean(e_ms), world, dev)
+            lat.append((time.perf_counter() - t0) * 1e3)
+        del ws_h
+        # throughput through the frame pipeline: every step copies its inputs
+        # in from pinned host memory and its outputs back, overlapped with the
+        # neighbouring frames' computation; the host waits for a frame's
+        # outputs before it hands their buffers to a later frame
+        depth = 2
+        h_outs = [h_out] + [{k: torch.empty_like(v).pin_memory() for k, v in h_out.items()}
+                            for _ in range(depth - 1)]
+        with _lib.Pipeline(W, H, p, cam, depth=depth) as pl:
+            for k in range(2 * depth):
+                if k >= depth:
+                    pl.wait(k - depth)
+                pl.submit(h_imgs, h_flow, h_outs[k % depth])
+            pl.wait(2 * depth - 1)
+            if world > 1:
+                torch.distributed.barrier()
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                if k >= depth:
+                    pl.wait(k - depth + 2 * depth)
+                pl.submit(h_imgs, h_flow, h_outs[k % depth])
+            pl.wait(2 * depth + args.steps - 1)
+            e_total = (time.perf_counter() - t0) * 1e3
+        e_mean = max_over_ranks(e_total / args.steps, world, dev)
         e2e = {"value": round(replica_rate(e_mean, world), 2), "unit": "frames/s",
                "h2d_bytes_per_step": 4 * N + 8 * N, "d2h_bytes_per_step": 16 * N + 12 * N + 12 * N + N,
-               "ms_per_step": round(e_mean, 4)}
+               "ms_per_step": round(e_mean, 4),
+               "api": f"sf_pipeline_submit / sf_pipeline_wait, {depth} slots, pinned host buffers",
+               "l2": "not flushed in the pipelined run: each step's inputs arrive by copy from host "
+                     "memory and a frame's 0.9 GB working set exceeds the L2",
+               "latency_ms_sf_scene_flow_host": round(max_over_ranks(statistics.mean(lat), world, dev), 4)}
 
     result = {
         "metric": METRIC, "value": round(replica_rate(ms, world), 2), "unit": "frames/s",

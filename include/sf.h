@@ -241,6 +241,44 @@ sf_status sf_scene_flow_host(const uint8_t* left_t, const uint8_t* right_t,
                              uint8_t* valid_out, void* dev_workspace, size_t ws_bytes,
                              void* stream);
 
+/* ---- frame pipeline: host buffers, copies overlapped with compute -------- */
+
+/* A pipeline of scene-flow frames of one size W x H, for a stream of
+ * quadruples that live in host memory.  It holds `depth` (2..8) staging slots
+ * in device memory for a frame's inputs and outputs, the sf_scene_flow
+ * workspace, and three streams (copies in, compute, copies out) ordered by
+ * events, so that while frame k computes, frame k+1's inputs are copied in
+ * and frame k-1's outputs copied out.  The computation is sf_scene_flow's,
+ * one frame at a time.  Unlike the other calls, the pipeline owns device
+ * memory: allocated here (on the current device), freed by
+ * sf_pipeline_destroy.  Returns SF_ERR_INVALID_ARG for a bad size, params,
+ * camera or depth, SF_ERR_CUDA if an allocation fails. */
+typedef struct sf_pipeline sf_pipeline;
+sf_status sf_pipeline_create(int32_t W, int32_t H, const sf_sgm_params* p, const sf_camera* cam,
+                             int32_t depth, sf_pipeline** out);
+
+/* Queues one frame and returns without waiting for it.  HOST pointers: the
+ * four images (uint8 [H][W], dense), flow (float [H][W][2]) and the outputs
+ * s4_out (float [H][W][4]), motion_out / point_out (float [H][W][3] or NULL)
+ * and valid_out (uint8 [H][W]).  Pinned host memory gives asynchronous
+ * copies; with pageable memory each copy blocks the host.  The inputs must
+ * stay unchanged, and the outputs unread, until sf_pipeline_wait for this
+ * frame returns.  *ticket (ticket may be NULL) numbers the frame: 0, 1, ...
+ * Thread-safe with respect to other calls on the same pipeline. */
+sf_status sf_pipeline_submit(sf_pipeline* pl, const uint8_t* left_t, const uint8_t* right_t,
+                             const uint8_t* left_t1, const uint8_t* right_t1, const float* flow,
+                             float* s4_out, float* motion_out, float* point_out, uint8_t* valid_out,
+                             int64_t* ticket);
+
+/* Blocks until the outputs of frame `ticket` (and of every frame submitted
+ * before it) are in host memory.  An error raised by that work returns
+ * SF_ERR_CUDA; an unknown ticket SF_ERR_INVALID_ARG. */
+sf_status sf_pipeline_wait(sf_pipeline* pl, int64_t ticket);
+
+/* Waits for every queued frame, then frees the pipeline's streams, events and
+ * device memory. */
+sf_status sf_pipeline_destroy(sf_pipeline* pl);
+
 /* ---- batches of quadruples with uneven sizes ------------------------------ */
 
 /* One quadruple of a batch: device pointers as in sf_scene_flow, its own size

@@ -33,6 +33,7 @@ EXPORTED = [
     "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
     "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
     "sf_scene_flow_learned", "sf_scene_flow_learned_frames", "sf_debug_set",
+    "sf_pipeline_create", "sf_pipeline_submit", "sf_pipeline_wait", "sf_pipeline_destroy",
 ]
 
 SF_DEBUG_SPIN_LIMIT = 1
@@ -126,6 +127,10 @@ def load(path: str = LIB_PATH):
             "sf_scene_flow": (i32, [P, P, P, P, i32, P, i32, i32, PP, PC, P, P, P, P, P, P, P, sz, P]),
             "sf_scene_flow_host_workspace_size": (sz, [i32, i32, PP]),
             "sf_scene_flow_host": (i32, [P, P, P, P, P, i32, i32, PP, PC, P, P, P, P, P, sz, P]),
+            "sf_pipeline_create": (i32, [i32, i32, PP, PC, i32, ctypes.POINTER(P)]),
+            "sf_pipeline_submit": (i32, [P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_int64)]),
+            "sf_pipeline_wait": (i32, [P, ctypes.c_int64]),
+            "sf_pipeline_destroy": (i32, [P]),
             "sf_trace_arm": (i32, [P, i32, P]),
             "sf_trace_disarm": (i32, []),
             "sf_kernel_launches": (ctypes.c_uint64, []),
@@ -376,6 +381,64 @@ def sf_scene_flow_host(imgs, flow, p: SgmParams, cam: Camera, dev_ws, out, strea
                                      _ptr(out.get("point")), _ptr(out["valid"]), _ptr(dev_ws),
                                      dev_ws.numel(), _stream(stream)))
     return out
+
+
+class Pipeline:
+    """sf_pipeline_*: scene flow of host-memory quadruples of one size, the
+    copies of neighbouring frames overlapped with the computation.
+    ``submit`` takes CPU tensors (pinned for asynchronous copies) and returns
+    a ticket; the frame's outputs are in its ``out`` tensors once ``wait``
+    returns for that ticket.  The tensors must stay alive until then."""
+
+    def __init__(self, W, H, p: SgmParams, cam: Camera, depth=2):
+        self._h = ctypes.c_void_p()
+        _check("sf_pipeline_create", load().sf_pipeline_create(W, H, ctypes.byref(p), ctypes.byref(cam),
+                                                               depth, ctypes.byref(self._h)))
+        self.W, self.H, self.depth = W, H, depth
+        self._held = {}
+
+    def submit(self, imgs, flow, out):
+        shapes = [(im, torch.uint8, (self.H, self.W), f"imgs[{k}]") for k, im in enumerate(imgs)]
+        shapes += [(flow, torch.float32, (self.H, self.W, 2), "flow"),
+                   (out["s4"], torch.float32, (self.H, self.W, 4), "s4"),
+                   (out["valid"], torch.uint8, (self.H, self.W), "valid")]
+        shapes += [(out[k], torch.float32, (self.H, self.W, 3), k) for k in ("motion", "point")
+                   if out.get(k) is not None]
+        for t, dt, shape, name in shapes:
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dt or tuple(t.shape) != shape:
+                raise ValueError(f"{name}: expected a host {dt} tensor of shape {shape}")
+        t = ctypes.c_int64()
+        _check("sf_pipeline_submit",
+               load().sf_pipeline_submit(self._h, _ptr(imgs[0]), _ptr(imgs[1]), _ptr(imgs[2]), _ptr(imgs[3]),
+                                         _ptr(flow), _ptr(out["s4"]), _ptr(out.get("motion")),
+                                         _ptr(out.get("point")), _ptr(out["valid"]), ctypes.byref(t)))
+        self._held[t.value] = (imgs, flow, out)
+        return t.value
+
+    def wait(self, ticket):
+        _check("sf_pipeline_wait", load().sf_pipeline_wait(self._h, ticket))
+        for k in [k for k in self._held if k <= ticket]:
+            del self._held[k]
+
+    def close(self):
+        if self._h:
+            st = load().sf_pipeline_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._held.clear()
+            _check("sf_pipeline_destroy", st)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().sf_pipeline_destroy(self._h)
+        except Exception:
+            pass
 
 
 class StageTracer:
