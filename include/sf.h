@@ -439,7 +439,10 @@ sf_status sf_confnet_pack(const float* params, void* packed, void* stream);
  * dint, dsub: the left pass's winners (needed for valid_out / disp_out);
  * prob_out: float [H][W] or NULL; valid_out: uint8 [H][W] or NULL
  * (1 = accepted); disp_out: float [H][W] or NULL (dsub where accepted, NaN
- * elsewhere).  All device pointers. */
+ * elsewhere).  All device pointers.  The kernel's waits for its own
+ * tensor-core work are bounded; should one give up, the outputs of the tiles
+ * not yet done stay unwritten (the learned-path calls report that case as
+ * SF_ERR_TIMEOUT through their workspace error word; this call has none). */
 sf_status sf_confnet_infer(const void* packed, const uint16_t* features, const int16_t* dint,
                            const float* dsub, int32_t W, int32_t H, float threshold, float* prob_out,
                            uint8_t* valid_out, float* disp_out, void* stream);

@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
       // layer 1 has read the features: the next tile's may come in
       if (layer == 0 && !failed && tile + (int)gridDim.x < ntiles) fetch_features(tile + gridDim.x);
       if (failed) {
-        if (tid == 0) atomicExch(a.err, 1);
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
         break;
       }
       fence_after();
@@ -880,6 +880,228 @@ __global__ void adam_kernel(float* th, float* m, float* v, const float* g, int n
 
 }  // namespace
 
+// Per-pixel form (D % 8 == 0): one thread per pixel walks its curves in
+// chunks of 32 disparities (whole 32-byte sectors of S, of the horizontal
+// paths and of the partial-sum words, all loads issued before the
+// arithmetic), then 8 at a time for a tail, and keeps every statistic
+// online, so no warp reduction is needed:
+//   - S0, d*: first strict minimum;
+//   - S2 (min over |d - d*| >= 2): when a new minimum appears at d, the
+//     candidates so far are those at d' <= d - 2, whose minimum is the prefix
+//     minimum lagged by two; afterwards every d >= d* + 2 joins;
+//   - S(d* - 1) is the value preceding the new minimum, S(d* + 1) is taken
+//     when d = d* + 1 (0 where out of range, as in the other forms);
+//   - the three group winners as (value << 8 | d) minima.
+constexpr uint32_t kBig = 0xffffffffu;   // "no value yet" in the online minima
+
+struct PxState {
+  uint32_t kh, kd, ku, s0, m2, lag, prev, vm, vp;
+  int ds;
+};
+
+// Eight disparities d0 .. d0+7: S words (two u16 each), horizontal bytes
+// (forward and backward, four per word), partial-sum words (the pixel's half).
+__device__ __forceinline__ void px_step8(PxState& st, int d0, const uint32_t* sw, uint32_t f0, uint32_t f1,
+                                         uint32_t b0, uint32_t b1, const uint32_t* ww, int hi) {
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    const uint32_t d = (uint32_t)(d0 + e);
+    const uint32_t sv = (e & 1) ? sw[e >> 1] >> 16 : sw[e >> 1] & 0xffffu;
+    const uint32_t fb = e < 4 ? f0 : f1, bb = e < 4 ? b0 : b1;
+    const uint32_t gh = ((fb >> (8 * (e & 3))) & 0xffu) + ((bb >> (8 * (e & 3))) & 0xffu);
+    const uint32_t gd = hi ? ww[e] >> 16 : ww[e] & 0xffffu;
+    st.kh = min(st.kh, (gh << 8) | d);
+    st.kd = min(st.kd, (gd << 8) | d);
+    st.ku = min(st.ku, ((sv - gh - gd) << 8) | d);
+    if (sv < st.s0) {
+      st.s0 = sv;
+      st.ds = (int)d;
+      st.m2 = st.lag;
+      st.vm = d > 0 ? st.prev : 0u;
+      st.vp = 0u;
+    } else {
+      if ((int)d >= st.ds + 2) st.m2 = min(st.m2, sv);
+      if ((int)d == st.ds + 1) st.vp = sv;
+    }
+    st.lag = min(st.lag, st.prev);
+    st.prev = sv;
+  }
+}
+
+// Features, winner and subpixel winner of pixel `pix` (column x) from its
+// online statistics.
+__device__ __forceinline__ void px_finish(const FeatureArgs& a, const PxState& st, size_t pix, int x) {
+  const uint32_t kh = st.kh, kd = st.kd, ku = st.ku, s0 = st.s0, m2 = st.m2, vm = st.vm, vp = st.vp;
+  const int ds = st.ds;
+  const int cstar = a.cost[pix * a.Dp + ds];
+  const uint32_t s2 = m2 == kBig ? s0 : m2;
+  int curv = 0;
+  if (a.D > 1) {
+    if (ds == 0)
+      curv = 2 * ((int)vp - (int)s0);
+    else if (ds == a.D - 1)
+      curv = 2 * ((int)vm - (int)s0);
+    else
+      curv = (int)vm + (int)vp - 2 * (int)s0;
+  }
+  const int dis = min(abs((int)(kh & 0xffu) - ds), 16) + min(abs((int)(kd & 0xffu) - ds), 16) +
+                  min(abs((int)(ku & 0xffu) - ds), 16);
+  const int margin = min(max(x - ds, 0), 64);
+  const float f[kF] = {(float)s0 * (1.0f / 1024.0f), (float)(s2 - s0) * (1.0f / 256.0f),
+                       (float)curv * (1.0f / 256.0f), (float)dis * (1.0f / 16.0f),
+                       (float)ds * (1.0f / 128.0f),   (float)margin * (1.0f / 64.0f),
+                       (float)cstar * (1.0f / 64.0f), 0.0f};   // channel 7: visibility_kernel
+  uint32_t packed[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+    packed[i] = *reinterpret_cast<const uint32_t*>(&h2);
+  }
+  reinterpret_cast<uint4*>(a.feat)[pix] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+  a.dint[pix] = (int16_t)ds;
+  float v = (float)ds;
+  if (a.subpixel && ds > 0 && ds < a.D - 1) {
+    const int am = (int)vm - (int)s0, bp = (int)vp - (int)s0;
+    v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
+  }
+  a.dsub[pix] = v;
+}
+
+
+__global__ void __launch_bounds__(256, 2)
+    features_px_kernel(FeatureArgs a) {
+  const size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= (size_t)a.W * a.H) return;
+  const int y = (int)(pix / a.W), x = (int)(pix - (size_t)y * a.W);
+  const int j = x >> 5, pr = x & 15, hi = (x >> 4) & 1;
+  const uint4* srow = reinterpret_cast<const uint4*>(a.S + pix * a.D);       // 8 disparities each
+  const uint4* hfr = reinterpret_cast<const uint4*>(a.hfwd + pix * a.Dp);    // 16 disparities each
+  const uint4* hbr = reinterpret_cast<const uint4*>(a.hbwd + pix * a.Dp);
+  const uint4* sdr =
+      reinterpret_cast<const uint4*>(a.sdown + (((size_t)y * a.J + j) * 16 + pr) * (size_t)a.dpad_shape);
+  PxState st{kBig, kBig, kBig, kBig, kBig, kBig, kBig, 0u, 0u, 0};
+  int d0 = 0;
+  for (; d0 + 32 <= a.D; d0 += 32) {
+    uint4 sv[4], fv[2], bv[2], wv[8];
+#pragma unroll
+    for (int i = 0; i < 4; i++) sv[i] = __ldg(srow + (d0 >> 3) + i);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      fv[i] = __ldg(hfr + (d0 >> 4) + i);
+      bv[i] = __ldg(hbr + (d0 >> 4) + i);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) wv[i] = __ldg(sdr + (d0 >> 2) + i);
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+      const uint32_t sw[4] = {sv[g].x, sv[g].y, sv[g].z, sv[g].w};
+      const uint4 f = fv[g >> 1], b = bv[g >> 1];
+      const uint32_t f0 = (g & 1) ? f.z : f.x, f1 = (g & 1) ? f.w : f.y;
+      const uint32_t b0 = (g & 1) ? b.z : b.x, b1 = (g & 1) ? b.w : b.y;
+      const uint32_t ww[8] = {wv[2 * g].x,     wv[2 * g].y,     wv[2 * g].z,     wv[2 * g].w,
+                              wv[2 * g + 1].x, wv[2 * g + 1].y, wv[2 * g + 1].z, wv[2 * g + 1].w};
+      px_step8(st, d0 + 8 * g, sw, f0, f1, b0, b1, ww, hi);
+    }
+  }
+  for (; d0 < a.D; d0 += 8) {
+    const uint4 s8 = __ldg(srow + (d0 >> 3));
+    const uint2 f8 = __ldg(reinterpret_cast<const uint2*>(a.hfwd + pix * a.Dp) + (d0 >> 3));
+    const uint2 b8 = __ldg(reinterpret_cast<const uint2*>(a.hbwd + pix * a.Dp) + (d0 >> 3));
+    const uint4 wa = __ldg(sdr + (d0 >> 2)), wb = __ldg(sdr + (d0 >> 2) + 1);
+    const uint32_t sw[4] = {s8.x, s8.y, s8.z, s8.w};
+    const uint32_t ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+    px_step8(st, d0, sw, f8.x, f8.y, b8.x, b8.y, ww, hi);
+  }
+  px_finish(a, st, pix, x);
+}
+
+// Staged form (D % 32 == 0): a block of 128 threads takes 128 columns of
+// one row.  Each chunk of 32 disparities of S, of the two horizontal paths
+// and of the partial-sum words comes into shared memory by coalesced 16-byte
+// asynchronous copies (double-buffered: the next chunk's copies run while
+// this one is consumed); each thread then reads its own pixel's rows, padded
+// by 16 bytes so that a warp's 16-byte reads spread over all banks, and
+// updates the same online statistics as the per-pixel form.
+constexpr int kStThreads = 128;
+constexpr int kStS = 80, kStH = 48, kStW = 144;              // padded row bytes
+constexpr int kStStage = kStThreads * (kStS + 2 * kStH) + 4 * 16 * kStW;
+constexpr int kStSmem = 2 * kStStage;
+
+__device__ __forceinline__ void cp16(uint8_t* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kStThreads)
+    features_staged_kernel(FeatureArgs a) {
+  extern __shared__ __align__(16) uint8_t fsm[];
+  const int segs = (a.W + kStThreads - 1) / kStThreads;
+  const int y = blockIdx.x / segs, x0 = (blockIdx.x - y * segs) * kStThreads;
+  const int tid = threadIdx.x, x = x0 + tid;
+  const int ncols = min(kStThreads, a.W - x0);
+  const int strips = (ncols + 31) / 32, j0 = x0 / 32;
+  const size_t row0 = (size_t)y * a.W + x0;
+  auto load_chunk = [&](int d0, int stage) {
+    uint8_t* sS = fsm + stage * kStStage;
+    uint8_t* sF = sS + kStThreads * kStS;
+    uint8_t* sB = sF + kStThreads * kStH;
+    uint8_t* sW = sB + kStThreads * kStH;
+    for (int c = tid; c < kStThreads * 4; c += kStThreads) {
+      const int px = c >> 2, part = c & 3;
+      if (px < ncols) cp16(sS + px * kStS + part * 16, a.S + (row0 + px) * a.D + d0 + part * 8);
+    }
+    for (int c = tid; c < kStThreads * 2; c += kStThreads) {
+      const int px = c >> 1, part = c & 1;
+      if (px < ncols) {
+        cp16(sF + px * kStH + part * 16, a.hfwd + (row0 + px) * a.Dp + d0 + part * 16);
+        cp16(sB + px * kStH + part * 16, a.hbwd + (row0 + px) * a.Dp + d0 + part * 16);
+      }
+    }
+    for (int c = tid; c < 4 * 16 * 8; c += kStThreads) {
+      const int r = c >> 3, part = c & 7, sl = r >> 4, pr = r & 15;
+      if (sl < strips)
+        cp16(sW + r * kStW + part * 16,
+             a.sdown + (((size_t)y * a.J + j0 + sl) * 16 + pr) * (size_t)a.dpad_shape + d0 + part * 4);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  PxState st{kBig, kBig, kBig, kBig, kBig, kBig, kBig, 0u, 0u, 0};
+  const int hi = (x >> 4) & 1, wrow = ((tid >> 5) << 4) + (x & 15);
+  const int nchunks = a.D / 32;
+  load_chunk(0, 0);
+  for (int k = 0; k < nchunks; k++) {
+    if (k + 1 < nchunks) {
+      load_chunk(32 * (k + 1), (k + 1) & 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid < ncols) {
+      const uint8_t* sS = fsm + (k & 1) * kStStage;
+      const uint8_t* sF = sS + kStThreads * kStS;
+      const uint8_t* sB = sF + kStThreads * kStH;
+      const uint8_t* sW = sB + kStThreads * kStH;
+      const uint4* ps = reinterpret_cast<const uint4*>(sS + tid * kStS);
+      const uint4* pf = reinterpret_cast<const uint4*>(sF + tid * kStH);
+      const uint4* pb = reinterpret_cast<const uint4*>(sB + tid * kStH);
+      const uint4* pw = reinterpret_cast<const uint4*>(sW + wrow * kStW);
+#pragma unroll
+      for (int g = 0; g < 4; g++) {
+        const uint4 sv = ps[g], wa = pw[2 * g], wb = pw[2 * g + 1];
+        const uint4 f = pf[g >> 1], b = pb[g >> 1];
+        const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w};
+        const uint32_t ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        px_step8(st, 32 * k + 8 * g, sw, (g & 1) ? f.z : f.x, (g & 1) ? f.w : f.y, (g & 1) ? b.z : b.x,
+                 (g & 1) ? b.w : b.y, ww, hi);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < ncols) px_finish(a, st, row0 + tid, x);
+}
+
 // Channel 7, the visibility margin: pixel x of a row matches right-image
 // column u(x) = x - d*(x); with m(x) the minimum of u over the pixels right of
 // x, v = clamp(m - u, -16, 16) (16 for the last pixel), stored as v / 16.
@@ -921,7 +1143,20 @@ __global__ void __launch_bounds__(kVisThreads)
 // ---------------------------------------------------------------------------
 cudaError_t launch_features(const FeatureArgs& a, cudaStream_t s) {
   count_launches(2);
-  if (a.D % 4 == 0) {
+  if (a.D % 32 == 0) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(features_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    const size_t blocks = (size_t)a.H * ((a.W + kStThreads - 1) / kStThreads);
+    features_staged_kernel<<<(unsigned)blocks, kStThreads, kStSmem, s>>>(a);
+  } else if (a.D % 8 == 0) {
+    const size_t threads = (size_t)a.W * a.H;
+    features_px_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+  } else if (a.D % 4 == 0) {
     const size_t threads = (size_t)a.J * 16 * a.H * 32;
     if (a.D <= 128)
       features_vec_kernel<1><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
