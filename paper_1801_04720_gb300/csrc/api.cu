@@ -1187,6 +1187,8 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
                             false);
   if (st != SF_OK) return st;
   const fused::Shape shape = fused::shape_for(D, false);
+  static_assert(confnet::kMaxInferPass >= fused::kMaxPass, "one network launch per learned call");
+  confnet::InferArgs ia{};
   for (int k = 0; k < npairs; k++) {
     const LearnedPair& b = plan.pr[k];
     confnet::FeatureArgs fa{};
@@ -1205,21 +1207,22 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
       StageTrace trace(SF_STAGE_FEATURES, s);
       SF_TRY_CUDA(confnet::launch_features(fa, s));
     }
-    if (packed) {
-      confnet::InferArgs ia{};
-      ia.W = W; ia.H = H;
-      ia.packed = packed;
-      ia.feat = fa.feat;
-      ia.dint = fa.dint;
-      ia.dsub = fa.dsub;
-      ia.threshold = threshold;
-      ia.prob = prob_out ? prob_out[k] : nullptr;
-      ia.valid = valid_out ? valid_out[k] : nullptr;
-      ia.disp = disp_out ? disp_out[k] : nullptr;
-      ia.err = reinterpret_cast<int*>(ws + plan.err);
-      StageTrace trace(SF_STAGE_CONFNET, s);
-      SF_TRY_CUDA(confnet::launch_infer(ia, s));
-    }
+    confnet::InferPass& ip = ia.pass[k];
+    ip.feat = fa.feat;
+    ip.dint = fa.dint;
+    ip.dsub = fa.dsub;
+    ip.prob = prob_out ? prob_out[k] : nullptr;
+    ip.valid = valid_out ? valid_out[k] : nullptr;
+    ip.disp = disp_out ? disp_out[k] : nullptr;
+  }
+  if (packed) {
+    // one network launch over the tiles of every pair
+    ia.W = W; ia.H = H; ia.npass = npairs;
+    ia.packed = packed;
+    ia.threshold = threshold;
+    ia.err = reinterpret_cast<int*>(ws + plan.err);
+    StageTrace trace(SF_STAGE_CONFNET, s);
+    SF_TRY_CUDA(confnet::launch_infer(ia, s));
   }
   return SF_OK;
 }
@@ -1253,15 +1256,15 @@ sf_status sf_confnet_infer(const void* packed, const uint16_t* features, const i
   if (!aligned(dint, 2) || !aligned(dsub, 4) || !aligned(prob_out, 4) || !aligned(disp_out, 4))
     return SF_ERR_INVALID_ARG;
   confnet::InferArgs ia{};
-  ia.W = W; ia.H = H;
+  ia.W = W; ia.H = H; ia.npass = 1;
   ia.packed = packed;
-  ia.feat = features;
-  ia.dint = dint;
-  ia.dsub = dsub;
+  ia.pass[0].feat = features;
+  ia.pass[0].dint = dint;
+  ia.pass[0].dsub = dsub;
+  ia.pass[0].prob = prob_out;
+  ia.pass[0].valid = valid_out;
+  ia.pass[0].disp = disp_out;
   ia.threshold = threshold;
-  ia.prob = prob_out;
-  ia.valid = valid_out;
-  ia.disp = disp_out;
   ia.err = nullptr;
   SF_TRY_CUDA(confnet::launch_infer(ia, (cudaStream_t)stream));
   return SF_OK;

@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   bool failed = false;
 
   const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
-  const int ntiles = tiles_x * tiles_y;
+  const int per_pass = tiles_x * tiles_y, ntiles = per_pass * a.npass;
   const uint32_t w_base = smem_u32(sm + kSmW);
   const uint32_t w2_base = w_base + kW1Elems * 2, w3_base = w2_base + kW2Elems * 2;
   const uint32_t w4_base = w3_base + kW2Elems * 2;
@@ -521,13 +521,15 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   // features of a tile's region 0 (origin X0-4, Y0-4; zeros outside the
   // image) by asynchronous copies, so that the next tile's arrive while this
   // tile's layers 2-4 run
-  auto fetch_features = [&](int tl) {
+  auto fetch_features = [&](int t) {
+    const int ps = t / per_pass, tl = t - ps * per_pass;
+    const uint16_t* feat = a.pass[ps].feat;
     const int X0 = (tl % tiles_x) * kTX, Y0 = (tl / tiles_x) * kTY;
     for (int i = tid; i < region_rows(0) * kP; i += kThreads) {
       const int gy = Y0 - 4 + i / kP, gx = X0 - 4 + i % kP;
       const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-      const void* src = in ? static_cast<const void*>(reinterpret_cast<const uint4*>(a.feat) + (size_t)gy * a.W + gx)
-                           : a.feat;
+      const void* src = in ? static_cast<const void*>(reinterpret_cast<const uint4*>(feat) + (size_t)gy * a.W + gx)
+                           : feat;
       const unsigned d = smem_u32(feat_s + 16 * i);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(in ? 16 : 0)
                    : "memory");
@@ -549,7 +551,9 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
 
   if (blockIdx.x < ntiles) fetch_features(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int X0 = (tile % tiles_x) * kTX, Y0 = (tile / tiles_x) * kTY;
+    const int ps = tile / per_pass, tl = tile - ps * per_pass;
+    const InferPass& out = a.pass[ps];
+    const int X0 = (tl % tiles_x) * kTX, Y0 = (tl / tiles_x) * kTY;
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     fence_async_smem();
     fence_before();
@@ -644,11 +648,11 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
           if (jj < kTX && gy < a.H && gx < a.W) {
             const float prob = 1.0f / (1.0f + expf(-z));
             const size_t pix = (size_t)gy * a.W + gx;
-            if (a.prob) a.prob[pix] = prob;
-            if (a.valid || a.disp) {
-              const bool ok = gx - (int)a.dint[pix] >= 0 && prob >= a.threshold;
-              if (a.valid) a.valid[pix] = ok ? 1 : 0;
-              if (a.disp) a.disp[pix] = ok ? a.dsub[pix] : __int_as_float(0x7fc00000);
+            if (out.prob) out.prob[pix] = prob;
+            if (out.valid || out.disp) {
+              const bool ok = gx - (int)out.dint[pix] >= 0 && prob >= a.threshold;
+              if (out.valid) out.valid[pix] = ok ? 1 : 0;
+              if (out.disp) out.disp[pix] = ok ? out.dsub[pix] : __int_as_float(0x7fc00000);
             }
           }
         }
@@ -1187,7 +1191,8 @@ cudaError_t launch_infer(const InferArgs& a, cudaStream_t s) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const int ntiles = ((a.W + kTX - 1) / kTX) * ((a.H + kTY - 1) / kTY);
+  if (a.npass < 1 || a.npass > kMaxInferPass) return cudaErrorInvalidValue;
+  const int ntiles = ((a.W + kTX - 1) / kTX) * ((a.H + kTY - 1) / kTY) * a.npass;
   count_launches(1);
   infer_kernel<<<(unsigned)std::min(ntiles, sms), kThreads, kSmTotal, s>>>(a);
   return cudaGetLastError();

@@ -34,17 +34,25 @@ struct FeatureArgs {
   float* dsub;             // subpixel winner
 };
 
-struct InferArgs {
-  int W, H;
-  const void* packed;      // kPackedBytes, 16-byte aligned
+// One pass (stereo pair) of a network launch.
+struct InferPass {
   const uint16_t* feat;    // bf16 [H][W][8]
   const int16_t* dint;     // winners (valid / disp outputs)
   const float* dsub;
-  float threshold;
   float* prob;             // [H][W] or nullptr
   uint8_t* valid;          // [H][W] or nullptr
   float* disp;             // [H][W] or nullptr (dsub where accepted, NaN elsewhere)
-  int* err;                // set to 1 if a bounded wait gave up
+};
+constexpr int kMaxInferPass = 4;
+
+// One launch covers the tiles of every pass (all of one size), so the
+// persistent blocks share the whole set of tiles.
+struct InferArgs {
+  int W, H, npass;
+  const void* packed;      // kPackedBytes, 16-byte aligned
+  InferPass pass[kMaxInferPass];
+  float threshold;
+  int* err;                // set to 1 if a bounded wait gave up (may be nullptr)
 };
 
 struct TrainArgs {
