@@ -428,6 +428,25 @@ sf_status sf_check_workspace(const void* workspace, int32_t W, int32_t H, const 
 /* Number of network parameters (21121). */
 int32_t sf_confnet_param_count(void);
 
+/* Seeded initial parameters, written to the device buffer `params` (fp32,
+ * sf_confnet_param_count() values, 4-byte aligned): each weight of a layer
+ * with ci input channels is sqrt(2 / (9 ci)) times a standard normal sample
+ * (He initialisation), each bias 0.  Sample i depends only on (seed, i): a
+ * splitmix64 hash of both gives two uniforms, Box-Muller turns them into a
+ * normal.  Asynchronous on `stream`. */
+sf_status sf_confnet_init(float* params, uint64_t seed, void* stream);
+
+/* Writes the device parameters to a file at `path` (host string): the bytes
+ * "SFCN", then little-endian uint32 version (1), features (8), channels (32),
+ * count (21121), then count float32 values in the order above.  Copies
+ * synchronously.  A file that cannot be written returns SF_ERR_INVALID_ARG. */
+sf_status sf_confnet_save(const float* params, const char* path);
+
+/* Reads a file written by sf_confnet_save into the device buffer `params`.
+ * A missing file, another format, version or size, or trailing bytes return
+ * SF_ERR_INVALID_ARG and leave `params` unchanged. */
+sf_status sf_confnet_load(const char* path, float* params);
+
 /* Bytes of the packed inference weights written by sf_confnet_pack. */
 size_t sf_confnet_packed_bytes(void);
 

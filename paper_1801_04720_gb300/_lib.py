@@ -34,6 +34,7 @@ EXPORTED = [
     "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
     "sf_scene_flow_learned", "sf_scene_flow_learned_frames", "sf_debug_set",
     "sf_pipeline_create", "sf_pipeline_submit", "sf_pipeline_wait", "sf_pipeline_destroy",
+    "sf_confnet_init", "sf_confnet_save", "sf_confnet_load",
 ]
 
 SF_DEBUG_SPIN_LIMIT = 1
@@ -144,6 +145,9 @@ def load(path: str = LIB_PATH):
             "sf_scene_flow_learned_frames": (i32, [P, i32, i32, i32, i32, PP, PC, P, ctypes.c_float, P, sz,
                                                    P]),
             "sf_confnet_param_count": (i32, []),
+            "sf_confnet_init": (i32, [P, ctypes.c_uint64, P]),
+            "sf_confnet_save": (i32, [P, ctypes.c_char_p]),
+            "sf_confnet_load": (i32, [ctypes.c_char_p, P]),
             "sf_confnet_packed_bytes": (sz, []),
             "sf_confnet_pack": (i32, [P, P, P]),
             "sf_confnet_infer": (i32, [P, P, P, P, i32, i32, ctypes.c_float, P, P, P, P]),
@@ -519,6 +523,24 @@ def sf_set_sweep_shape(d_lo, d_hi, dc, halo):
 
 def confnet_param_count() -> int:
     return int(load().sf_confnet_param_count())
+
+
+def confnet_init(seed, device="cuda", stream=None):
+    """sf_confnet_init: seeded He-normal parameters (fp32 device tensor)."""
+    params = torch.empty(int(load().sf_confnet_param_count()), dtype=torch.float32, device=device)
+    _check("sf_confnet_init", load().sf_confnet_init(_ptr(params), int(seed) & (2 ** 64 - 1), _stream(stream)))
+    return params
+
+
+def confnet_save(params, path):
+    _dev(params, torch.float32, "params")
+    _check("sf_confnet_save", load().sf_confnet_save(_ptr(params), os.fsencode(path)))
+
+
+def confnet_load(path, device="cuda"):
+    params = torch.empty(int(load().sf_confnet_param_count()), dtype=torch.float32, device=device)
+    _check("sf_confnet_load", load().sf_confnet_load(os.fsencode(path), _ptr(params)))
+    return params
 
 
 def confnet_pack(params_t, stream=None):
