@@ -10,6 +10,8 @@
 //      integer rate, so sharing the distances between both passes halves it.
 //      Rows whose W x (Dp + 16) bytes exceed one CTA's shared memory take
 //      cost_tiled_kernel instead: one launch per reference image, x-tiles.
+//      The learned path needs C_L alone: the same kernel then writes each
+//      row's distances straight to C_L, without the shared-memory band.
 //   2. hline_kernel: the two horizontal paths (+1,0) and (-1,0), each row an
 //      independent line; two rows share a register (u16x2 lanes).  Writes
 //      L_r as uint8 volumes.  Runs beside the down sweep.
@@ -63,7 +65,9 @@ __global__ void __launch_bounds__(1024, 1)
   // (srt[j & 3][j >> 2]) so that lanes reading cR(x - 4 lane - k) hit
   // consecutive words.  Then the distances H(cL(x), cR(x-d)) as rows
   // [W][Ds]; 4 padding bytes per row spread the diagonal reads of the
-  // right-reference pass over the banks.
+  // right-reference pass over the banks.  With CR == nullptr (the left
+  // volume only) each row's distances go straight to C_L and no band is used.
+  const bool left_only = CR == nullptr;
   const int Q = (W + 3) >> 2;
   const int cw = W + 4 * Q;   // 8-byte words per census buffer
   uint64_t* cbuf = reinterpret_cast<uint64_t*>(smem);
@@ -90,7 +94,8 @@ __global__ void __launch_bounds__(1024, 1)
     const uint64_t* srt = sl + W;
     for (int x = warp; x < W; x += nw) {
       const uint64_t a = sl[x];
-      uint32_t* row = reinterpret_cast<uint32_t*>(band + x * Ds);
+      uint32_t* row = left_only ? reinterpret_cast<uint32_t*>(CL + ((size_t)y * W + x) * Dp)
+                                : reinterpret_cast<uint32_t*>(band + x * Ds);
       // right pixel j = x - 4g - k sits at srt[(x-k) & 3][((x-k) >> 2) - g]
       int base[4];
 #pragma unroll
@@ -109,6 +114,7 @@ __global__ void __launch_bounds__(1024, 1)
         row[g] = packed;
       }
     }
+    if (left_only) continue;
     __syncthreads();
     // left-reference row: the rows of the band; right-reference row:
     // C_R(x, d) = band[x + d][d], or cmax past the edge
@@ -957,8 +963,20 @@ cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int 
                              int cmax, uint8_t* CL, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
   count_launches(1);
-  dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
-  cost_tiled_kernel<<<grid, 256, 0, s>>>(cL, cR, W, H, D, Dp, cmax, 0, CL);
+  // the persistent kernel without its band: two census rows in shared memory
+  const size_t smem = 2 * ((size_t)W + 4 * (size_t)((W + 3) / 4)) * sizeof(uint64_t);
+  if (smem > kCostPairSmemMax) {
+    dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
+    cost_tiled_kernel<<<grid, 256, 0, s>>>(cL, cR, W, H, D, Dp, cmax, 0, CL);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaFuncSetAttribute(cost_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  cost_pair_kernel<<<std::min(H, sms), 1024, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, nullptr);
   return cudaGetLastError();
 }
 
