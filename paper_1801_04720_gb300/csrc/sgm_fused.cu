@@ -100,16 +100,23 @@ __global__ void __launch_bounds__(1024, 1)
       int base[4];
 #pragma unroll
       for (int k = 0; k < 4; k++) base[k] = ((x - k) & 3) * Q + ((x - k) >> 2);
+      // every candidate of this column exists (warp-uniform): no checks
+      const bool full = D == Dp && x >= Dp - 1;
       for (int g = lane; g < groups; g += 32) {
         const int d0 = 4 * g;
         uint32_t packed = 0;
+        if (full) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const bool ok = d0 + k < D && d0 + k <= x;
-          // (index 0 where there is no candidate: every address stays in the row)
-          const uint64_t b = srt[ok ? base[k] - g : 0];
-          const uint32_t c = ok ? (uint32_t)__popcll(a ^ b) : (uint32_t)cmax;
-          packed |= c << (8 * k);
+          for (int k = 0; k < 4; k++) packed |= (uint32_t)__popcll(a ^ srt[base[k] - g]) << (8 * k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            const bool ok = d0 + k < D && d0 + k <= x;
+            // (index 0 where there is no candidate: every address stays in the row)
+            const uint64_t b = srt[ok ? base[k] - g : 0];
+            const uint32_t c = ok ? (uint32_t)__popcll(a ^ b) : (uint32_t)cmax;
+            packed |= c << (8 * k);
+          }
         }
         row[g] = packed;
       }
@@ -123,16 +130,22 @@ __global__ void __launch_bounds__(1024, 1)
     for (int x = warp; x < W; x += nw) {
       const uint32_t* src = reinterpret_cast<const uint32_t*>(band + x * Ds);
       const int diag = x * Ds;   // band[x + d][d] = band[diag + d (Ds + 1)]
+      const bool inside = x + Dp <= W;   // the whole diagonal is in the row (warp-uniform)
       for (int g = lane; g < groups; g += 32) {
         dl[x * groups + g] = src[g];
         const int d0 = 4 * g;
         const int o0 = diag + d0 * (Ds + 1);
         uint32_t packed = 0;
+        if (inside) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const bool in = x + d0 + k < W;
-          const uint32_t v = band[in ? o0 + k * (Ds + 1) : 0];
-          packed |= (in ? v : (uint32_t)cmax) << (8 * k);
+          for (int k = 0; k < 4; k++) packed |= (uint32_t)band[o0 + k * (Ds + 1)] << (8 * k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            const bool in = x + d0 + k < W;
+            const uint32_t v = band[in ? o0 + k * (Ds + 1) : 0];
+            packed |= (in ? v : (uint32_t)cmax) << (8 * k);
+          }
         }
         dr[x * groups + g] = packed;
       }
