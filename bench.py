@@ -35,9 +35,10 @@ def parse():
                     help="keep the built-in sweep shape instead of the tuned one")
     ap.add_argument("--batch", type=int, default=64,
                     help="quadruples in the uneven-batch measurement (0 = skip)")
-    ap.add_argument("--learned-eval", type=int, default=200,
+    ap.add_argument("--learned-eval", type=int, default=None,
                     help="held-out scenes for the learned path's false-accept rate "
-                         "(0 = timing only, -1 = skip the learned path)")
+                         "(0 = timing only, -1 = skip the learned path; default 200, "
+                         "-1 under --profile)")
     ap.add_argument("--stream", type=int, default=2,
                     help="frames of the 2048x1024, D=256 stream recipe to time (0 = skip)")
     ap.add_argument("--shape", default=None,
@@ -51,8 +52,9 @@ def parse():
         args.no_cpu_baseline = True
         args.batch = 0
         args.no_autotune = True
-        args.learned_eval = -1
         args.stream = 0
+    if args.learned_eval is None:
+        args.learned_eval = -1 if args.profile else 200
     return args
 
 
@@ -161,6 +163,18 @@ def bytes_model(stage, N, D, passes=4):
     if stage == "sgm_sweep":
         return passes * 2 * N * D
     return 3 * N * D
+
+
+def frame_bytes_model(N, D):
+    """Algorithmic HBM bytes of one plain scene-flow frame (4 SGM passes and
+    the combination) for a design that stores nothing but the partial sum of
+    one scan order: per pass that uint16 sum is written once and read once
+    (4 N D), 16 N D over the passes; plus the four images in (4 N), their
+    census strings written and read (64 N), the integer winners of the four
+    passes written and read by the checks (16 N), both disparity maps
+    written and read (16 N), the flow in (8 N) and the outputs out (s4,
+    motion, point, valid: 41 N)."""
+    return 16 * N * D + 149 * N
 
 
 def measured_traffic(stage, shape=None):
@@ -338,6 +352,10 @@ def run_ours(args, world, rank, local):
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": round(dom_ms, 5)},
+        "frame_hbm": {"model_bytes_per_frame": frame_bytes_model(N, D_MAX),
+                      "achieved_gbs": round(frame_bytes_model(N, D_MAX) / (ms * 1e-3) / 1e9, 1),
+                      "frac": round(frame_bytes_model(N, D_MAX) / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+                      "model": "frame_bytes_model: 16 N D + 149 N"},
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_tot.items()},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "sweep_shape": tuned["classes"] if tuned else "built-in",
@@ -561,7 +579,12 @@ def run_stream(args, dev, _lib, torch, flush):
     N = W * H
     return {"workload": f"automotive stream {W}x{H} D={D}, 40 moving segments, {n} frames rendered",
             "plain": {"value": round(1000.0 / ms_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain, 3),
-                      "Gcost_entries_per_s": round(4 * N * D / (ms_plain * 1e-3) / 1e9, 1)},
+                      "Gcost_entries_per_s": round(4 * N * D / (ms_plain * 1e-3) / 1e9, 1),
+                      "hbm": {"model_bytes_per_frame": frame_bytes_model(N, D),
+                              "achieved_gbs": round(frame_bytes_model(N, D) / (ms_plain * 1e-3) / 1e9, 1),
+                              "peak_gbs": peaks()[0],
+                              "frac": round(frame_bytes_model(N, D) / (ms_plain * 1e-3) / 1e9 / peaks()[0], 4),
+                              "model": "frame_bytes_model: 16 N D + 149 N"}},
             "learned_two_frames_per_launch": {"value": round(2000.0 / ms_learned, 2), "unit": "frames/s",
                                               "ms_per_step": round(ms_learned, 3)},
             "learned_vs_plain_check": {k: round(v, 5) for k, v in rates.items()},
