@@ -376,10 +376,14 @@ constexpr int kSmX = kSmFeat + kPlane0;             // layer-1 then layer-3 acti
 constexpr int kSmY = kSmX + 4 * kPlane1;            // layer-2 activations
 constexpr int kSmW = kSmY + 4 * kPlane2;            // packed weights
 constexpr int kSmBias = kSmW + kWElems * 2;
-constexpr int kSmBar = kSmBias + kBiasFloats * 4;
-constexpr int kSmTmem = kSmBar + 8;
+constexpr int kMaxPairs = (region_rows(1) * kP / 128 + 1) / 2;   // M-tile pairs of the largest layer
+constexpr int kSmBar = kSmBias + kBiasFloats * 4;                  // one mbarrier per M-tile pair
+constexpr int kSmTmem = kSmBar + 8 * (kMaxPairs + 1);            // + one for the final drain
 constexpr int kSmTotal = kSmTmem + 8;
-constexpr int kThreads = 256;
+constexpr int kEpiWarps = 8;                                       // epilogue warps (two per TMEM lane quarter)
+constexpr int kIssuer = kEpiWarps;                                 // the warp that issues the MMAs
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = kEpiThreads + 32;
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kMmaSpin = 1ll << 24;
 static_assert(4 * kPlane3 <= 4 * kPlane1, "layer-3 activations reuse the layer-1 buffer");
@@ -493,7 +497,8 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   for (int i = tid; i < (kWElems * 2 + kBiasFloats * 4) / 16; i += kThreads)
     reinterpret_cast<uint4*>(sm + kSmW)[i] = wsrc[i];
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    for (int i = 0; i <= kMaxPairs; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + i)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -509,7 +514,6 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t barp = smem_u32(bar);
-  uint32_t phase = 0;
   bool failed = false;
 
   const int tiles_x = (a.W + kTX - 1) / kTX, tiles_y = (a.H + kTY - 1) / kTY;
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
     const int ps = t / per_pass, tl = t - ps * per_pass;
     const uint16_t* feat = a.pass[ps].feat;
     const int X0 = (tl % tiles_x) * kTX, Y0 = (tl / tiles_x) * kTY;
-    for (int i = tid; i < region_rows(0) * kP; i += kThreads) {
+    for (int i = tid; i < region_rows(0) * kP; i += kEpiThreads) {
       const int gy = Y0 - 4 + i / kP, gx = X0 - 4 + i % kP;
       const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
       const void* src = in ? static_cast<const void*>(reinterpret_cast<const uint4*>(feat) + (size_t)gy * a.W + gx)
@@ -549,7 +553,59 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   const uint64_t ad3 = mat_desc(smem_u32(bufy), kPlane2, 128u), bd3 = mat_desc(w3_base, kC * 16u, 128u);
   const uint64_t ad4 = mat_desc(smem_u32(bufx), kPlane3, 128u), bd4 = mat_desc(w4_base, 16u * 16u, 128u);
 
-  if (blockIdx.x < ntiles) fetch_features(blockIdx.x);
+  // epilogue of one M tile of a layer: this warp's 32 rows (its TMEM lane
+  // quarter) -> bias, ReLU, bf16 -> the next layer's planes; the last layer
+  // writes the probability and the decisions
+  auto epilogue = [&](int layer, int mt, int X0, int Y0, const InferPass& out) {
+    const int rg0 = 4 - (layer + 1);                  // region origin offset of the output
+    const int wl = kP - 2 * (layer + 1);              // valid region width
+    const int m = 128 * mt + 32 * quad + lane;
+    const int i = m / kP, jj = m - i * kP;
+    if (layer < 3) {
+      uint8_t* dst = layer == 1 ? bufy : bufx;
+      const int plane = layer == 0 ? kPlane1 : layer == 1 ? kPlane2 : kPlane3;
+      const float* bl = bias + kC * layer;
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(kC * mt), v);
+      const int gy = Y0 - rg0 + i, gx = X0 - rg0 + jj;
+      const bool keep = jj < wl && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+#pragma unroll
+      for (int cgrp = 0; cgrp < 4; cgrp++) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float lo = keep ? fmaxf(v[8 * cgrp + 2 * e] + bl[8 * cgrp + 2 * e], 0.0f) : 0.0f;
+          const float hi = keep ? fmaxf(v[8 * cgrp + 2 * e + 1] + bl[8 * cgrp + 2 * e + 1], 0.0f) : 0.0f;
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
+          w4[e] = *reinterpret_cast<const uint32_t*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(dst + cgrp * plane + 16 * m) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      }
+    } else {
+      const float z = tmem_ld1(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(16 * mt)) + bias[3 * kC];
+      const int gy = Y0 + i, gx = X0 + jj;
+      if (jj < kTX && gy < a.H && gx < a.W) {
+        const float prob = 1.0f / (1.0f + expf(-z));
+        const size_t pix = (size_t)gy * a.W + gx;
+        if (out.prob) out.prob[pix] = prob;
+        if (out.valid || out.disp) {
+          const bool ok = gx - (int)out.dint[pix] >= 0 && prob >= a.threshold;
+          if (out.valid) out.valid[pix] = ok ? 1 : 0;
+          if (out.disp) out.disp[pix] = ok ? out.dsub[pix] : __int_as_float(0x7fc00000);
+        }
+      }
+    }
+  };
+
+  // Per layer the issuer commits the MMAs of each pair of M tiles to that
+  // pair's mbarrier; the epilogue warps take the pairs as they complete
+  // (warps 0-3 the even tile of a pair, 4-7 the odd one), so the epilogue of
+  // one pair overlaps the MMAs of the next.  The layer ends with a CTA
+  // barrier: the next layer reads the activations just written and reuses
+  // the TMEM columns.
+  const bool epi = warp < kEpiWarps;
+  uint32_t phases = 0;                                // parity of each pair's mbarrier
+  if (epi && blockIdx.x < ntiles) fetch_features(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int ps = tile / per_pass, tl = tile - ps * per_pass;
     const InferPass& out = a.pass[ps];
@@ -561,108 +617,72 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
     fence_after();
 
     for (int layer = 0; layer < 4 && !failed; layer++) {
-      const int out_rows = region_rows(layer + 1);
-      const int nm = out_rows * kP / 128;
+      const int nm = region_rows(layer + 1) * kP / 128;
+      const int npairs = (nm + 1) / 2;
       const int N = layer == 3 ? 16 : kC;
-      const uint32_t idesc = instr_desc(N);
-      // ---- issue: warp 0 walks the MMAs of all M tiles (warp-uniform
-      // descriptors), one elected lane issues each ----
-      if (warp == 0) {
-        fence_after();
-        if (layer == 0) {
-          for (int mt = 0; mt < nm; mt++) {
-#pragma unroll
-            for (int j = 0; j < 5; j++)
-              if (elect_one()) mma_bf16(tmem + (uint32_t)(kC * mt), ad1[j] + 128u * mt, bd1[j], idesc, j > 0);
-          }
-        } else {
-          const uint64_t ab = layer == 1 ? ad2 : layer == 2 ? ad3 : ad4;
-          const uint64_t bb = layer == 1 ? bd2 : layer == 2 ? bd3 : bd4;
-          const uint32_t plane16 = (layer == 1 ? kPlane1 : layer == 2 ? kPlane2 : kPlane3) / 16;
-          for (int mt = 0; mt < nm; mt++) {
-            const uint64_t am = ab + 128u * mt;
-#pragma unroll
-            for (int t = 0; t < 9; t++) {
-#pragma unroll
-              for (int s = 0; s < 2; s++)
-                if (elect_one())
-                  mma_bf16(tmem + (uint32_t)(N * mt), am + 2u * s * plane16 + (uint32_t)tap_off(t),
-                           bb + (uint32_t)(2 * t + s) * 2u * N, idesc, (t | s) != 0);
-            }
-          }
-        }
-        if (elect_one()) mma_commit(barp);
-        __syncwarp();
-      }
-      // ---- wait for the layer's accumulators (bounded) ----
-      long long spins = 0;
       bool timed_out = false;
-      while (!bar_try_wait(barp, phase)) {
-        if (++spins > kMmaSpin) {
-          timed_out = true;
-          break;
-        }
-      }
-      phase ^= 1u;
-      failed = __syncthreads_or(timed_out) != 0;
-      // layer 1 has read the features: the next tile's may come in
-      if (layer == 0 && !failed && tile + (int)gridDim.x < ntiles) fetch_features(tile + gridDim.x);
-      if (failed) {
-        if (tid == 0 && a.err) atomicExch(a.err, 1);
-        break;
-      }
-      fence_after();
-      // ---- epilogue: this warp's 32 rows of its M tiles ----
-      const int rg0 = 4 - (layer + 1);                  // region origin offset of the output
-      const int wl = kP - 2 * (layer + 1);              // valid region width
-      if (layer < 3) {
-        uint8_t* out = layer == 1 ? bufy : bufx;
-        const int plane = layer == 0 ? kPlane1 : layer == 1 ? kPlane2 : kPlane3;
-        const float* bl = bias + kC * layer;
-        for (int mt = half; mt < nm; mt += 2) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(kC * mt), v);
-          const int m = 128 * mt + 32 * quad + lane;
-          const int i = m / kP, jj = m - i * kP;
-          const int gy = Y0 - rg0 + i, gx = X0 - rg0 + jj;
-          const bool keep = jj < wl && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+      if (warp == kIssuer) {
+        // ---- issue: warp-uniform descriptors, one elected lane per MMA ----
+        fence_after();
+        const uint32_t idesc = instr_desc(N);
+        const uint64_t ab = layer == 1 ? ad2 : layer == 2 ? ad3 : ad4;
+        const uint64_t bb = layer == 1 ? bd2 : layer == 2 ? bd3 : bd4;
+        const uint32_t plane16 = (layer == 1 ? kPlane1 : layer == 2 ? kPlane2 : kPlane3) / 16;
+        for (int pi = 0; pi < npairs; pi++) {
+          for (int mt = 2 * pi; mt < 2 * pi + 2 && mt < nm; mt++) {
+            if (layer == 0) {
 #pragma unroll
-          for (int cgrp = 0; cgrp < 4; cgrp++) {
-            uint32_t w4[4];
+              for (int j = 0; j < 5; j++)
+                if (elect_one()) mma_bf16(tmem + (uint32_t)(kC * mt), ad1[j] + 128u * mt, bd1[j], idesc, j > 0);
+            } else {
+              const uint64_t am = ab + 128u * mt;
 #pragma unroll
-            for (int e = 0; e < 4; e++) {
-              const float lo = keep ? fmaxf(v[8 * cgrp + 2 * e] + bl[8 * cgrp + 2 * e], 0.0f) : 0.0f;
-              const float hi = keep ? fmaxf(v[8 * cgrp + 2 * e + 1] + bl[8 * cgrp + 2 * e + 1], 0.0f) : 0.0f;
-              const __nv_bfloat162 h2 = __floats2bfloat162_rn(lo, hi);
-              w4[e] = *reinterpret_cast<const uint32_t*>(&h2);
+              for (int t = 0; t < 9; t++) {
+#pragma unroll
+                for (int s = 0; s < 2; s++)
+                  if (elect_one())
+                    mma_bf16(tmem + (uint32_t)(N * mt), am + 2u * s * plane16 + (uint32_t)tap_off(t),
+                             bb + (uint32_t)(2 * t + s) * 2u * N, idesc, (t | s) != 0);
+              }
             }
-            *reinterpret_cast<uint4*>(out + cgrp * plane + 16 * m) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
           }
+          if (elect_one()) mma_commit(barp + 8u * (uint32_t)pi);
+          __syncwarp();
         }
       } else {
-        for (int mt = half; mt < nm; mt += 2) {
-          const float z = tmem_ld1(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(16 * mt)) + bias[3 * kC];
-          const int m = 128 * mt + 32 * quad + lane;
-          const int i = m / kP, jj = m - i * kP;
-          const int gy = Y0 + i, gx = X0 + jj;
-          if (jj < kTX && gy < a.H && gx < a.W) {
-            const float prob = 1.0f / (1.0f + expf(-z));
-            const size_t pix = (size_t)gy * a.W + gx;
-            if (out.prob) out.prob[pix] = prob;
-            if (out.valid || out.disp) {
-              const bool ok = gx - (int)out.dint[pix] >= 0 && prob >= a.threshold;
-              if (out.valid) out.valid[pix] = ok ? 1 : 0;
-              if (out.disp) out.disp[pix] = ok ? out.dsub[pix] : __int_as_float(0x7fc00000);
+        // ---- epilogue, pair by pair (bounded waits) ----
+        for (int pi = 0; pi < npairs; pi++) {
+          long long spins = 0;
+          while (!bar_try_wait(barp + 8u * (uint32_t)pi, (phases >> pi) & 1u)) {
+            if (++spins > kMmaSpin) {
+              timed_out = true;
+              break;
             }
           }
+          phases ^= 1u << pi;
+          if (timed_out) break;
+          fence_after();
+          const int mt = 2 * pi + half;
+          if (mt < nm) epilogue(layer, mt, X0, Y0, out);
         }
+        // every MMA of layer 1 has completed: the next tile's features may come in
+        if (layer == 0 && !timed_out && tile + (int)gridDim.x < ntiles) fetch_features(tile + gridDim.x);
       }
       fence_async_smem();
       fence_before();
-      __syncthreads();
+      failed = __syncthreads_or(timed_out) != 0;
+      if (failed && tid == 0 && a.err) atomicExch(a.err, 1);
     }
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy left in flight
+  if (warp == kIssuer) {
+    // no MMA left in flight before the TMEM is freed (a no-op unless a wait gave up)
+    if (elect_one()) mma_commit(barp + 8u * (uint32_t)kMaxPairs);
+    __syncwarp();
+    long long spins = 0;
+    while (!bar_try_wait(barp + 8u * (uint32_t)kMaxPairs, 0u) && ++spins <= kMmaSpin) {
+    }
+  }
   fence_before();
   __syncthreads();
   fence_after();
