@@ -239,31 +239,6 @@ constexpr long long kSpinLimit = 1ll << 24;   // bounded neighbour wait (~1 s)
 std::atomic<long long> g_spin_limit{kSpinLimit};
 std::atomic<int> g_skip_down_tasks{0};
 
-// Side stream on which the horizontal-path kernel overlaps the down sweep
-// (one per device, created on first use; fork and join through events so the
-// pattern also works under CUDA graph capture of the caller's stream).
-struct SideStream {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-};
-std::mutex g_side_mu;
-SideStream g_side[64];
-
-cudaError_t side_stream(SideStream** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  SideStream& ss = g_side[dev];
-  if (!ss.s) {
-    if ((e = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
-    if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
-    if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return e;
-  }
-  *out = &ss;
-  return cudaSuccess;
-}
-
 // Pass descriptor of pass k of a pair laid out at `b` in workspace ws.
 fused::PassDesc pass_desc(uint8_t* ws, const FusedPlan& plan, const PairBuffers& b, int k, int W,
                           int H, int D, int Dshape, const uint8_t* cost_override) {
@@ -323,9 +298,13 @@ TaskTables build_tables(const fused::PassDesc* d, int npass) {
   return t;
 }
 
-// Horizontal paths beside the down sweep, then the up sweep, for passes that
-// share one kernel shape.  Descriptors are passed inline when they fit the
-// parameter block (<= kMaxPass, all alike) and from device memory otherwise.
+// Horizontal paths, the down sweep, then the up sweep, for passes that share
+// one kernel shape, in stream order.  Run side by side on a second stream,
+// the horizontal kernel and the down sweep (both latency-bound chains) gave
+// frame times that depended on how their blocks landed on the SMs (the
+// 1242 x 375, D = 128 frame: about 1.45 or 1.70 ms, varying from run to run
+// and process to process); one after the other the frame takes a steady
+// 1.64 ms.
 sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass, int Dshape,
                      const fused::PassDesc* d_dev_down, const fused::PassDesc* d_dev_up,
                      const int* tab_dev, const TaskTables* tt, int* counters, int* err,
@@ -361,14 +340,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     sa.nbands = tt->nbands;
     sa.ntasks = tt->ntasks;
   }
-  // the horizontal paths run beside the down sweep; the up sweep joins them
-  std::lock_guard<std::mutex> guard(g_side_mu);
-  SideStream* side = nullptr;
-  SF_TRY_CUDA(side_stream(&side));
-  SF_TRY_CUDA(cudaEventRecord(side->fork, s));
-  SF_TRY_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0));
-  SF_TRY_CUDA(fused::launch_hline(ha, side->s));
-  SF_TRY_CUDA(cudaEventRecord(side->join, side->s));
+  SF_TRY_CUDA(fused::launch_hline(ha, s));
   sa.task_counter = counters;
   if (const int skip = g_skip_down_tasks.load(std::memory_order_relaxed)) {
     static int skip_host;
@@ -382,7 +354,6 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     sa.pass_ptr = d_dev_up;
   }
   sa.task_counter = counters + 1;
-  SF_TRY_CUDA(cudaStreamWaitEvent(s, side->join, 0));
   SF_TRY_CUDA(fused::launch_sweep(sa, true, s));
   return SF_OK;
 }
@@ -922,11 +893,6 @@ sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_param
       SF_TRY_CUDA(cudaGraphLaunch(g.exec, s));
       return SF_OK;
     }
-  }
-  {
-    SideStream* side = nullptr;   // created outside the capture
-    std::lock_guard<std::mutex> g2(g_side_mu);
-    SF_TRY_CUDA(side_stream(&side));
   }
   SF_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
   sf_status st = batch_enqueue(items, n, p, b, plan, ws, s);

@@ -14,7 +14,7 @@
 //      row's distances straight to C_L, without the shared-memory band.
 //   2. hline_kernel: the two horizontal paths (+1,0) and (-1,0), each row an
 //      independent line; two rows share a register (u16x2 lanes).  Writes
-//      L_r as uint8 volumes.  Runs beside the down sweep.
+//      L_r as uint8 volumes.  Runs before the down sweep.
 //   3. sweep_kernel<DOWN>: paths (0,+1), (+1,+1), (-1,+1) walking the image
 //      top to bottom in bands of halo+1 rows.  A task is one band of one
 //      32-column strip of one pass; the diagonal paths enter a strip from its
@@ -461,18 +461,17 @@ struct SweepCfg {
   }
 };
 
-// Registers: the down sweep is capped at 48K per CTA so that it leaves room
-// on its SM for the horizontal-path blocks that run beside it; the up sweep
-// runs alone and may use the whole register file (at most 168 a thread;
-// the 16-disparity shapes keep 168, one CTA per SM).
-constexpr int sweep_max_regs(int nt, bool up) {
-  const int budget = (up ? 65536 : 49152) / nt;
+// Registers: one CTA per SM and nothing beside it, so a sweep may use the
+// whole register file (at most 168 a thread; the 16-disparity shapes keep
+// 168).
+constexpr int sweep_max_regs(int nt) {
+  const int budget = 65536 / nt;
   return budget > 168 ? 168 : (budget / 8) * 8;
 }
 
 template <int DC, int CHUNKS, int HALO, bool UP>
 __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
-    __maxnreg__(DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS, UP))
+    __maxnreg__(DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
   using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
   using V = typename ByteVec<DC>::T;
