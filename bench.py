@@ -178,9 +178,9 @@ def frame_bytes_model(N, D):
 
 
 def measured_traffic(stage, shape=None):
-    """DRAM bytes per launch of `stage` from the committed ncu capture, or None
-    when there is none, the kernel sources changed since it was taken, or it
-    was taken with another sweep shape ("DCxHALO") than the one timed."""
+    """DRAM bytes per launch of `stage` from the committed ncu captures, or
+    None when there is none for the sweep shape ("DCxHALO") timed, or the
+    kernel sources changed since they were taken."""
     import hashlib
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -190,6 +190,8 @@ def measured_traffic(stage, shape=None):
             h.update(open(os.path.join(ROOT, src), "rb").read())
         if h.hexdigest() != rec["sources_sha256"]:
             return None
+        if "by_shape" in rec:
+            return rec["by_shape"][shape]["bytes_per_launch"] if shape in rec["by_shape"] else None
         if rec.get("shape", "any") != "any" and rec.get("shape") != shape:
             return None
         return rec["bytes_per_launch"]
