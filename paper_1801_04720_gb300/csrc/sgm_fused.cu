@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256)
 // an mbarrier, so the serial walk along x reads its costs from shared memory.
 constexpr int kHlinePairs = 8;                 // line pairs per CTA
 constexpr int kHlineRows = 2 * kHlinePairs;
-constexpr int kHlineTileBytes = 32 * 1024;     // one buffer
+constexpr int kHlineTileBytes = 56 * 1024;     // one buffer (two CTAs fit an SM)
 constexpr long long kMbarSpin = 1ll << 22;     // bounded mbarrier wait
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -1028,10 +1028,12 @@ static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   count_launches(1);
-  // the horizontal volumes do not depend on the sweeps' shape: 8 disparities
-  // per thread (shortest serial step) wherever 16 chunks cover D
+  // the horizontal volumes do not depend on the sweeps' shape: 16
+  // disparities per thread (with the kernel running alone, the shorter
+  // chunk-minimum reduction and the wider per-thread work measured faster
+  // than 8 at D = 128)
   Shape sh;
-  sh.dc = a.Dmax <= 128 ? 8 : 16;
+  sh.dc = 16;
   sh.chunks = sh.dc == 8 ? 2 : 4;
   while (sh.chunks * sh.dc < a.Dmax) sh.chunks <<= 1;
   sh.halo = 0;
