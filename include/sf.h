@@ -5,7 +5,9 @@
  *
  * C ABI.  Plain pointers and sizes only.  Unless a function says otherwise:
  *   - every array pointer is a DEVICE pointer owned by the caller; the library
- *     never allocates, frees or keeps a pointer after the call returns;
+ *     never allocates, frees or keeps a pointer after the call returns (the
+ *     frame pipeline, sf_pipeline_*, is the one exception: it owns device
+ *     memory between sf_pipeline_create and sf_pipeline_destroy);
  *   - parameter structs (sf_sgm_params, sf_camera) live in HOST memory and are
  *     read during the call only;
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream); the work
@@ -439,7 +441,9 @@ sf_status sf_confnet_init(float* params, uint64_t seed, void* stream);
 /* Writes the device parameters to a file at `path` (host string): the bytes
  * "SFCN", then little-endian uint32 version (1), features (8), channels (32),
  * count (21121), then count float32 values in the order above.  Copies
- * synchronously.  A file that cannot be written returns SF_ERR_INVALID_ARG. */
+ * synchronously on the legacy default stream, which does not wait for
+ * non-blocking streams: finish the work that wrote `params` first.  A file
+ * that cannot be written returns SF_ERR_INVALID_ARG. */
 sf_status sf_confnet_save(const float* params, const char* path);
 
 /* Reads a file written by sf_confnet_save into the device buffer `params`.
