@@ -533,7 +533,9 @@ def confnet_init(seed, device="cuda", stream=None):
 
 
 def confnet_save(params, path):
+    """sf_confnet_save, after the work queued on this device has finished."""
     _dev(params, torch.float32, "params")
+    torch.cuda.synchronize(params.device)
     _check("sf_confnet_save", load().sf_confnet_save(_ptr(params), os.fsencode(path)))
 
 
