@@ -1,0 +1,67 @@
+"""bench.py's host-side models on CPU: the algorithmic byte counts behind the
+roofline numbers, and the lookup of measured DRAM traffic, which must give
+nothing once the kernel sources differ from those the capture was taken
+with, or for a sweep shape that was not captured."""
+import hashlib
+import json
+
+import pytest
+
+
+def test_sweep_bytes_model():
+    import bench
+    N, D = 1242 * 375, 128
+    # the partial sum of one scan order, uint16, written and read once per pass
+    assert bench.bytes_model("sgm_sweep", N, D) == 4 * 2 * N * D
+    assert bench.bytes_model("sgm_sweep", N, D) == 476_928_000
+    assert bench.bytes_model("aggregate", N, D) == 3 * N * D
+
+
+def test_frame_bytes_model_itemised():
+    import bench
+    N, D = 1000, 64
+    items = {
+        "partial sums, 4 passes x (write + read) x uint16": 4 * 2 * 2 * N * D,
+        "images in": 4 * N,
+        "census strings written and read": 4 * 8 * 2 * N,
+        "winners of four passes written and read": 4 * 2 * 2 * N,
+        "two disparity maps written and read": 2 * 4 * 2 * N,
+        "flow in": 8 * N,
+        "outputs (s4, motion, point, valid)": (16 + 12 + 12 + 1) * N,
+    }
+    assert bench.frame_bytes_model(N, D) == sum(items.values())
+
+
+@pytest.fixture()
+def fake_root(tmp_path, monkeypatch):
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"kernel v1")
+    sha = hashlib.sha256(b"kernel v1").hexdigest()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"sgm_sweep": {"by_shape": {"16x16": {"bytes_per_launch": 11}, "8x16": {"bytes_per_launch": 22}},
+                         "sources": ["k.cu"], "sources_sha256": sha},
+           "aggregate": {"bytes_per_launch": 33, "shape": "any", "sources": ["k.cu"], "sources_sha256": sha},
+           "old": {"bytes_per_launch": 44, "shape": "16x16", "sources": ["k.cu"], "sources_sha256": sha}}
+    (prof / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return src
+
+
+def test_measured_traffic_by_shape(fake_root):
+    import bench
+    assert bench.measured_traffic("sgm_sweep", "16x16") == 11
+    assert bench.measured_traffic("sgm_sweep", "8x16") == 22
+    assert bench.measured_traffic("sgm_sweep", "16x8") is None
+    assert bench.measured_traffic("aggregate") == 33
+    assert bench.measured_traffic("old", "16x16") == 44
+    assert bench.measured_traffic("old", "8x16") is None
+    assert bench.measured_traffic("missing") is None
+
+
+def test_measured_traffic_void_after_source_change(fake_root):
+    import bench
+    fake_root.write_bytes(b"kernel v2")
+    assert bench.measured_traffic("sgm_sweep", "16x16") is None
+    assert bench.measured_traffic("aggregate") is None
