@@ -358,17 +358,26 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
   return SF_OK;
 }
 
-// Census and the shared distance computation of one stereo pair.
-sf_status run_pair_costs(const uint8_t* left, const uint8_t* right, int W, int H, int pitch, int D,
-                         const sf_sgm_params* p, uint8_t* ws, const PairBuffers& b, cudaStream_t s) {
-  const size_t N = (size_t)W * H;
-  (void)N;
-  uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b.census_l);
-  uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b.census_r);
-  SF_TRY_CUDA(launch_census(left, W, H, pitch, p->census_w, p->census_h, cl, s));
-  SF_TRY_CUDA(launch_census(right, W, H, pitch, p->census_w, p->census_h, cr, s));
-  SF_TRY_CUDA(fused::launch_cost_pair(cl, cr, W, H, D, fused::padded_d(D), p->census_w * p->census_h - 1,
-                                      ws + b.pass[0].cost, ws + b.pass[1].cost, s));
+// Census of `npairs` stereo pairs of one size, then the shared distance
+// computation of all of them in one launch (the rows of every pair spread
+// over the persistent CTAs).
+sf_status run_pair_costs(const uint8_t* const* left, const uint8_t* const* right, int npairs, int W, int H,
+                         int pitch, int D, const sf_sgm_params* p, uint8_t* ws, const PairBuffers* const* b,
+                         cudaStream_t s) {
+  if (npairs < 1 || npairs > fused::kMaxPass) return SF_ERR_INVALID_ARG;
+  fused::CostPairs job{};
+  job.npairs = npairs;
+  for (int k = 0; k < npairs; k++) {
+    uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b[k]->census_l);
+    uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b[k]->census_r);
+    SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, cl, s));
+    SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, cr, s));
+    job.cL[k] = cl;
+    job.cR[k] = cr;
+    job.CL[k] = ws + b[k]->pass[0].cost;
+    job.CR[k] = ws + b[k]->pass[1].cost;
+  }
+  SF_TRY_CUDA(fused::launch_cost_pair(job, W, H, D, fused::padded_d(D), p->census_w * p->census_h - 1, s));
   return SF_OK;
 }
 
@@ -381,8 +390,10 @@ sf_status run_fused_pairs(const uint8_t* const* left, const uint8_t* const* righ
   FusedPlan plan = single_plan(W, H, p->D, npairs);
   const size_t N = (size_t)W * H;
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
-  for (int k = 0; k < npairs; k++) {
-    sf_status st = run_pair_costs(left[k], right[k], W, H, pitch, p->D, p, ws, plan.pairs[k], s);
+  {
+    const PairBuffers* bufs[fused::kMaxPass];
+    for (int k = 0; k < npairs; k++) bufs[k] = &plan.pairs[k];
+    sf_status st = run_pair_costs(left, right, npairs, W, H, pitch, p->D, p, ws, bufs, s);
     if (st != SF_OK) return st;
   }
   fused::PassDesc d[fused::kMaxPass];
@@ -535,9 +546,10 @@ sf_status batch_enqueue(const sf_batch_item* items, int n, const sf_sgm_params* 
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
   for (int i = 0; i < n; i++) {
     const sf_batch_item& it = items[i];
-    sf_status st = run_pair_costs(it.left_t, it.right_t, it.W, it.H, it.pitch, it.D, p, ws, plan.pairs[2 * i], s);
-    if (st != SF_OK) return st;
-    st = run_pair_costs(it.left_t1, it.right_t1, it.W, it.H, it.pitch, it.D, p, ws, plan.pairs[2 * i + 1], s);
+    const uint8_t* L[2] = {it.left_t, it.left_t1};
+    const uint8_t* R[2] = {it.right_t, it.right_t1};
+    const PairBuffers* bufs[2] = {&plan.pairs[2 * i], &plan.pairs[2 * i + 1]};
+    sf_status st = run_pair_costs(L, R, 2, it.W, it.H, it.pitch, it.D, p, ws, bufs, s);
     if (st != SF_OK) return st;
   }
   uint8_t* tab = ws + plan.tables;
@@ -1124,13 +1136,22 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
   const int J = (W + fused::kTW - 1) / fused::kTW;
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
   fused::PassDesc d[fused::kMaxPass];
+  fused::CostPairs job{};
+  job.npairs = npairs;
   for (int k = 0; k < npairs; k++) {
     const LearnedPair& b = plan.pr[k];
     uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b.census_l);
     uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b.census_r);
     SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, cl, s));
     SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, cr, s));
-    SF_TRY_CUDA(fused::launch_cost_left(cl, cr, W, H, D, Dp, p->census_w * p->census_h - 1, ws + b.cost, s));
+    job.cL[k] = cl;
+    job.cR[k] = cr;
+    job.CL[k] = ws + b.cost;
+  }
+  // the left volumes of every pair in one launch
+  SF_TRY_CUDA(fused::launch_cost_left(job, W, H, D, Dp, p->census_w * p->census_h - 1, s));
+  for (int k = 0; k < npairs; k++) {
+    const LearnedPair& b = plan.pr[k];
     fused::PassDesc& pd = d[k];
     pd = fused::PassDesc{};
     pd.W = W; pd.H = H; pd.D = D; pd.Dp = Dp; pd.J = J;

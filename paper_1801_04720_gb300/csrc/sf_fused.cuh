@@ -82,11 +82,18 @@ inline size_t cost_pair_smem(int W, int D) {
 // rows whose census pair + distances exceed this use per-reference x-tiles
 constexpr size_t kCostPairSmemMax = 227u * 1024u;
 
-cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
-                             int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s);
-// left-reference volume only (x-tiled, one POPC per distance)
-cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
-                             int cmax, uint8_t* CL, cudaStream_t s);
+// Census strings and cost volumes of up to kMaxPass stereo pairs of one
+// size: one persistent launch over the rows of all of them.
+struct CostPairs {
+  int npairs;
+  const uint64_t* cL[kMaxPass];
+  const uint64_t* cR[kMaxPass];
+  uint8_t* CL[kMaxPass];
+  uint8_t* CR[kMaxPass];     // nullptr in launch_cost_left
+};
+cudaError_t launch_cost_pair(const CostPairs& job, int W, int H, int D, int Dp, int cmax, cudaStream_t s);
+// left-reference volumes only
+cudaError_t launch_cost_left(const CostPairs& job, int W, int H, int D, int Dp, int cmax, cudaStream_t s);
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s);
 cudaError_t launch_sweep(const SweepArgs& a, bool up, cudaStream_t s);
 

@@ -57,8 +57,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // 1. cost volumes of a stereo pair
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024, 1)
-    cost_pair_kernel(const uint64_t* __restrict__ cL, const uint64_t* __restrict__ cR, int W, int H,
-                     int D, int Dp, int cmax, uint8_t* __restrict__ CL, uint8_t* __restrict__ CR) {
+    cost_pair_kernel(const CostPairs job, int W, int H, int D, int Dp, int cmax) {
   extern __shared__ __align__(16) uint8_t smem[];
   // per census buffer (two, the next row's arriving while this row is
   // computed): the left census row, then the right one split by index mod 4
@@ -67,7 +66,10 @@ __global__ void __launch_bounds__(1024, 1)
   // [W][Ds]; 4 padding bytes per row spread the diagonal reads of the
   // right-reference pass over the banks.  With CR == nullptr (the left
   // volume only) each row's distances go straight to C_L and no band is used.
-  const bool left_only = CR == nullptr;
+  // One launch walks the rows of every pair of the job (row r: pair r / H),
+  // so the persistent CTAs share them evenly.
+  const bool left_only = job.CR[0] == nullptr;
+  const int nrows = job.npairs * H;
   const int Q = (W + 3) >> 2;
   const int cw = W + 4 * Q;   // 8-byte words per census buffer
   uint64_t* cbuf = reinterpret_cast<uint64_t*>(smem);
@@ -75,7 +77,10 @@ __global__ void __launch_bounds__(1024, 1)
   const int Ds = Dp + 4;
   const int groups = Dp >> 2;   // 4 disparities per lane and step
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  auto fetch = [&](int y, int buf) {
+  auto fetch = [&](int row, int buf) {
+    const int k = row / H, y = row - k * H;
+    const uint64_t* cL = job.cL[k];
+    const uint64_t* cR = job.cR[k];
     uint64_t* sl = cbuf + buf * cw;
     uint64_t* srt = sl + W;
     for (int i = threadIdx.x; i < W; i += blockDim.x) {
@@ -85,16 +90,19 @@ __global__ void __launch_bounds__(1024, 1)
     cp_async_commit();
   };
   int buf = 0;
-  if (blockIdx.x < H) fetch(blockIdx.x, 0);
-  for (int y = blockIdx.x; y < H; y += gridDim.x, buf ^= 1) {
+  if (blockIdx.x < nrows) fetch(blockIdx.x, 0);
+  for (int row = blockIdx.x; row < nrows; row += gridDim.x, buf ^= 1) {
+    const int pk = row / H, y = row - pk * H;
+    uint8_t* const CL = job.CL[pk];
+    uint8_t* const CR = job.CR[pk];
     cp_async_wait<0>();
     __syncthreads();   // this row's census is in; the band is free
-    if (y + (int)gridDim.x < H) fetch(y + gridDim.x, buf ^ 1);
+    if (row + (int)gridDim.x < nrows) fetch(row + gridDim.x, buf ^ 1);
     const uint64_t* sl = cbuf + buf * cw;
     const uint64_t* srt = sl + W;
     for (int x = warp; x < W; x += nw) {
       const uint64_t a = sl[x];
-      uint32_t* row = left_only ? reinterpret_cast<uint32_t*>(CL + ((size_t)y * W + x) * Dp)
+      uint32_t* dst = left_only ? reinterpret_cast<uint32_t*>(CL + ((size_t)y * W + x) * Dp)
                                 : reinterpret_cast<uint32_t*>(band + x * Ds);
       // right pixel j = x - 4g - k sits at srt[(x-k) & 3][((x-k) >> 2) - g]
       int base[4];
@@ -118,7 +126,7 @@ __global__ void __launch_bounds__(1024, 1)
             packed |= c << (8 * k);
           }
         }
-        row[g] = packed;
+        dst[g] = packed;
       }
     }
     if (left_only) continue;
@@ -971,15 +979,18 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
 
 }  // namespace
 
-cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
-                             int cmax, uint8_t* CL, cudaStream_t s) {
+cudaError_t launch_cost_left(const CostPairs& job, int W, int H, int D, int Dp, int cmax, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
-  count_launches(1);
+  if (job.npairs < 1 || job.npairs > kMaxPass) return cudaErrorInvalidValue;
+  CostPairs jl = job;
+  for (int k = 0; k < kMaxPass; k++) jl.CR[k] = nullptr;
   // the persistent kernel without its band: two census rows in shared memory
   const size_t smem = 2 * ((size_t)W + 4 * (size_t)((W + 3) / 4)) * sizeof(uint64_t);
   if (smem > kCostPairSmemMax) {
+    count_launches(job.npairs);
     dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
-    cost_tiled_kernel<<<grid, 256, 0, s>>>(cL, cR, W, H, D, Dp, cmax, 0, CL);
+    for (int k = 0; k < job.npairs; k++)
+      cost_tiled_kernel<<<grid, 256, 0, s>>>(job.cL[k], job.cR[k], W, H, D, Dp, cmax, 0, job.CL[k]);
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(cost_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -988,19 +999,24 @@ cudaError_t launch_cost_left(const uint64_t* cL, const uint64_t* cR, int W, int 
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  cost_pair_kernel<<<std::min(H, sms), 1024, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, nullptr);
+  count_launches(1);
+  cost_pair_kernel<<<std::min(job.npairs * H, sms), 1024, smem, s>>>(jl, W, H, D, Dp, cmax);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int Dp,
-                             int cmax, uint8_t* CL, uint8_t* CR, cudaStream_t s) {
+cudaError_t launch_cost_pair(const CostPairs& job, int W, int H, int D, int Dp, int cmax, cudaStream_t s) {
   StageTrace trace(SF_STAGE_COST, s);
+  if (job.npairs < 1 || job.npairs > kMaxPass) return cudaErrorInvalidValue;
+  for (int k = 0; k < job.npairs; k++)
+    if (!job.CR[k]) return cudaErrorInvalidValue;
   const size_t smem = cost_pair_smem(W, D);
   if (smem > kCostPairSmemMax) {
-    count_launches(2);
+    count_launches(2 * job.npairs);
     dim3 grid((W + kCostTileX - 1) / kCostTileX, H);
-    cost_tiled_kernel<<<grid, 256, 0, s>>>(cL, cR, W, H, D, Dp, cmax, 0, CL);
-    cost_tiled_kernel<<<grid, 256, 0, s>>>(cR, cL, W, H, D, Dp, cmax, 1, CR);
+    for (int k = 0; k < job.npairs; k++) {
+      cost_tiled_kernel<<<grid, 256, 0, s>>>(job.cL[k], job.cR[k], W, H, D, Dp, cmax, 0, job.CL[k]);
+      cost_tiled_kernel<<<grid, 256, 0, s>>>(job.cR[k], job.cL[k], W, H, D, Dp, cmax, 1, job.CR[k]);
+    }
     return cudaGetLastError();
   }
   cudaError_t e = cudaFuncSetAttribute(cost_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1010,7 +1026,7 @@ cudaError_t launch_cost_pair(const uint64_t* cL, const uint64_t* cR, int W, int 
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  cost_pair_kernel<<<std::min(H, sms), 1024, smem, s>>>(cL, cR, W, H, D, Dp, cmax, CL, CR);
+  cost_pair_kernel<<<std::min(job.npairs * H, sms), 1024, smem, s>>>(job, W, H, D, Dp, cmax);
   return cudaGetLastError();
 }
 
