@@ -362,6 +362,14 @@ def run_ours(args, world, rank, local):
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "sweep_shape": tuned["classes"] if tuned else "built-in",
     }
+    # KITTI-style accuracy of this frame's output against the scene's ground truth
+    from paper_1801_04720_gb300 import evaluate
+    step()
+    torch.cuda.synchronize()
+    result["accuracy_vs_ground_truth"] = {
+        "rule": "outlier: error > 3 px and > 5 % of the true value; rates over the kept pixels",
+        "plain": {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
+            out["s4"], out["valid"], q.gt_disp0, q.gt_disp1, q.gt_flow).items()}}
     if args.batch > 0:
         result["batch"] = run_batch(args, dev, _lib, synth, torch)
     if args.learned_eval >= 0:
@@ -489,6 +497,10 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
     gt = [torch.from_numpy(q.gt_disp0).to(dev)]
     frame_gt = {"plain_check": train_confnet.accuracy([plain["disp"]], gt),
                 "learned": train_confnet.accuracy([lo["disp"]], gt)}
+    from paper_1801_04720_gb300 import evaluate
+    step()
+    torch.cuda.synchronize()
+    sf_acc = evaluate.scene_flow_accuracy(out["s4"], out["valid"], q.gt_disp0, q.gt_disp1, q.gt_flow)
     res = {"metric": "scene-flow frames/s, learned confidence in place of the L-R check",
            "value": round(replica_rate(ms, world), 2), "unit": "frames/s", "ms_per_step": round(ms, 4),
            "vs_plain": round(replica_rate(ms, world) / plain_fps, 3), "threshold": thr,
@@ -498,7 +510,8 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
            "gpu_launches": int(launches), "stages_ms_per_step": stages,
            "automotive_frame": {k: round(v, 5) for k, v in frame_rates.items()},
            "automotive_frame_vs_ground_truth": {k: {kk: round(vv, 5) for kk, vv in v.items()}
-                                                for k, v in frame_gt.items()}}
+                                                for k, v in frame_gt.items()},
+           "scene_flow_accuracy_vs_ground_truth": {k: round(v, 5) for k, v in sf_acc.items()}}
     n_eval = min(args.learned_eval, len(train_confnet.EVAL_SEEDS))
     if n_eval > 0:
         # held-out scenes of both training recipes (never trained or calibrated on)
@@ -578,6 +591,16 @@ def run_stream(args, dev, _lib, torch, flush):
         gts.append(torch.from_numpy(frames[k].gt_disp0).to(dev))
     rates = train_confnet.rates(dec, thr)
     vs_gt = {"plain_check": train_confnet.accuracy(dp, gts), "learned": train_confnet.accuracy(dl, gts)}
+    # KITTI-style scene-flow accuracy of frame 0 on both paths
+    from paper_1801_04720_gb300 import evaluate
+    _lib.sf_scene_flow(dimgs[0], dflow[0], p, cam, ws=ws, out=out, stream=stream)
+    _lib.sf_scene_flow_learned_frames([(dimgs[0], dflow[0]), (dimgs[1], dflow[1])], p, cam, packed, thr,
+                                      ws=ws2, outs=outs2, stream=stream)
+    torch.cuda.synchronize()
+    f0 = frames[0]
+    sf_acc = {name: {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
+        o["s4"], o["valid"], f0.gt_disp0, f0.gt_disp1, f0.gt_flow).items()}
+        for name, o in (("plain", out), ("learned", outs2[0]))}
     N = W * H
     return {"workload": f"automotive stream {W}x{H} D={D}, 40 moving segments, {n} frames rendered",
             "plain": {"value": round(1000.0 / ms_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain, 3),
@@ -591,6 +614,7 @@ def run_stream(args, dev, _lib, torch, flush):
                                               "ms_per_step": round(ms_learned, 3)},
             "learned_vs_plain_check": {k: round(v, 5) for k, v in rates.items()},
             "vs_ground_truth": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in vs_gt.items()},
+            "scene_flow_accuracy_frame0": sf_acc,
             "parity": "frame 0 of this recipe against the oracle in tests/test_gpu_fullsize.py "
                       "(integers bit-exact); the oracle is not timed here"}
 
