@@ -4,21 +4,24 @@
 // which needs a second SGM pass with the right image as reference.  This
 // path predicts that check's outcome from the left pass alone:
 //
-//   1. features_kernel: seven channels per pixel of the left pass's
-//      aggregated cost curve S (best cost, margin to the best cost outside
-//      the winner's neighbourhood, curvature, disagreement of the three path
-//      groups, winner, distance to the left border, matching cost at the
-//      winner), each an integer over a power of two, stored as bfloat16
-//      [H][W][8].  The winner and its parabolic subpixel value come out of
-//      the same pass, computed exactly like the plain select.  Then
+//   1. features (features_staged_kernel for D a multiple of 32,
+//      features_px_kernel for other multiples of 8, features_vec_kernel /
+//      features_kernel otherwise): seven channels per pixel of the left
+//      pass's aggregated cost curve S (best cost, margin to the best cost
+//      outside the winner's neighbourhood, curvature, disagreement of the
+//      three path groups, winner, distance to the left border, matching cost
+//      at the winner), each an integer over a power of two, stored as
+//      bfloat16 [H][W][8].  The winner and its parabolic subpixel value come
+//      out of the same pass, computed exactly like the plain select.  Then
 //      visibility_kernel fills channel 7 from the winners of each row: the
 //      occlusion test that the left-right check performs, read off the left
 //      disparities alone.
 //   2. infer_kernel: a 4-layer 3x3 network (8 -> 32 -> 32 -> 32 -> 1, ReLU,
 //      sigmoid), bfloat16 weights and activations, fp32 accumulation on the
 //      5th-generation tensor cores: tcgen05.mma with operands in shared
-//      memory and accumulators in tensor memory, one elected thread issuing,
-//      all four layers of an output tile fused in shared memory.
+//      memory and accumulators in tensor memory, one warp issuing and eight
+//      draining the accumulators, all four layers of an output tile fused in
+//      shared memory, the tiles of every pass of a call in one launch.
 //   3. training kernels (fp32 CUDA cores): forward with the same bfloat16
 //      roundings, weighted binary cross-entropy, data and weight gradients,
 //      Adam.
