@@ -366,10 +366,15 @@ def run_ours(args, world, rank, local):
     from paper_1801_04720_gb300 import evaluate
     step()
     torch.cuda.synchronize()
+    s4_h, valid_h, flow_h = out["s4"].cpu(), out["valid"].cpu(), flow.cpu()
     result["accuracy_vs_ground_truth"] = {
         "rule": "outlier: error > 3 px and > 5 % of the true value; rates over the kept pixels",
         "plain": {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
-            out["s4"], out["valid"], q.gt_disp0, q.gt_disp1, q.gt_flow).items()}}
+            s4_h, valid_h, q.gt_disp0, q.gt_disp1, q.gt_flow).items()},
+        "plain_dense": {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy_dense(
+            s4_h, flow_h, q.gt_disp0, q.gt_disp1, q.gt_flow).items()},
+        "dense": "d0 and d1 filled by background interpolation (evaluate.fill_background), "
+                 "(u, v) from the input flow"}
     if args.batch > 0:
         result["batch"] = run_batch(args, dev, _lib, synth, torch)
     if args.learned_eval >= 0:
@@ -500,7 +505,8 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
     from paper_1801_04720_gb300 import evaluate
     step()
     torch.cuda.synchronize()
-    sf_acc = evaluate.scene_flow_accuracy(out["s4"], out["valid"], q.gt_disp0, q.gt_disp1, q.gt_flow)
+    sf_acc = evaluate.scene_flow_accuracy(out["s4"].cpu(), out["valid"].cpu(), q.gt_disp0, q.gt_disp1,
+                                          q.gt_flow)
     res = {"metric": "scene-flow frames/s, learned confidence in place of the L-R check",
            "value": round(replica_rate(ms, world), 2), "unit": "frames/s", "ms_per_step": round(ms, 4),
            "vs_plain": round(replica_rate(ms, world) / plain_fps, 3), "threshold": thr,
@@ -599,8 +605,10 @@ def run_stream(args, dev, _lib, torch, flush):
     torch.cuda.synchronize()
     f0 = frames[0]
     sf_acc = {name: {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
-        o["s4"], o["valid"], f0.gt_disp0, f0.gt_disp1, f0.gt_flow).items()}
+        o["s4"].cpu(), o["valid"].cpu(), f0.gt_disp0, f0.gt_disp1, f0.gt_flow).items()}
         for name, o in (("plain", out), ("learned", outs2[0]))}
+    sf_acc["plain_dense"] = {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy_dense(
+        out["s4"].cpu(), dflow[0].cpu(), f0.gt_disp0, f0.gt_disp1, f0.gt_flow).items()}
     N = W * H
     return {"workload": f"automotive stream {W}x{H} D={D}, 40 moving segments, {n} frames rendered",
             "plain": {"value": round(1000.0 / ms_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain, 3),

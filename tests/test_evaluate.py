@@ -72,3 +72,49 @@ def test_nothing_kept():
     s4, valid, gt0, gt1, gtf = _scene()
     r = ev.scene_flow_accuracy(s4, torch.zeros_like(valid), gt0, gt1, gtf)
     assert r == {"density": 0.0, "D1": 0.0, "D2": 0.0, "Fl": 0.0, "SF": 0.0}
+
+
+def test_fill_background_rows_hand_case():
+    nan = float("nan")
+    a = torch.tensor([[nan, 5.0, nan, nan, 9.0, 7.0, nan],
+                      [1.0, nan, 3.0, nan, nan, nan, nan]])
+    got = ev.fill_background(a)
+    # row 0: leading run takes 5; the run between 5 and 9 takes min = 5;
+    # the trailing run takes 7.  Row 1: 1 | min(1, 3) | 3 | trailing 3s
+    assert got.tolist() == [[5.0, 5.0, 5.0, 5.0, 9.0, 7.0, 7.0],
+                            [1.0, 1.0, 3.0, 3.0, 3.0, 3.0, 3.0]]
+
+
+def test_fill_background_empty_rows_take_columns():
+    nan = float("nan")
+    a = torch.tensor([[nan, nan, nan],
+                      [2.0, nan, 8.0],
+                      [nan, nan, nan],
+                      [6.0, 4.0, nan]])
+    got = ev.fill_background(a)
+    # rows 1 and 3 fill along the row first: [2, 2, 8] and [6, 4, 4]; rows 0
+    # and 2 have nothing and take their columns of that row-filled map: row 0
+    # from the row below, row 2 the smaller of its neighbours above and below
+    assert got[1].tolist() == [2.0, 2.0, 8.0]
+    assert got[3].tolist() == [6.0, 4.0, 4.0]
+    assert got[0].tolist() == [2.0, 2.0, 8.0]
+    assert got[2].tolist() == [2.0, 2.0, 4.0]
+
+
+def test_fill_background_all_missing_stays_missing():
+    a = torch.full((2, 3), float("nan"))
+    assert torch.isnan(ev.fill_background(a)).all()
+
+
+def test_dense_accuracy_uses_input_flow_and_filled_disparities():
+    s4, valid, gt0, gt1, gtf = _scene()
+    flow = gtf.clone()
+    s4[0, 1:4, :] = float("nan")          # a gap in row 0
+    s4[0, 0, 2] = 38.0                    # left neighbour of the gap (error 2 px)
+    r = ev.scene_flow_accuracy_dense(s4, flow, gt0, gt1, gtf)
+    assert r["density"] == 1.0
+    # the gap takes min(38, 40) = 38 for d0: errors of 2 px, not outliers
+    assert r["D1"] == 0.0 and r["SF"] == 0.0
+    s4[0, 0, 2] = 30.0                    # now the fill is 10 px off on 4 pixels
+    r = ev.scene_flow_accuracy_dense(s4, flow, gt0, gt1, gtf)
+    assert r["D1"] == pytest.approx(4 / 10)
