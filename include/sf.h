@@ -61,7 +61,19 @@ typedef enum {
  *                        where (rx, ry) is the step from p - r to p.
  *   D                  : number of disparities, 1..256 (values 0..D-1).
  *   subpixel           : 1 = parabolic refinement of the winner, 0 = off.
- *   lr_tol             : left-right tolerance in pixels, >= 0 (inclusive). */
+ *   lr_tol             : left-right tolerance in pixels, >= 0 (inclusive).
+ *   adaptive_p2        : 0 = constant P2; 1 = the intensity-adaptive P2 of the
+ *                        SGM the paper cites (Hirschmueller 2008): on the path
+ *                        step from q = p - r to p the penalty for a change of
+ *                        two or more disparities is P2 / |I(p) - I(q)|
+ *                        (integer division), never below P1, and P2 where
+ *                        I(p) = I(q); I is the pass's reference image.
+ *   uniqueness         : ratio in percent, 0..99 (0 = off).  A left winner d*
+ *                        is removed (it fails the left-right check) unless
+ *                        100 * S2 >= (100 + uniqueness) * S(d*), S2 the
+ *                        smallest S(d) over |d - d*| >= 2 (kept when there is
+ *                        no such d).  A post-filter of SGM implementations;
+ *                        the paper names SGM only. */
 typedef struct {
   int32_t census_w, census_h;
   uint16_t P1, P2;
@@ -69,6 +81,8 @@ typedef struct {
   int32_t D;
   int32_t subpixel;
   int32_t lr_tol;
+  int32_t adaptive_p2;
+  int32_t uniqueness;
 } sf_sgm_params;
 
 /* Pinhole stereo camera: focal length f (px), baseline B (m), principal point
@@ -78,7 +92,7 @@ typedef struct {
 } sf_camera;
 
 /* Fills p with census 9x7, P1 = 7, P2 = 86, all 8 paths, D = 128, subpixel on,
- * lr_tol = 1. */
+ * lr_tol = 1, constant P2, no uniqueness filter. */
 void sf_default_params(sf_sgm_params* p);
 
 /* Human-readable name of a status code (static storage). */
@@ -113,9 +127,21 @@ size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p)
  * cost: uint8 [H][W][D]; agg_out: uint16 [H][W][D].  With D % 16 == 0, a
  * 16-byte aligned cost volume and a workspace of at least
  * sf_aggregate_workspace_size() bytes the fused band sweeps run; otherwise
- * (workspace may then be NULL) one kernel per path. */
+ * (workspace may then be NULL) one kernel per path.  p->adaptive_p2 = 1 needs
+ * the reference image: it returns SF_ERR_INVALID_ARG here (use
+ * sf_sgm_aggregate_guided). */
 sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
                            uint16_t* agg_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* sf_sgm_aggregate with the reference image of the pass as a guide, for
+ * p->adaptive_p2 = 1 (Sec. 3.1's SGM with the cited paper's adaptive P2, see
+ * sf_sgm_params): guide is uint8 [H][pitch] (device), the image the cost
+ * volume was computed for (left image for the left-reference volume).  With
+ * adaptive_p2 = 0 the guide is ignored and the result is sf_sgm_aggregate's.
+ * Same workspace rules as sf_sgm_aggregate. */
+sf_status sf_sgm_aggregate_guided(const uint8_t* cost, const uint8_t* guide, int32_t pitch, int32_t W,
+                                  int32_t H, const sf_sgm_params* p, uint16_t* agg_out, void* workspace,
+                                  size_t ws_bytes, void* stream);
 
 /* Bytes of the scratch array built into the library for
  * sf_sgm_aggregate_noalloc (32 MiB per device). */
@@ -156,6 +182,9 @@ sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_s
  * (cudaGetSymbolAddress, with that device current; this may load the
  * library's device code).  Make that first call on each device before any
  * stream capture begins.  The current device must be the device of `stream`.
+ * Every later call made outside stream capture looks the address up again,
+ * so a device or context reset (which may move the array) is picked up;
+ * a call under capture uses the address of the last call made outside it.
  *
  * Concurrency: there is ONE scratch array per device and process.  Two calls
  * whose work overlaps on the GPU (different streams, or different host
@@ -333,6 +362,20 @@ void sf_batch_release_graphs(void);
  * for D, return SF_ERR_UNSUPPORTED; dc = 0 restores the built-in choice for
  * the class.  Process-wide; results are identical for every shape. */
 sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo);
+
+/* sf_set_sweep_shape with the scheduling order of the paths as well (no
+ * counterpart in the paper, which sums the eight paths of Sec. 3.1 in any
+ * order: the sum is exact).  order = 0: the horizontal paths, then the three
+ * downward paths (0,+1), (+1,+1), (-1,+1) in one launch walking the image top
+ * to bottom, then the three upward paths in a second launch walking bottom to
+ * top, which adds everything and selects.  order = 1: the horizontal paths,
+ * then both vertical scan orders in ONE launch, started from opposite ends of
+ * the image: each band of rows is finished (sums, winner, subpixel) by
+ * whichever order reaches it second, the other having left its partial sum,
+ * so twice as many band tasks are available at a time.  Integers are
+ * identical in every order and shape.  Other orders, or shapes the build
+ * does not provide, return SF_ERR_UNSUPPORTED. */
+sf_status sf_set_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order);
 
 /* ---- tracing and counters (host-side bookkeeping; no paper counterpart) --- */
 

@@ -12,7 +12,11 @@ paper it follows:
 * census / cost: the matching cost of SGM (Sec. 3.1 names SGM, citing
   Hirschmueller 2008); census window, P1, P2 and D are the method's parameters.
 * ``path_cost`` / ``aggregate``: the eight-path semi-global aggregation
-  (Sec. 3.1, "eight different paths").
+  (Sec. 3.1, "eight different paths"); with a guide image, the P2 of each
+  path step adapts to the intensity step as in the cited SGM (Hirschmueller
+  2008): P2 / |I(p) - I(p-r)| rounded down, never below P1.
+* ``uniqueness``: removes winners whose cost is not clearly below every
+  disparity two or more away (a post-filter of SGM implementations).
 * ``select``: winner-take-all with parabolic subpixel refinement.
 * ``lr_check``: the left-right consistency check that makes the disparity map
   non-dense (Sec. 3.1).
@@ -66,12 +70,16 @@ def _load():
             lib.oracle_census.argtypes = [P, i, i, i, i, P]
             lib.oracle_cost.argtypes = [P, P, i, i, i, i, i, P]
             lib.oracle_path.argtypes = [P, i, i, i, i, i, i, i, P]
+            lib.oracle_path_guided.argtypes = [P, P, i, i, i, i, i, i, i, P]
             lib.oracle_aggregate.argtypes = [P, i, i, i, i, i, ctypes.c_uint32, P, P]
+            lib.oracle_aggregate_guided.argtypes = [P, P, i, i, i, i, i, ctypes.c_uint32, P, P]
+            lib.oracle_uniqueness.argtypes = [P, i, i, i, i, P, P]
             lib.oracle_select.argtypes = [P, i, i, i, i, P, P]
             lib.oracle_lr_check.argtypes = [P, P, P, i, i, i, P, P]
             lib.oracle_combine.argtypes = [P, P, P, i, i, d, d, d, d, P, P, P, P]
             for fn in ("oracle_census", "oracle_cost", "oracle_path", "oracle_aggregate",
-                       "oracle_select", "oracle_lr_check", "oracle_combine"):
+                       "oracle_select", "oracle_lr_check", "oracle_combine", "oracle_path_guided",
+                       "oracle_aggregate_guided", "oracle_uniqueness"):
                 getattr(lib, fn).restype = None
             _lib = lib
     return _lib
@@ -102,23 +110,46 @@ def cost_volume(c_ref: np.ndarray, c_other: np.ndarray, D: int, ref_is_right: bo
     return out
 
 
-def path_cost(cost: np.ndarray, P1: int, P2: int, r: tuple[int, int]) -> np.ndarray:
-    """L_r for one traversal direction r = (rx, ry), int32 [H][W][D]."""
+def _guide(img, H, W):
+    if img is None:
+        return None, None
+    g = np.ascontiguousarray(img, dtype=np.uint8)
+    assert g.shape == (H, W)
+    return g, _ptr(g)
+
+
+def path_cost(cost: np.ndarray, P1: int, P2: int, r: tuple[int, int], img=None) -> np.ndarray:
+    """L_r for one traversal direction r = (rx, ry), int32 [H][W][D].  With a
+    guide image (uint8 [H][W]) the P2 of each step is intensity-adaptive."""
     cost = np.ascontiguousarray(cost, dtype=np.uint8)
     H, W, D = cost.shape
     out = np.empty((H, W, D), dtype=np.int32)
-    _load().oracle_path(_ptr(cost), W, H, D, P1, P2, r[0], r[1], _ptr(out))
+    g, gp = _guide(img, H, W)
+    _load().oracle_path_guided(_ptr(cost), gp, W, H, D, P1, P2, r[0], r[1], _ptr(out))
     return out
 
 
-def aggregate(cost: np.ndarray, P1: int, P2: int, path_mask: int = 0xFF) -> np.ndarray:
+def aggregate(cost: np.ndarray, P1: int, P2: int, path_mask: int = 0xFF, img=None) -> np.ndarray:
     """S = sum of L_r over the enabled paths, int32 [H][W][D]."""
     cost = np.ascontiguousarray(cost, dtype=np.uint8)
     H, W, D = cost.shape
     S = np.empty((H, W, D), dtype=np.int32)
     scratch = np.empty((H, W, D), dtype=np.int32)
-    _load().oracle_aggregate(_ptr(cost), W, H, D, P1, P2, path_mask & 0xFF, _ptr(S), _ptr(scratch))
+    g, gp = _guide(img, H, W)
+    _load().oracle_aggregate_guided(_ptr(cost), gp, W, H, D, P1, P2, path_mask & 0xFF, _ptr(S),
+                                    _ptr(scratch))
     return S
+
+
+def uniqueness(S: np.ndarray, dint: np.ndarray, dsub: np.ndarray, ratio: int) -> np.ndarray:
+    """Copy of dsub with NaN where the winner is not unique:
+    100 * min_{|d - d*| >= 2} S(d) < (100 + ratio) * S(d*)."""
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    H, W, D = S.shape
+    dint = np.ascontiguousarray(dint, dtype=np.int16)
+    out = np.array(dsub, dtype=np.float64, copy=True, order="C")
+    _load().oracle_uniqueness(_ptr(S), W, H, D, int(ratio), _ptr(dint), _ptr(out))
+    return out
 
 
 def select(S: np.ndarray, subpixel: bool = True):
@@ -160,25 +191,37 @@ def combine(D0: np.ndarray, D1: np.ndarray, flow: np.ndarray, f: float, B: float
 
 
 def sgm_pass(ref_census: np.ndarray, other_census: np.ndarray, D: int, P1: int, P2: int,
-             ref_is_right: bool, cmax: int, path_mask: int = 0xFF, subpixel: bool = True):
-    """One SGM pass: cost, aggregation, selection.  Returns (dint, dsub)."""
+             ref_is_right: bool, cmax: int, path_mask: int = 0xFF, subpixel: bool = True,
+             guide=None, unique: int = 0):
+    """One SGM pass: cost, aggregation (intensity-adaptive P2 when `guide`,
+    the pass's reference image, is given), selection, and the uniqueness
+    filter when unique > 0.  Returns (dint, dsub)."""
     C = cost_volume(ref_census, other_census, D, ref_is_right, cmax)
-    S = aggregate(C, P1, P2, path_mask)
-    return select(S, subpixel)
+    S = aggregate(C, P1, P2, path_mask, img=guide)
+    dint, dsub = select(S, subpixel)
+    if unique:
+        dsub = uniqueness(S, dint, dsub, unique)
+    return dint, dsub
 
 
 def disparity(left: np.ndarray, right: np.ndarray, D: int = 128, P1: int = 7, P2: int = 86,
               cw: int = 9, ch: int = 7, tol: int = 1, path_mask: int = 0xFF,
-              subpixel: bool = True):
+              subpixel: bool = True, adaptive_p2: bool = False, uniqueness: int = 0):
     """Full SGM disparity for one stereo pair with the left-right check.
+
+    adaptive_p2: each pass adapts P2 to its reference image's intensity
+    steps.  uniqueness: ratio in percent of the filter on the left winners
+    (0 = off); a removed winner fails the check.
 
     Returns a dict with dL, dR (int16), dL_sub (float64), valid (uint8) and
     disp (float64, NaN where the check failed)."""
     cmax = cw * ch - 1
     cL = census(left, cw, ch)
     cR = census(right, cw, ch)
-    dL, dL_sub = sgm_pass(cL, cR, D, P1, P2, False, cmax, path_mask, subpixel)
-    dR, _ = sgm_pass(cR, cL, D, P1, P2, True, cmax, path_mask, subpixel)
+    dL, dL_sub = sgm_pass(cL, cR, D, P1, P2, False, cmax, path_mask, subpixel,
+                          guide=left if adaptive_p2 else None, unique=uniqueness)
+    dR, _ = sgm_pass(cR, cL, D, P1, P2, True, cmax, path_mask, subpixel,
+                     guide=right if adaptive_p2 else None)
     valid, disp = lr_check(dL, dR, dL_sub, tol)
     return {"dL": dL, "dR": dR, "dL_sub": dL_sub, "valid": valid, "disp": disp}
 

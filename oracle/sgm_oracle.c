@@ -91,14 +91,29 @@ void oracle_cost(const uint64_t* c_ref, const uint64_t* c_other, int W, int H, i
   }
 }
 
+/* Penalty for a disparity change of two or more on the path step from
+ * q = p - r to p.  Constant P2 unless `img` (the reference image of the pass,
+ * uint8 [H][W]) is given: then the cited SGM (Hirschmueller 2008, cited in
+ * Sec. 3.1) adapts it to the intensity step, P2 / |I(p) - I(q)| rounded down
+ * and never below P1, keeping P2 where the intensities are equal. */
+static int step_penalty(const uint8_t* img, int W, int x, int y, int qx, int qy, int P1, int P2) {
+  if (!img) return P2;
+  int g = (int)img[y * W + x] - (int)img[qy * W + qx];
+  if (g < 0) g = -g;
+  if (g == 0) return P2;
+  int v = P2 / g;
+  return v < P1 ? P1 : v;
+}
+
 /* One SGM path r = (rx, ry) (Sec. 3.1: eight paths radiate from each pixel).
  * L_r(p,d) = C(p,d) + min( L_r(p-r,d), L_r(p-r,d-1)+P1, L_r(p-r,d+1)+P1,
  *                          min_k L_r(p-r,k)+P2 ) - min_k L_r(p-r,k),
  * and L_r(p,d) = C(p,d) where p-r lies outside the image.  The d-1 / d+1
  * terms are left out at d = 0 and d = D-1.  Pixels are visited in an order
- * in which p-r always comes before p. */
-void oracle_path(const uint8_t* cost, int W, int H, int D, int P1, int P2, int rx, int ry,
-                 int32_t* L) {
+ * in which p-r always comes before p.  With a guide image `img` (may be NULL)
+ * the P2 of each step is step_penalty()'s. */
+void oracle_path_guided(const uint8_t* cost, const uint8_t* img, int W, int H, int D, int P1, int P2,
+                        int rx, int ry, int32_t* L) {
   int y_first = (ry >= 0) ? 0 : H - 1, y_step = (ry >= 0) ? 1 : -1;
   int x_first = (rx >= 0) ? 0 : W - 1, x_step = (rx >= 0) ? 1 : -1;
   for (int iy = 0, y = y_first; iy < H; iy++, y += y_step) {
@@ -114,15 +129,22 @@ void oracle_path(const uint8_t* cost, int W, int H, int D, int P1, int P2, int r
       int32_t prev_min = prev[0];
       for (int k = 1; k < D; k++)
         if (prev[k] < prev_min) prev_min = prev[k];
+      const int p2 = step_penalty(img, W, x, y, qx, qy, P1, P2);
       for (int d = 0; d < D; d++) {
         int32_t best = prev[d];
         if (d > 0 && prev[d - 1] + P1 < best) best = prev[d - 1] + P1;
         if (d < D - 1 && prev[d + 1] + P1 < best) best = prev[d + 1] + P1;
-        if (prev_min + P2 < best) best = prev_min + P2;
+        if (prev_min + p2 < best) best = prev_min + p2;
         out[d] = c[d] + best - prev_min;
       }
     }
   }
+}
+
+/* The path with constant penalties. */
+void oracle_path(const uint8_t* cost, int W, int H, int D, int P1, int P2, int rx, int ry,
+                 int32_t* L) {
+  oracle_path_guided(cost, NULL, W, H, D, P1, P2, rx, ry, L);
 }
 
 /* The eight traversal directions, in the order of the path-mask bits. */
@@ -135,16 +157,22 @@ void oracle_direction(int index, int* rx, int* ry) {
 }
 
 /* Aggregated cost S(p,d) = sum over the enabled paths r of L_r(p,d).
- * scratch holds one int32 [H][W][D] path buffer. */
-void oracle_aggregate(const uint8_t* cost, int W, int H, int D, int P1, int P2,
-                      uint32_t path_mask, int32_t* S, int32_t* scratch) {
+ * scratch holds one int32 [H][W][D] path buffer.  img: guide image for the
+ * adaptive P2 of every path, or NULL for constant P2. */
+void oracle_aggregate_guided(const uint8_t* cost, const uint8_t* img, int W, int H, int D, int P1,
+                             int P2, uint32_t path_mask, int32_t* S, int32_t* scratch) {
   size_t n = (size_t)W * H * D;
   for (size_t i = 0; i < n; i++) S[i] = 0;
   for (int r = 0; r < 8; r++) {
     if (!((path_mask >> r) & 1u)) continue;
-    oracle_path(cost, W, H, D, P1, P2, kDirX[r], kDirY[r], scratch);
+    oracle_path_guided(cost, img, W, H, D, P1, P2, kDirX[r], kDirY[r], scratch);
     for (size_t i = 0; i < n; i++) S[i] += scratch[i];
   }
+}
+
+void oracle_aggregate(const uint8_t* cost, int W, int H, int D, int P1, int P2,
+                      uint32_t path_mask, int32_t* S, int32_t* scratch) {
+  oracle_aggregate_guided(cost, NULL, W, H, D, P1, P2, path_mask, S, scratch);
 }
 
 /* Winner-take-all with parabolic subpixel refinement.  d* is the smallest d
@@ -170,10 +198,33 @@ void oracle_select(const int32_t* S, int W, int H, int D, int subpixel, int16_t*
   }
 }
 
+/* Uniqueness filter on the winners of oracle_select (a post-filter of SGM
+ * implementations; the paper only names SGM, Sec. 3.1).  With S0 = S(d*)
+ * and S2 the smallest S(d) over |d - d*| >= 2, the winner is unique iff
+ * 100 * S2 >= (100 + ratio) * S0 (percent; ratio = 0 keeps every winner,
+ * and so does a curve with no d two away from d*).  Removed winners get a
+ * NaN subpixel value; dint is left as it is. */
+void oracle_uniqueness(const int32_t* S, int W, int H, int D, int ratio, const int16_t* dint,
+                       double* dsub) {
+  for (int i = 0; i < W * H; i++) {
+    const int32_t* s = S + (size_t)i * D;
+    int best = dint[i];
+    int found = 0;
+    int32_t s2 = 0;
+    for (int d = 0; d < D; d++) {
+      if (d >= best - 1 && d <= best + 1) continue;
+      if (!found || s[d] < s2) s2 = s[d];
+      found = 1;
+    }
+    if (found && 100 * (int64_t)s2 < (int64_t)(100 + ratio) * s[best]) dsub[i] = NAN;
+  }
+}
+
 /* Left-right consistency check (Sec. 3.1): the left disparity at x is kept
  * iff x - dL >= 0 and |dL(x,y) - dR(x-dL(x,y), y)| <= tol on the integer
- * winner-take-all values.  Kept pixels carry the subpixel left value, the
- * others NaN; valid is 1 / 0. */
+ * winner-take-all values, and the left winner was not removed before the
+ * check (a NaN subpixel value: the uniqueness filter).  Kept pixels carry
+ * the subpixel left value, the others NaN; valid is 1 / 0. */
 void oracle_lr_check(const int16_t* dL, const int16_t* dR, const double* dL_sub, int W, int H,
                      int tol, uint8_t* valid, double* disp) {
   for (int y = 0; y < H; y++) {
@@ -182,7 +233,7 @@ void oracle_lr_check(const int16_t* dL, const int16_t* dR, const double* dL_sub,
       int dl = dL[i];
       int ok = 0;
       int xr = x - dl;
-      if (xr >= 0) {
+      if (xr >= 0 && !isnan(dL_sub[i])) {
         int diff = dl - (int)dR[y * W + xr];
         if (diff < 0) diff = -diff;
         ok = diff <= tol;

@@ -29,6 +29,7 @@ EXPORTED = [
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
     "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
     "sf_batch_workspace_size", "sf_batch_run", "sf_batch_release_graphs", "sf_set_sweep_shape",
+    "sf_set_sweep_schedule", "sf_sgm_aggregate_guided",
     "sf_sgm_aggregate_noalloc", "sf_confnet_param_count", "sf_confnet_packed_bytes",
     "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
     "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
@@ -57,7 +58,8 @@ class SFError(RuntimeError):
 class SgmParams(ctypes.Structure):
     _fields_ = [("census_w", ctypes.c_int32), ("census_h", ctypes.c_int32),
                 ("P1", ctypes.c_uint16), ("P2", ctypes.c_uint16), ("path_mask", ctypes.c_uint32),
-                ("D", ctypes.c_int32), ("subpixel", ctypes.c_int32), ("lr_tol", ctypes.c_int32)]
+                ("D", ctypes.c_int32), ("subpixel", ctypes.c_int32), ("lr_tol", ctypes.c_int32),
+                ("adaptive_p2", ctypes.c_int32), ("uniqueness", ctypes.c_int32)]
 
 
 class Camera(ctypes.Structure):
@@ -84,8 +86,10 @@ def hparams(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, w_neg=1.0, step=1):
     return ConfnetHparams(lr, beta1, beta2, eps, w_neg, step)
 
 
-def params(D=128, P1=7, P2=86, census_w=9, census_h=7, path_mask=0xFF, subpixel=True, lr_tol=1):
-    return SgmParams(census_w, census_h, P1, P2, path_mask, D, int(subpixel), lr_tol)
+def params(D=128, P1=7, P2=86, census_w=9, census_h=7, path_mask=0xFF, subpixel=True, lr_tol=1,
+           adaptive_p2=False, uniqueness=0):
+    return SgmParams(census_w, census_h, P1, P2, path_mask, D, int(subpixel), lr_tol, int(adaptive_p2),
+                     int(uniqueness))
 
 
 def camera(f, B, cx, cy):
@@ -140,6 +144,8 @@ def load(path: str = LIB_PATH):
             "sf_batch_run": (i32, [P, i32, PP, ctypes.c_uint32, P, sz, P]),
             "sf_batch_release_graphs": (None, []),
             "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
+            "sf_set_sweep_schedule": (i32, [i32, i32, i32, i32, i32]),
+            "sf_sgm_aggregate_guided": (i32, [P, P, i32, i32, i32, PP, P, P, sz, P]),
             "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
             "sf_debug_set": (i32, [i32, ctypes.c_int64]),
             "sf_scene_flow_learned_frames": (i32, [P, i32, i32, i32, i32, PP, PC, P, ctypes.c_float, P, sz,
@@ -238,6 +244,26 @@ def sf_sgm_aggregate(cost, p: SgmParams, out=None, ws="auto", stream=None):
     nbytes = ws.numel() if ws is not None else 0
     _check("sf_sgm_aggregate", load().sf_sgm_aggregate(_ptr(cost), W, H, ctypes.byref(p), _ptr(out),
                                                        _ptr(ws), nbytes, _stream(stream)))
+    return out
+
+
+def sf_sgm_aggregate_guided(cost, guide, p: SgmParams, out=None, ws="auto", stream=None):
+    """sf_sgm_aggregate with the pass's reference image (uint8 [H][W]) as the
+    guide of the intensity-adaptive P2."""
+    _dev(cost, torch.uint8, "cost")
+    _dev(guide, torch.uint8, "guide")
+    H, W, D = cost.shape
+    if D != p.D or tuple(guide.shape) != (H, W):
+        raise ValueError("cost volume depth must equal p.D and the guide be [H][W]")
+    if out is None:
+        out = torch.empty((H, W, D), dtype=torch.int16, device=cost.device)
+    if isinstance(ws, str):
+        n = sf_aggregate_workspace_size(W, H, p)
+        ws = torch.empty(n, dtype=torch.uint8, device=cost.device) if n else None
+    nbytes = ws.numel() if ws is not None else 0
+    _check("sf_sgm_aggregate_guided",
+           load().sf_sgm_aggregate_guided(_ptr(cost), _ptr(guide), guide.stride(0), W, H, ctypes.byref(p),
+                                          _ptr(out), _ptr(ws), nbytes, _stream(stream)))
     return out
 
 
@@ -517,6 +543,10 @@ def sf_batch_release_graphs():
 
 def sf_set_sweep_shape(d_lo, d_hi, dc, halo):
     _check("sf_set_sweep_shape", load().sf_set_sweep_shape(d_lo, d_hi, dc, halo))
+
+
+def sf_set_sweep_schedule(d_lo, d_hi, dc, halo, order):
+    _check("sf_set_sweep_schedule", load().sf_set_sweep_schedule(d_lo, d_hi, dc, halo, order))
 
 
 # ---- learned confidence ------------------------------------------------------

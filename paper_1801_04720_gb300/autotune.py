@@ -1,11 +1,13 @@
-"""Autotuner for the band-sweep kernel shape.
+"""Autotuner for the band sweeps: kernel shape and path-scheduling order.
 
-For each class of disparity counts it times every sweep shape the library
-provides (disparities per thread dc, halo width) on a synthetic quadruple of
-the requested size through sf_scene_flow, keeps the fastest, and stores the
-choice in a JSON cache keyed by GPU name and size.  ``apply`` installs a cached
-choice with sf_set_sweep_shape.  Every shape computes identical integers; only
-the speed differs."""
+For each class of disparity counts it times every candidate (disparities per
+thread dc, halo width, and the scheduling order of the paths: 0 = down sweep
+then up sweep in two launches, 1 = both scan orders in one launch meeting in
+the middle) on a synthetic quadruple of the requested size through
+sf_scene_flow, keeps the fastest, and stores the choice in a JSON cache keyed
+by GPU name and size.  ``apply`` installs a cached choice with
+sf_set_sweep_schedule.  Every candidate computes identical integers; only the
+speed differs."""
 from __future__ import annotations
 
 import json
@@ -17,7 +19,9 @@ import torch
 
 from . import _lib, synth
 
-CANDIDATES = [(8, 16), (8, 8), (16, 8), (16, 16)]
+# (dc, halo, order)
+CANDIDATES = [(8, 16, 0), (8, 8, 0), (16, 8, 0), (16, 16, 0),
+              (16, 8, 1), (16, 16, 1), (8, 8, 1), (8, 16, 1)]
 DEFAULT_CLASSES = [(1, 32), (33, 64), (65, 128), (129, 256)]
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
@@ -57,20 +61,20 @@ def tune(W=1242, H=375, classes=DEFAULT_CLASSES, steps=20, warmup=3, cache=CACHE
         q = synth.fronto_planes(W=W, H=H, D=D, disparities=(2, max(3, D // 3), max(4, D - 5)),
                                 seed=seed)
         timings = {}
-        for dc, halo in CANDIDATES:
+        for dc, halo, order in CANDIDATES:
             try:
-                _lib.sf_set_sweep_shape(lo, hi, dc, halo)
+                _lib.sf_set_sweep_schedule(lo, hi, dc, halo, order)
             except _lib.SFError:
                 continue
             try:
-                timings[f"{dc}x{halo}"] = _time_scene_flow(q, D, steps, warmup)
+                timings[f"{dc}x{halo}o{order}"] = _time_scene_flow(q, D, steps, warmup)
             finally:
                 _lib.sf_set_sweep_shape(lo, hi, 0, 0)
         if not timings:
             continue
         best = min(timings, key=timings.get)
-        dc, halo = (int(v) for v in best.split("x"))
-        result["classes"].append({"lo": lo, "hi": hi, "dc": dc, "halo": halo,
+        dc, halo, order = parse_key(best)
+        result["classes"].append({"lo": lo, "hi": hi, "dc": dc, "halo": halo, "order": order,
                                   "ms": round(timings[best], 4),
                                   "candidates_ms": {k: round(v, 4) for k, v in timings.items()}})
     if cache:
@@ -80,11 +84,18 @@ def tune(W=1242, H=375, classes=DEFAULT_CLASSES, steps=20, warmup=3, cache=CACHE
     return result
 
 
+def parse_key(key):
+    """'16x8o1' -> (16, 8, 1)."""
+    shape, order = key.split("o")
+    dc, halo = (int(v) for v in shape.split("x"))
+    return dc, halo, int(order)
+
+
 def apply(result):
-    """Installs the shapes of a tune() result; returns how many were set."""
+    """Installs the choices of a tune() result; returns how many were set."""
     n = 0
     for c in result.get("classes", []):
-        _lib.sf_set_sweep_shape(c["lo"], c["hi"], c["dc"], c["halo"])
+        _lib.sf_set_sweep_schedule(c["lo"], c["hi"], c["dc"], c["halo"], c.get("order", 0))
         n += 1
     return n
 
@@ -96,15 +107,21 @@ def cached(cache, gpu, W, H):
             res = json.load(f)
     except (OSError, ValueError):
         return None
-    if res.get("gpu") == gpu and res.get("W") == W and res.get("H") == H:
+    if res.get("gpu") == gpu and res.get("W") == W and res.get("H") == H and \
+            all("order" in c for c in res.get("classes", [])):
         return res
     return None
 
 
-def load_or_tune(W=1242, H=375, cache=CACHE, **kw):
-    """Uses the cached choice for this GPU and size, tuning when there is none."""
+def load_or_tune(W=1242, H=375, cache=CACHE, classes=DEFAULT_CLASSES, **kw):
+    """Uses the cached choice for this GPU and size, tuning when there is none
+    (or when the cache lacks one of the requested classes)."""
     res = cached(cache, torch.cuda.get_device_name(), W, H)
+    if res is not None:
+        have = {(c["lo"], c["hi"]) for c in res["classes"]}
+        if not all(tuple(c) in have for c in classes):
+            res = None
     if res is None:
-        res = tune(W=W, H=H, cache=cache, **kw)
+        res = tune(W=W, H=H, cache=cache, classes=classes, **kw)
     apply(res)
     return res

@@ -3,6 +3,9 @@
 // disparities [l*K, l*K + K).  The min over d of the previous step comes from
 // a warp-wide redux; the d-1 / d+1 neighbours at lane boundaries from
 // shuffles.  Directions run one after another, each adding its L_r into S.
+// With a guide image the P2 of each step adapts to the intensity step, as in
+// the SGM the paper cites: P2 / |I(p) - I(p-r)| rounded down, at least P1,
+// P2 itself where the intensities are equal.
 #include "sf_internal.cuh"
 
 namespace sf {
@@ -13,8 +16,9 @@ constexpr uint32_t kInf = 0x3fffffffu;
 
 template <int K>
 __global__ void __launch_bounds__(256)
-    aggregate_direction_kernel(const uint8_t* __restrict__ cost, int W, int H, int D, int P1, int P2,
-                               int rx, int ry, uint16_t* __restrict__ S, int accumulate) {
+    aggregate_direction_kernel(const uint8_t* __restrict__ cost, const uint8_t* __restrict__ guide,
+                               int gpitch, int W, int H, int D, int P1, int P2, int rx, int ry,
+                               uint16_t* __restrict__ S, int accumulate) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int nlines = (rx == 0) ? W : (ry == 0) ? H : W + H - 1;
@@ -54,7 +58,12 @@ __global__ void __launch_bounds__(256)
       uint32_t right = __shfl_down_sync(kFullMask, L[0], 1);
       if (lane == 0) left = kInf;
       if (lane == 31) right = kInf;
-      const uint32_t q = prev_min + (uint32_t)P2;
+      int p2 = P2;
+      if (guide) {
+        const int step = abs((int)guide[(size_t)y * gpitch + x] - (int)guide[(size_t)(y - ry) * gpitch + (x - rx)]);
+        if (step > 0) p2 = max(P1, P2 / step);
+      }
+      const uint32_t q = prev_min + (uint32_t)p2;
       uint32_t nl[K];
 #pragma unroll
       for (int k = 0; k < K; k++) {
@@ -86,7 +95,8 @@ __global__ void __launch_bounds__(256)
 }  // namespace
 
 cudaError_t launch_aggregate(const uint8_t* cost, int W, int H, int D, int P1, int P2,
-                             uint32_t path_mask, uint16_t* S, cudaStream_t s) {
+                             uint32_t path_mask, uint16_t* S, cudaStream_t s, const uint8_t* guide,
+                             int gpitch) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   if ((path_mask & 0xffu) == 0) return cudaMemsetAsync(S, 0, sizeof(uint16_t) * W * H * D, s);
   int accumulate = 0;
@@ -97,13 +107,17 @@ cudaError_t launch_aggregate(const uint8_t* cost, int W, int H, int D, int P1, i
     const int threads = 256, warps_per_block = threads / 32;
     const int blocks = (nlines + warps_per_block - 1) / warps_per_block;
     if (D <= 32)
-      aggregate_direction_kernel<1><<<blocks, threads, 0, s>>>(cost, W, H, D, P1, P2, rx, ry, S, accumulate);
+      aggregate_direction_kernel<1><<<blocks, threads, 0, s>>>(cost, guide, gpitch, W, H, D, P1, P2, rx, ry, S,
+                                                                accumulate);
     else if (D <= 64)
-      aggregate_direction_kernel<2><<<blocks, threads, 0, s>>>(cost, W, H, D, P1, P2, rx, ry, S, accumulate);
+      aggregate_direction_kernel<2><<<blocks, threads, 0, s>>>(cost, guide, gpitch, W, H, D, P1, P2, rx, ry, S,
+                                                                accumulate);
     else if (D <= 128)
-      aggregate_direction_kernel<4><<<blocks, threads, 0, s>>>(cost, W, H, D, P1, P2, rx, ry, S, accumulate);
+      aggregate_direction_kernel<4><<<blocks, threads, 0, s>>>(cost, guide, gpitch, W, H, D, P1, P2, rx, ry, S,
+                                                                accumulate);
     else
-      aggregate_direction_kernel<8><<<blocks, threads, 0, s>>>(cost, W, H, D, P1, P2, rx, ry, S, accumulate);
+      aggregate_direction_kernel<8><<<blocks, threads, 0, s>>>(cost, guide, gpitch, W, H, D, P1, P2, rx, ry, S,
+                                                                accumulate);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -87,6 +87,8 @@ sf_status check_params(const sf_sgm_params* p, int32_t W, int32_t H) {
   if (p->path_mask & ~0xffu) return SF_ERR_INVALID_ARG;
   if (p->subpixel != 0 && p->subpixel != 1) return SF_ERR_INVALID_ARG;
   if (p->lr_tol < 0) return SF_ERR_INVALID_ARG;
+  if (p->adaptive_p2 != 0 && p->adaptive_p2 != 1) return SF_ERR_INVALID_ARG;
+  if (p->uniqueness < 0 || p->uniqueness > 99) return SF_ERR_INVALID_ARG;
   return SF_OK;
 }
 
@@ -135,13 +137,16 @@ sf_status sgm_full_impl(const uint8_t* left, const uint8_t* right, int W, int H,
   int16_t* dR = dR_out ? dR_out : reinterpret_cast<int16_t*>(ws + lay.dR);
   float* dsub = reinterpret_cast<float*>(ws + lay.dsub);
   uint8_t* valid = valid_out;
-  // left image as reference
+  // left image as reference (the guide of the adaptive P2 is the pass's
+  // reference image; the uniqueness filter applies to the left winners)
   SF_TRY_CUDA(launch_cost_volume(left, right, W, H, pitch, p->census_w, p->census_h, p->D, 0, cost, s));
-  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg, s));
-  SF_TRY_CUDA(launch_select(agg, W, H, p->D, p->subpixel, dL, dsub, s));
+  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg, s,
+                               p->adaptive_p2 ? left : nullptr, pitch));
+  SF_TRY_CUDA(launch_select(agg, W, H, p->D, p->subpixel, dL, dsub, s, p->uniqueness));
   // right image as reference
   SF_TRY_CUDA(launch_cost_volume(right, left, W, H, pitch, p->census_w, p->census_h, p->D, 1, cost, s));
-  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg, s));
+  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg, s,
+                               p->adaptive_p2 ? right : nullptr, pitch));
   SF_TRY_CUDA(launch_select(agg, W, H, p->D, 0, dR, nullptr, s));
   if (!valid) valid = reinterpret_cast<uint8_t*>(ws + lay.cost);  // cost is dead by now
   SF_TRY_CUDA(launch_lr_check(dL, dR, dsub, W, H, p->lr_tol, valid, disp_out, s));
@@ -258,19 +263,22 @@ fused::PassDesc pass_desc(uint8_t* ws, const FusedPlan& plan, const PairBuffers&
   d.dint = reinterpret_cast<int16_t*>(ws + pb.dint);
   d.dsub = nullptr;
   d.S = nullptr;
+  d.guide = nullptr;
+  d.gpitch = 0;
   (void)plan;
   return d;
 }
 
 // Task tables of a set of passes with one kernel shape: passes sorted by band
-// count (descending); band-major task order.  Written to `tab` (host ints):
+// count (descending); step-major task order (a merged launch lists each step's
+// tasks twice, down sweep then up sweep).  Written to `tab` (host ints):
 // [band_start (nb+1)] [band_npass (nb)] [prefixJ (npass+1)] [hline block prefix (npass+1)].
 struct TaskTables {
   std::vector<int> ints;
   int nbands = 0, ntasks = 0, nblocks = 0, off_band_start = 0, off_band_npass = 0, off_prefixJ = 0,
       off_hblocks = 0;
 };
-TaskTables build_tables(const fused::PassDesc* d, int npass) {
+TaskTables build_tables(const fused::PassDesc* d, int npass, bool merged) {
   TaskTables t;
   int nb_max = 0;
   for (int k = 0; k < npass; k++) nb_max = std::max(nb_max, d[k].nb);
@@ -288,7 +296,7 @@ TaskTables build_tables(const fused::PassDesc* d, int npass) {
     while (active < npass && d[active].nb > b) active++;
     t.ints[t.off_band_start + b] = task;
     t.ints[t.off_band_npass + b] = active;
-    task += prefixJ[active];
+    task += (merged ? 2 : 1) * prefixJ[active];
   }
   t.ints[t.off_band_start + nb_max] = task;
   t.ntasks = task;
@@ -310,6 +318,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
                      const int* tab_dev, const TaskTables* tt, int* counters, int* err,
                      cudaStream_t s, bool tuned = true) {
   const bool inl = d_dev_down == nullptr;
+  const bool merged = fused::shape_for(Dshape, tuned).order == 1;
   fused::HLineArgs ha{};
   ha.P1 = p->P1; ha.P2 = p->P2; ha.Dmax = Dshape; ha.npass = npass; ha.path_mask = p->path_mask;
   ha.builtin_shape = tuned ? 0 : 1;
@@ -317,6 +326,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
   fused::SweepArgs sa{};
   sa.builtin_shape = tuned ? 0 : 1;
   sa.P1 = p->P1; sa.P2 = p->P2; sa.subpixel = p->subpixel; sa.Dmax = Dshape; sa.npass = npass;
+  sa.unique = p->uniqueness;
   sa.path_mask = p->path_mask;
   sa.en_h0 = (p->path_mask >> 0) & 1u;
   sa.en_h1 = (p->path_mask >> 1) & 1u;
@@ -327,7 +337,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     ha.uniform_blocks = 2 * ((d[0].H + 15) / 16);
     ha.nblocks = npass * ha.uniform_blocks;
     sa.uniform_items = npass * d[0].J;
-    sa.ntasks = d[0].nb * sa.uniform_items;
+    sa.ntasks = (merged ? 2 : 1) * d[0].nb * sa.uniform_items;
     sa.nbands = d[0].nb;
   } else {
     ha.pass_ptr = d_dev_down;
@@ -347,14 +357,25 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     skip_host = skip;
     SF_TRY_CUDA(cudaMemcpyAsync(counters, &skip_host, sizeof(int), cudaMemcpyHostToDevice, s));
   }
-  SF_TRY_CUDA(fused::launch_sweep(sa, false, s));
+  if (merged) {
+    // both scan orders in one launch; every task may select, so all use the
+    // descriptors that carry the outputs
+    if (inl) {
+      for (int k = 0; k < npass; k++) sa.inl[k] = d[k];
+    } else {
+      sa.pass_ptr = d_dev_up;
+    }
+    SF_TRY_CUDA(fused::launch_sweep(sa, 2, s));
+    return SF_OK;
+  }
+  SF_TRY_CUDA(fused::launch_sweep(sa, 0, s));
   if (inl) {
     for (int k = 0; k < npass; k++) sa.inl[k] = d[k];   // with outputs of the up sweep
   } else {
     sa.pass_ptr = d_dev_up;
   }
   sa.task_counter = counters + 1;
-  SF_TRY_CUDA(fused::launch_sweep(sa, true, s));
+  SF_TRY_CUDA(fused::launch_sweep(sa, 1, s));
   return SF_OK;
 }
 
@@ -401,6 +422,10 @@ sf_status run_fused_pairs(const uint8_t* const* left, const uint8_t* const* righ
     for (int r = 0; r < 2; r++) {
       fused::PassDesc& pd = d[2 * k + r];
       pd = pass_desc(ws, plan, plan.pairs[k], r, W, H, p->D, p->D, nullptr);
+      if (p->adaptive_p2) {
+        pd.guide = r == 0 ? left[k] : right[k];
+        pd.gpitch = pitch;
+      }
       int16_t* const* user = r == 0 ? dL_out : dR_out;
       if (user && user[k]) pd.dint = user[k];
       if (r == 0) pd.dsub = reinterpret_cast<float*>(ws + plan.pairs[k].dsub);
@@ -422,7 +447,7 @@ std::vector<int> b_shape_keys() {
   std::vector<int> v;
   for (int D = 16; D <= SF_MAX_DISPARITY; D += 16) {
     const fused::Shape sh = fused::shape_for(D);
-    v.push_back(sh.dc * 10000 + sh.chunks * 100 + sh.halo);
+    v.push_back(sh.order * 1000000 + sh.dc * 10000 + sh.chunks * 100 + sh.halo);
   }
   return v;
 }
@@ -484,7 +509,7 @@ BatchSetup batch_setup(const sf_batch_item* items, int n, const sf_sgm_params* p
     int c = 0;
     for (; c < (int)b.classes.size(); c++) {
       const fused::Shape& o = b.classes[c].sh;
-      if (o.dc == sh.dc && o.chunks == sh.chunks && o.halo == sh.halo) break;
+      if (o.dc == sh.dc && o.chunks == sh.chunks && o.halo == sh.halo && o.order == sh.order) break;
     }
     if (c == (int)b.classes.size()) {
       b.classes.push_back(BatchClass());
@@ -509,7 +534,7 @@ BatchSetup batch_setup(const sf_batch_item* items, int n, const sf_sgm_params* p
       tmp[k].J = (ps.W + fused::kTW - 1) / fused::kTW;
       tmp[k].nb = nb_of(c.pass_ids[k]);
     }
-    c.tt = build_tables(tmp.data(), (int)tmp.size());
+    c.tt = build_tables(tmp.data(), (int)tmp.size(), c.sh.order == 1);
     c.off_down = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
     c.off_up = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
     c.off_tab = o; o = align_up(o + c.tt.ints.size() * sizeof(int), 256);
@@ -520,7 +545,7 @@ BatchSetup batch_setup(const sf_batch_item* items, int n, const sf_sgm_params* p
 
 // Host image of the tables region for a plan placed in workspace ws.
 std::vector<uint8_t> batch_tables(const BatchSetup& b, const FusedPlan& plan, uint8_t* ws,
-                                  const sf_sgm_params* p) {
+                                  const sf_sgm_params* p, const sf_batch_item* items) {
   std::vector<uint8_t> blob(b.table_bytes, 0);
   for (const BatchClass& c : b.classes) {
     fused::PassDesc* dn = reinterpret_cast<fused::PassDesc*>(blob.data() + c.off_down);
@@ -530,13 +555,19 @@ std::vector<uint8_t> batch_tables(const BatchSetup& b, const FusedPlan& plan, ui
       const PairShape& ps = b.pairs[pair];
       dn[k] = pass_desc(ws, plan, plan.pairs[pair], r, ps.W, ps.H, ps.D, ps.D, nullptr);
       dn[k].dint = nullptr;
+      if (p->adaptive_p2) {
+        // pair 2 i + f of item i: frame t (f = 0) or t+1; pass r: reference image
+        const sf_batch_item& it = items[pair / 2];
+        const bool t1 = (pair & 1) != 0;
+        dn[k].guide = r == 0 ? (t1 ? it.left_t1 : it.left_t) : (t1 ? it.right_t1 : it.right_t);
+        dn[k].gpitch = it.pitch;
+      }
       up[k] = dn[k];
       up[k].dint = reinterpret_cast<int16_t*>(ws + plan.pairs[pair].pass[r].dint);
       up[k].dsub = r == 0 ? reinterpret_cast<float*>(ws + plan.pairs[pair].dsub) : nullptr;
     }
     memcpy(blob.data() + c.off_tab, c.tt.ints.data(), c.tt.ints.size() * sizeof(int));
   }
-  (void)p;
   return blob;
 }
 
@@ -624,6 +655,8 @@ void sf_default_params(sf_sgm_params* p) {
   p->D = 128;
   p->subpixel = 1;
   p->lr_tol = 1;
+  p->adaptive_p2 = 0;
+  p->uniqueness = 0;
 }
 
 const char* sf_status_string(sf_status s) {
@@ -667,15 +700,15 @@ size_t sf_aggregate_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p)
   return single_plan(W, H, p->D, 1).total;
 }
 
-sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
-                           uint16_t* agg_out, void* workspace, size_t ws_bytes, void* stream) {
-  (void)workspace; (void)ws_bytes;
-  sf_status st = check_size(W, H);
-  if (st != SF_OK) return st;
-  if (!cost || !agg_out) return SF_ERR_INVALID_ARG;
-  if ((st = check_params(p, W, H)) != SF_OK) return st;
-  if (!aligned(agg_out, 2)) return SF_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// sf_sgm_aggregate(_guided): guide is the reference image for the adaptive
+// P2 (nullptr with constant P2).
+sf_status aggregate_impl(const uint8_t* cost, const uint8_t* guide, int gpitch, int32_t W, int32_t H,
+                         const sf_sgm_params* p, uint16_t* agg_out, void* workspace, size_t ws_bytes,
+                         cudaStream_t s) {
   // fused sweeps when the volume is 16-disparity aligned and a workspace of
   // sf_aggregate_workspace_size() bytes is given; staged kernels otherwise
   if (g_use_fused && p->D % 16 == 0 && aligned(cost, 16) && workspace && aligned(workspace, 256) &&
@@ -686,11 +719,40 @@ sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_s
     fused::PassDesc d = pass_desc(ws, plan, plan.pairs[0], 0, W, H, p->D, p->D, cost);
     d.dint = nullptr;
     d.S = agg_out;
+    d.guide = guide;
+    d.gpitch = gpitch;
     return run_sweeps(p, &d, 1, p->D, nullptr, nullptr, nullptr, nullptr,
                       reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s);
   }
-  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg_out, s));
+  SF_TRY_CUDA(launch_aggregate(cost, W, H, p->D, p->P1, p->P2, p->path_mask, agg_out, s, guide, gpitch));
   return SF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_sgm_aggregate(const uint8_t* cost, int32_t W, int32_t H, const sf_sgm_params* p,
+                           uint16_t* agg_out, void* workspace, size_t ws_bytes, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!cost || !agg_out) return SF_ERR_INVALID_ARG;
+  if ((st = check_params(p, W, H)) != SF_OK) return st;
+  if (p->adaptive_p2) return SF_ERR_INVALID_ARG;   // needs the guide: sf_sgm_aggregate_guided
+  if (!aligned(agg_out, 2)) return SF_ERR_INVALID_ARG;
+  return aggregate_impl(cost, nullptr, 0, W, H, p, agg_out, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+sf_status sf_sgm_aggregate_guided(const uint8_t* cost, const uint8_t* guide, int32_t pitch, int32_t W,
+                                  int32_t H, const sf_sgm_params* p, uint16_t* agg_out, void* workspace,
+                                  size_t ws_bytes, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!cost || !agg_out || !guide || pitch < W) return SF_ERR_INVALID_ARG;
+  if ((st = check_params(p, W, H)) != SF_OK) return st;
+  if (!aligned(agg_out, 2)) return SF_ERR_INVALID_ARG;
+  return aggregate_impl(cost, p->adaptive_p2 ? guide : nullptr, pitch, W, H, p, agg_out, workspace, ws_bytes,
+                        (cudaStream_t)stream);
 }
 
 sf_status sf_disparity_select(const uint16_t* agg, int32_t W, int32_t H, int32_t D,
@@ -892,7 +954,7 @@ sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_param
   if (!workspace || ws_bytes < plan.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
   uint8_t* ws = (uint8_t*)workspace;
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<uint8_t> blob = batch_tables(b, plan, ws, p);
+  std::vector<uint8_t> blob = batch_tables(b, plan, ws, p, items);
   // descriptor tables travel before the work (pageable source: the copy has
   // read it when the call returns)
   SF_TRY_CUDA(cudaMemcpyAsync(ws + plan.tables, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
@@ -939,7 +1001,11 @@ void sf_batch_release_graphs(void) {
 }
 
 sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo) {
-  return fused::set_shape_override(d_lo, d_hi, dc, halo) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
+  return fused::set_shape_override(d_lo, d_hi, dc, halo, 0) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
+}
+
+sf_status sf_set_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order) {
+  return fused::set_shape_override(d_lo, d_hi, dc, halo, order) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
 }
 
 sf_status sf_set_fused(int32_t enable) {
@@ -981,14 +1047,19 @@ constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoallocMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the first lookup may load the module's device code).
-sf_status noalloc_scratch(uint8_t** out) {
+// Device address of the scratch array on the current device.  Outside stream
+// capture it is looked up on every call (cheap once the module is loaded), so
+// an address that moved with a device or context reset is never reused; under
+// capture the address of the last uncaptured call on this device serves (the
+// first lookup may load the module's device code, which capture forbids).
+sf_status noalloc_scratch(cudaStream_t s, uint8_t** out) {
   int dev = -1;
   SF_TRY_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoallocMaxDevices) return SF_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SF_TRY_CUDA(cudaStreamIsCapturing(s, &cap));
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     const cudaError_t rc = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (rc != cudaSuccess || !p) {
@@ -1034,13 +1105,14 @@ extern "C" sf_status sf_sgm_aggregate_noalloc(const uint8_t* cost, int32_t W, in
   if (st != SF_OK) return st;
   if (!cost || !agg_out) return SF_ERR_INVALID_ARG;
   if ((st = check_params(p, W, H)) != SF_OK) return st;
+  if (p->adaptive_p2) return SF_ERR_INVALID_ARG;   // no guide image here
   if (p->D % 16 != 0) return SF_ERR_UNSUPPORTED;
   if (!aligned(cost, 16) || !aligned(agg_out, 2) || !aligned(err_out, 4)) return SF_ERR_INVALID_ARG;
   const NoallocLayout lay(W, H, p->D);
   if (lay.total > (size_t)SF_NOALLOC_SCRATCH_BYTES) return SF_ERR_UNSUPPORTED;
   uint8_t* ws = nullptr;
-  if ((st = noalloc_scratch(&ws)) != SF_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  if ((st = noalloc_scratch(s, &ws)) != SF_OK) return st;
   // the control words start every call at zero; the rest of the scratch is
   // fully written before it is read
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, lay.control_bytes, s));
@@ -1058,6 +1130,8 @@ extern "C" sf_status sf_sgm_aggregate_noalloc(const uint8_t* cost, int32_t W, in
   d.dint = nullptr;
   d.dsub = nullptr;
   d.S = agg_out;
+  d.guide = nullptr;
+  d.gpitch = 0;
   st = run_sweeps(p, &d, 1, p->D, nullptr, nullptr, nullptr, nullptr,
                   reinterpret_cast<int*>(ws + lay.counters), reinterpret_cast<int*>(ws + lay.err), s);
   if (st != SF_OK) return st;
@@ -1121,6 +1195,9 @@ sf_status check_learned(int W, int H, const sf_sgm_params* p) {
   if (st != SF_OK) return st;
   if ((st = check_params(p, W, H)) != SF_OK) return st;
   if (p->path_mask != 0xFFu) return SF_ERR_UNSUPPORTED;   // features use all eight paths
+  // the network's acceptance rule stands in for every check of the left
+  // winners, the uniqueness filter included
+  if (p->uniqueness != 0) return SF_ERR_UNSUPPORTED;
   return SF_OK;
 }
 
@@ -1166,6 +1243,8 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
     pd.dint = nullptr;
     pd.dsub = nullptr;
     pd.S = reinterpret_cast<uint16_t*>(ws + b.S);
+    pd.guide = p->adaptive_p2 ? left[k] : nullptr;
+    pd.gpitch = pitch;
   }
   // the learned path's two passes keep the built-in sweep shape (tuned
   // overrides are measured on the four passes of the plain frame)

@@ -10,9 +10,12 @@ namespace sf {
 namespace {
 
 // One warp per pixel; lanes stride over d.  The smallest d with the minimal
-// aggregated cost wins (ties resolve to the smaller disparity).
+// aggregated cost wins (ties resolve to the smaller disparity).  With a
+// uniqueness ratio u > 0 a winner whose cost S0 is not clearly below every
+// disparity two or more away (100 S2 < (100 + u) S0) gets a NaN subpixel
+// value, which the left-right check treats as removed.
 __global__ void __launch_bounds__(256)
-    select_kernel(const uint16_t* __restrict__ S, int W, int H, int D, int subpixel,
+    select_kernel(const uint16_t* __restrict__ S, int W, int H, int D, int subpixel, int unique,
                   int16_t* __restrict__ dint, float* __restrict__ dsub) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -28,6 +31,12 @@ __global__ void __launch_bounds__(256)
   }
   const uint32_t m = __reduce_min_sync(kFullMask, best);
   const uint32_t dstar = __reduce_min_sync(kFullMask, best == m ? best_d : 0xffffffffu);
+  uint32_t s2 = 0xffffffffu;
+  if (unique && dsub) {
+    for (int d = lane; d < D; d += 32)
+      if (d + 1 < (int)dstar || d > (int)dstar + 1) s2 = min(s2, (uint32_t)s[d]);
+    s2 = __reduce_min_sync(kFullMask, s2);
+  }
   if (lane == 0) {
     dint[warp] = (int16_t)dstar;
     if (dsub) {
@@ -38,6 +47,7 @@ __global__ void __launch_bounds__(256)
         // exact integers; IEEE division (no fast math) rounds once
         v = __fadd_rn((float)dstar, __fdiv_rn((float)(a - b), (float)(2 * (a + b))));
       }
+      if (s2 != 0xffffffffu && 100ull * s2 < (uint64_t)(100 + unique) * m) v = __int_as_float(0x7fc00000);
       dsub[warp] = v;
     }
   }
@@ -52,7 +62,8 @@ __global__ void lr_check_kernel(const int16_t* __restrict__ dL, const int16_t* _
   const int dl = dL[i];
   const int xr = x - dl;
   bool ok = false;
-  if (xr >= 0) ok = abs(dl - (int)dR[y * W + xr]) <= tol;
+  // a left winner removed before the check (NaN subpixel value) stays removed
+  if (xr >= 0 && !isnan(dL_sub[i])) ok = abs(dl - (int)dR[y * W + xr]) <= tol;
   valid[i] = ok;
   disp[i] = ok ? dL_sub[i] : __int_as_float(0x7fc00000);
 }
@@ -125,11 +136,11 @@ __global__ void combine_kernel(const float* __restrict__ D0, const float* __rest
 }  // namespace
 
 cudaError_t launch_select(const uint16_t* S, int W, int H, int D, int subpixel, int16_t* dint,
-                          float* dsub, cudaStream_t s) {
+                          float* dsub, cudaStream_t s, int unique) {
   StageTrace trace(SF_STAGE_SELECT, s);
   count_launches(1);
   const long long threads = (long long)W * H * 32;
-  select_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(S, W, H, D, subpixel, dint, dsub);
+  select_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(S, W, H, D, subpixel, unique, dint, dsub);
   return cudaGetLastError();
 }
 

@@ -14,14 +14,16 @@ constexpr int kMaxPass = 4;
 // Launch shape chosen by D: a thread owns DC disparities of two lines; the
 // disparities of a line pair are spread over `chunks` consecutive threads (a
 // power of two); the band sweeps carry `halo` extra columns on each side of
-// a strip and walk bands of halo + 1 rows.
+// a strip and walk bands of halo + 1 rows.  `order` schedules the two scan
+// orders: 0 = the down sweep's launch, then the up sweep's; 1 = both in one
+// launch, meeting in the middle.
 struct Shape {
-  int dc, chunks, halo;
+  int dc, chunks, halo, order;
 };
 // built-in rule unless a tuned override covers D (and `tuned` allows it)
 Shape shape_for(int D, bool tuned = true);
 bool shape_supported(int dc, int chunks, int halo);
-int set_shape_override(int d_lo, int d_hi, int dc, int halo);   // 0 = ok
+int set_shape_override(int d_lo, int d_hi, int dc, int halo, int order);   // 0 = ok
 inline int padded_d(int D) { return ((D + 15) / 16) * 16; }
 inline int band_rows(int D, bool tuned = true) { return shape_for(D, tuned).halo + 1; }
 
@@ -33,16 +35,18 @@ struct PassDesc {
   uint8_t* hfwd;         // [H][W][Dp] uint8, L of path (+1,0)
   uint8_t* hbwd;         // [H][W][Dp] uint8, L of path (-1,0)
   uint32_t* sdown;       // tile layout [H][J][16][chunks][dc] u32
-  uint8_t* bs;           // band-end states [2][3][W][Dp] u8
+  uint8_t* bs;           // band-end states [2 orders][2][3][W][Dp] u8
   int* flags_down;       // [J] bands completed by the down sweep
   int* flags_up;         // [J] bands completed by the up sweep
   int16_t* dint;         // winner per pixel (up sweep), or nullptr
   float* dsub;           // subpixel winner (up sweep), or nullptr
   uint16_t* S;           // full aggregated cost [H][W][D] (up sweep), or nullptr
+  const uint8_t* guide;  // reference image [H][gpitch] for the intensity-adaptive P2, or nullptr
+  int gpitch;
 };
 
 struct HLineArgs {
-  int P1, P2, Dmax, npass, nblocks;
+  int P1, P2, Dmax, npass, nblocks;   // P2: the constant P2, or the base of the adaptive one
   int builtin_shape;           // 1: ignore tuned shape overrides
   uint32_t path_mask;
   int uniform_blocks;          // > 0: every pass has this many blocks
@@ -54,6 +58,7 @@ struct HLineArgs {
 
 struct SweepArgs {
   int P1, P2, subpixel, Dmax, npass, ntasks;
+  int unique;                  // uniqueness ratio (percent) of the winners with a subpixel output, 0 = off
   int builtin_shape;           // 1: ignore tuned shape overrides
   uint32_t path_mask;
   int en_h0, en_h1;
@@ -75,7 +80,7 @@ inline size_t sdown_bytes(int W, int H, int Dshape, bool tuned = true) {
   const Shape s = shape_for(Dshape, tuned);
   return (size_t)H * J * 16 * s.chunks * s.dc * sizeof(uint32_t);
 }
-inline size_t bs_bytes(int W, int D) { return (size_t)2 * 3 * W * padded_d(D); }
+inline size_t bs_bytes(int W, int D) { return (size_t)2 * 2 * 3 * W * padded_d(D); }
 inline size_t cost_pair_smem(int W, int D) {
   return 2 * ((size_t)W * 8 + (size_t)((W + 3) / 4) * 32) + (size_t)W * (padded_d(D) + 4);
 }
@@ -95,7 +100,8 @@ cudaError_t launch_cost_pair(const CostPairs& job, int W, int H, int D, int Dp, 
 // left-reference volumes only
 cudaError_t launch_cost_left(const CostPairs& job, int W, int H, int D, int Dp, int cmax, cudaStream_t s);
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s);
-cudaError_t launch_sweep(const SweepArgs& a, bool up, cudaStream_t s);
+// mode 0: down sweep, 1: up sweep, 2: both orders in one launch
+cudaError_t launch_sweep(const SweepArgs& a, int mode, cudaStream_t s);
 
 }  // namespace fused
 }  // namespace sf

@@ -77,10 +77,13 @@ cudaError_t launch_census(const uint8_t* img, int W, int H, int pitch, int cw, i
 cudaError_t launch_cost_volume(const uint8_t* ref, const uint8_t* other, int W, int H, int pitch,
                                int cw, int ch, int D, int ref_is_right, uint8_t* cost,
                                cudaStream_t s);
+// guide: reference image [H][gpitch] for the intensity-adaptive P2, or nullptr
 cudaError_t launch_aggregate(const uint8_t* cost, int W, int H, int D, int P1, int P2,
-                             uint32_t path_mask, uint16_t* S, cudaStream_t s);
+                             uint32_t path_mask, uint16_t* S, cudaStream_t s,
+                             const uint8_t* guide = nullptr, int gpitch = 0);
+// unique: uniqueness ratio in percent (0 = off), applied where dsub is written
 cudaError_t launch_select(const uint16_t* S, int W, int H, int D, int subpixel, int16_t* dint,
-                          float* dsub, cudaStream_t s);
+                          float* dsub, cudaStream_t s, int unique = 0);
 cudaError_t launch_lr_check(const int16_t* dL, const int16_t* dR, const float* dL_sub, int W, int H,
                             int tol, uint8_t* valid, float* disp, cudaStream_t s);
 cudaError_t launch_combine(const float* D0, const float* D1, const float* flow, int W, int H,

@@ -25,6 +25,9 @@
 //   4. sweep_kernel<UP>: paths (0,-1), (-1,-1), (+1,-1) bottom to top, adds
 //      S_down and both horizontal paths, and fuses winner-take-all and the
 //      parabolic subpixel step (or writes the full aggregated cost).
+//   3+4. sweep_kernel<MERGED>: both scan orders in one launch, meeting in
+//      the middle: each band is finished (sums and selection) by whichever
+//      order reaches it second, so twice as many band tasks can run at once.
 // Tasks come from a band-major queue, so the sweep time is the band chain
 // (bands x per-band latency); each task is spread over many threads to keep
 // that latency short.  All arithmetic is exact integer math in 16-bit lanes
@@ -243,6 +246,14 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Penalty table of the intensity-adaptive P2 (the SGM cited in Sec. 3.1):
+// entry g = P2 / g rounded down, at least P1, for an intensity step g > 0,
+// and P2 for g = 0.  Filled by the whole block before its first barrier.
+__device__ __forceinline__ void fill_p2_table(uint16_t* lut, int P1, int P2) {
+  for (int g = threadIdx.x; g < 256; g += blockDim.x) lut[g] = (uint16_t)(g == 0 ? P2 : max(P1, P2 / g));
+}
+__device__ __forceinline__ uint32_t absdiff_u8(uint32_t a, uint32_t b) { return a > b ? a - b : b - a; }
+
 template <int DC, int CHUNKS>
 __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     hline_kernel(const __grid_constant__ HLineArgs a) {
@@ -250,6 +261,7 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
   extern __shared__ __align__(128) uint8_t hsmem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_fail;
+  __shared__ uint16_t s_lut[256];
   // block -> (pass, direction, 16-row block); passes listed by prefix of
   // their block counts (2 directions x row blocks)
   int p = 0;
@@ -306,12 +318,26 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  const bool adaptive = pd.guide != nullptr;
+  if (adaptive) fill_p2_table(s_lut, a.P1, a.P2);
   __syncthreads();
   if (t == 0) issue(0);
   uint32_t L[DC], Cr[DC], N[DC];
 #pragma unroll
   for (int i = 0; i < DC; i++) L[i] = 0;
   uint32_t m = 0;
+  // adaptive P2: the guide pixels of both rows at the walk's current column
+  // (rows past the block's last row read its last row; their lanes are not
+  // stored) and the previous column's values
+  const int gstep = dir == 0 ? 1 : -1;
+  const uint8_t* ga = nullptr;
+  const uint8_t* gb = nullptr;
+  uint32_t gprev0 = 0, gprev1 = 0;
+  if (adaptive) {
+    const int xstart = dir == 0 ? 0 : W - 1;
+    ga = pd.guide + (size_t)(ybase + min(r0, nrows - 1)) * pd.gpitch + xstart;
+    gb = pd.guide + (size_t)(ybase + r1) * pd.gpitch + xstart;
+  }
   // one step along the line: costs from the tile, the update, the outputs.
   // (A line's first step has L = 0 and m = 0, so its update is C whatever
   // the end values at d = 0 and d = Dp-1.)
@@ -335,7 +361,17 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     uint32_t right = __shfl_down_sync(0xffffffffu, Lp[0], 1, CHUNKS);
     if (q_first) left = kInf2;
     if (q_last) right = kInf2;
-    sgm_update<DC>(Lp, Cr, left, right, m, p1x2, p2x2, Ln);
+    uint32_t p2s = p2x2;
+    if (adaptive) {
+      // (a line's first step gets a meaningless penalty: its update is C)
+      const uint32_t i0 = __ldg(ga), i1 = __ldg(gb);
+      ga += gstep;
+      gb += gstep;
+      p2s = (uint32_t)s_lut[absdiff_u8(i0, gprev0)] | ((uint32_t)s_lut[absdiff_u8(i1, gprev1)] << 16);
+      gprev0 = i0;
+      gprev1 = i1;
+    }
+    sgm_update<DC>(Lp, Cr, left, right, m, p1x2, p2s, Ln);
     m = group_min2<CHUNKS>(tree_min<DC>(Ln));
     if (io) {
       V wa, wb;
@@ -346,19 +382,32 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     oa += step;
     ob += step;
   };
-  for (int c = 0; c < nchunks; c++) {
+  // Chunk c is phase c >> 1 of bars[c & 1]; waiting on that phase's parity
+  // returns once it has completed.
+  int c = 0;
+  for (; c < nchunks; c++) {
     if (t == 0 && c + 1 < nchunks) issue(c + 1);
-    // bounded wait for chunk c
-    {
+    const unsigned par = (unsigned)((c >> 1) & 1);
+    // bounded wait for chunk c by one thread; every thread then reads the
+    // verdict after the same barrier, so all of them leave or stay together
+    if (t == 0) {
       long long spins = 0;
-      while (!mbar_try_wait(&bars[c & 1], (unsigned)((c >> 1) & 1))) {
+      while (!mbar_try_wait(&bars[c & 1], par)) {
         if (++spins > kMbarSpin) {
           s_fail = 1;
           break;
         }
       }
     }
+    __syncthreads();
     if (s_fail) break;
+    // the phase has completed: each thread observes it itself (returns at
+    // once), which orders the copied bytes before its reads
+    {
+      long long spins = 0;
+      while (!mbar_try_wait(&bars[c & 1], par) && ++spins < kMbarSpin) {
+      }
+    }
     const int xs = chunk_x0(c), cw = chunk_w(c);
     const int cx0 = dir == 0 ? 0 : cw - 1;   // first column of the walk in this chunk
     const uint8_t* tile = hsmem + (c & 1) * kHlineTileBytes;
@@ -380,12 +429,16 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     __syncthreads();   // buffer c&1 is free for chunk c+2
   }
   if (s_fail) {
-    // a copy never completed: record it, let in-flight copies land (bounded)
+    // chunk c never completed: record it, then let the copies still in
+    // flight land before the CTA leaves its shared memory (bounded).  In
+    // flight: chunk c and, if it was issued, chunk c + 1; every earlier chunk
+    // was waited for.  Each is awaited on the parity of its own phase.
     if (t == 0) {
       atomicExch(a.err, 1);
-      for (int b = 0; b < 2; b++) {
+      const int last = min(c + 1, nchunks - 1);
+      for (int cc = c; cc <= last; cc++) {
         long long spins = 0;
-        while (!mbar_try_wait(&bars[b], 0) && !mbar_try_wait(&bars[b], 1) && ++spins < kMbarSpin) {
+        while (!mbar_try_wait(&bars[cc & 1], (unsigned)((cc >> 1) & 1)) && ++spins < kMbarSpin) {
         }
       }
     }
@@ -404,26 +457,42 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
 // halo pairs (x1 + h, x1 + HALO/2 + h) carry FR only.  Halo pairs whose
 // columns can no longer reach the strip before the band ends skip the update.
 
-// Task index -> (pass, band in processing order, strip).  Tasks are
-// band-major; with one shape for every pass the split is arithmetic,
+// Task index -> (pass, step in processing order, strip, scan order).  Tasks are
+// step-major; with one shape for every pass the split is arithmetic,
 // otherwise passes are sorted by band count (descending) and the tables give
-// each band's first task and the prefix of strip counts.
-__device__ __forceinline__ void decode_task(const SweepArgs& a, int task, int& p, int& bi, int& j) {
+// each step's first task and the prefix of strip counts.  A merged launch
+// (both scan orders in one queue) lists, per step, the tasks of the down
+// sweep and then those of the up sweep (scan 1).
+template <bool MERGED>
+__device__ __forceinline__ void decode_task(const SweepArgs& a, int task, int& p, int& bi, int& j, int& scan) {
+  scan = 0;
   if (a.uniform_items > 0) {
-    bi = task / a.uniform_items;
-    const int it = task - bi * a.uniform_items;
+    const int per = MERGED ? 2 * a.uniform_items : a.uniform_items;
+    bi = task / per;
+    int it = task - bi * per;
+    if (MERGED && it >= a.uniform_items) {
+      scan = 1;
+      it -= a.uniform_items;
+    }
     const int J = a.inl[0].J;
     p = it / J;
     j = it - p * J;
     return;
   }
-  int lo = 0, hi = a.nbands - 1;   // last band whose first task <= task
+  int lo = 0, hi = a.nbands - 1;   // last step whose first task <= task
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (a.band_start[mid] <= task) lo = mid; else hi = mid - 1;
   }
   bi = lo;
-  const int off = task - a.band_start[bi];
+  int off = task - a.band_start[bi];
+  if (MERGED) {
+    const int nact = a.prefixJ[a.band_npass[bi]];
+    if (off >= nact) {
+      scan = 1;
+      off -= nact;
+    }
+  }
   int plo = 0, phi = a.band_npass[bi] - 1;   // last pass whose strip prefix <= off
   while (plo < phi) {
     const int mid = (plo + phi + 1) >> 1;
@@ -448,40 +517,52 @@ __device__ __forceinline__ void store_u4(uint4* dst, int stride, const uint32_t*
   for (int w = 0; w < N / 4; w++) dst[w * stride] = make_uint4(r[4 * w], r[4 * w + 1], r[4 * w + 2], r[4 * w + 3]);
 }
 
-template <int DC, int CHUNKS, int HALO, bool UP>
+// Launch modes of the band sweeps: the down sweep alone, the up sweep alone
+// (it reads the down sweep's partial sums and selects), or both scan orders
+// in one launch.  In the merged launch each band of a strip is reached twice,
+// once by each scan order: the first arrival stores its three paths' partial
+// sum, the second adds it, the horizontal paths and its own three paths, and
+// selects.  With M = ceil(nb / 2), the down sweep arrives first at bands
+// 0 .. M-1 and the up sweep at bands M .. nb-1, so both run at once from
+// opposite ends and the work in flight doubles.
+constexpr int kModeDown = 0, kModeUp = 1, kModeMerged = 2;
+
+template <int DC, int CHUNKS, int HALO, int MODE>
 struct SweepCfg {
+  static constexpr bool SEC = MODE != kModeDown;   // second arrivals possible
   static constexpr int NP = 16 + HALO;      // column pairs per task
   static constexpr int NT = NP * CHUNKS;    // threads
   static constexpr int NO = 16 * CHUNKS;    // threads of owned pairs
   static constexpr int TH = HALO + 1;       // band rows
-  static constexpr int RING = UP ? 2 : 3;   // prefetch depth in rows
-  static constexpr int XW = DC / 4 + 4;     // uint4 slots per owned thread per row (UP)
+  static constexpr int RING = SEC ? 2 : 3;  // prefetch depth in rows
+  static constexpr int XW = DC / 4 + 4;     // uint4 slots per owned thread per row (second arrival)
   static constexpr bool select_by_halo() {
-    return UP && CHUNKS >= 2 && (HALO * CHUNKS) / kTW >= 1 &&
+    return SEC && CHUNKS >= 2 && (HALO * CHUNKS) / kTW >= 1 &&
            (CHUNKS % ((HALO * CHUNKS) / kTW > 0 ? (HALO * CHUNKS) / kTW : 1)) == 0;
   }
   static constexpr size_t smem_bytes() {
     return (size_t)2 * 2 * (DC / 4) * NT * 16     // diagonal hand-over
            + (size_t)2 * 2 * NP * 4                // pair minima
-           + (size_t)2 * (DC / 4) * NO * 16        // aggregated-cost rows for selection (UP)
+           + (size_t)2 * (DC / 4) * NO * 16        // aggregated-cost rows for selection
            + (size_t)RING * 2 * NT * DC            // cost ring
-           + (UP ? (size_t)RING * XW * NO * 16 : 0);
+           + (SEC ? (size_t)RING * XW * NO * 16 : 0);
   }
 };
 
-// Registers: one CTA per SM and nothing beside it, so a sweep may use the
-// whole register file (at most 168 a thread; the 16-disparity shapes keep
-// 168).
-constexpr int sweep_max_regs(int nt) {
-  const int budget = 65536 / nt;
+// Registers: a separate down or up launch runs one CTA per SM with nothing
+// beside it, so it may use the whole register file (at most 168 a thread;
+// the 16-disparity shapes keep 168); a merged launch aims at two CTAs per SM.
+constexpr int sweep_max_regs(int nt, int ctas) {
+  const int budget = 65536 / (nt * ctas);
   return budget > 168 ? 168 : (budget / 8) * 8;
 }
 
-template <int DC, int CHUNKS, int HALO, bool UP>
+template <int DC, int CHUNKS, int HALO, int MODE>
 __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
-    __maxnreg__(DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS))
+    __maxnreg__(MODE == kModeMerged ? sweep_max_regs((16 + HALO) * CHUNKS, 2)
+                                    : (DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS, 1)))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
-  using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
+  using Cfg = SweepCfg<DC, CHUNKS, HALO, MODE>;
   using V = typename ByteVec<DC>::T;
   constexpr int NP = Cfg::NP, NT = Cfg::NT, NO = Cfg::NO, TH = Cfg::TH, RING = Cfg::RING;
   constexpr int XW = Cfg::XW, G = DC / 4;
@@ -501,6 +582,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   uint4* ringx = reinterpret_cast<uint4*>(ringc + RING * 2 * NT);  // [slot][XW][owned thread]
   __shared__ int s_abort;
   __shared__ int s_task;
+  __shared__ uint16_t s_lut[256];   // adaptive P2 by intensity step
 
   const int t = threadIdx.x;
   const int pr = t / CHUNKS;
@@ -508,9 +590,6 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   const bool owned = pr < 16;
   const int d0 = q * DC;
   const uint32_t p1x2 = a.P1 * 0x10001u, p2x2 = a.P2 * 0x10001u;
-  const bool en_v = (a.path_mask >> (UP ? 3 : 2)) & 1u;
-  const bool en_fl = (a.path_mask >> (UP ? 6 : 4)) & 1u;
-  const bool en_fr = (a.path_mask >> (UP ? 5 : 7)) & 1u;
   static_assert(CHUNKS >= 2, "owned pairs fill whole warps");
   constexpr int HH = HALO / 2;             // pairs per halo side
   constexpr int LH0 = 16, RH0 = 16 + HH;    // first left / right halo pair
@@ -521,7 +600,6 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   const unsigned role_mask = __ballot_sync(0xffffffffu, owned) * (role == 0) +
                              __ballot_sync(0xffffffffu, role == 1) * (role == 1) +
                              __ballot_sync(0xffffffffu, role == 2) * (role == 2);
-  const bool en_all = en_v && en_fl && en_fr;
   const int hh = role == 1 ? pr - LH0 : pr - RH0;
   // hand-over sources: FL from column x-1, FR from column x+1.  Whole
   // registers move between pairs except at the seams of the layout, where
@@ -541,6 +619,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     else { fr_src = RH0; fr_src2 = pr; fr_sel = 0x7632u; }        // (x1+HALO/2, -)
   }
   if (t == 0) s_abort = 0;
+  fill_p2_table(s_lut, a.P1, a.P2);
   __syncthreads();
 
   // Tasks (band, pass, strip) in band-major order from a global counter: any
@@ -553,18 +632,29 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     __syncthreads();
     const int task = s_task;
     if (task >= ntasks) break;
-    int p, bi, j;
-    decode_task(a, task, p, bi, j);
+    int p, bi, j, scan;   // scan: 0 down sweep, 1 up sweep (merged launch)
+    decode_task<MODE == kModeMerged>(a, task, p, bi, j, scan);
     const PassDesc pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];   // by value: fields in registers
     const int W = pd.W, H = pd.H, Dp = pd.Dp, J = pd.J, D = pd.D;
+    // scan order of this task (up: bottom to top) and whether it is the
+    // second arrival at its band (adds the other order's partial sum and the
+    // horizontal paths, and selects) or the first (stores its partial sum)
+    const bool up = MODE == kModeUp || (MODE == kModeMerged && scan == 1);
+    const int band = up ? (pd.nb - 1 - bi) : bi;
+    const int meet = (pd.nb + 1) >> 1;
+    const bool second = MODE == kModeUp ? true
+                                        : (MODE == kModeDown ? false : (up ? band < meet : band >= meet));
+    const bool en_v = (a.path_mask >> (up ? 3 : 2)) & 1u;
+    const bool en_fl = (a.path_mask >> (up ? 6 : 4)) & 1u;
+    const bool en_fr = (a.path_mask >> (up ? 5 : 7)) & 1u;
+    const bool en_all = en_v && en_fl && en_fr;
     const bool pad = d0 + DC > D;
-    const bool s_vec = UP && pd.S && D % 8 == 0 && (reinterpret_cast<uintptr_t>(pd.S) & 15u) == 0;
+    const bool s_vec = second && pd.S && D % 8 == 0 && (reinterpret_cast<uintptr_t>(pd.S) & 15u) == 0;
     const bool live = d0 < Dp;   // chunks past the padded depth hold no data
-    const int band = UP ? (pd.nb - 1 - bi) : bi;
     const int ytop = band * TH;
     const int nrows = min(TH, H - ytop);
     const int x0 = j * kTW;
-    int* const flags = UP ? pd.flags_up : pd.flags_down;
+    int* const flags = up ? pd.flags_up : pd.flags_down;
     // ---- columns of this thread's pair ----
     int xlo, xhi;
     if (role == 0) {
@@ -585,12 +675,12 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     // neighbour wait (they do not depend on it) ----
     auto issue_row = [&](int r) {
       const bool ok = r < nrows;
-      const int yy = UP ? ytop + nrows - 1 - r : ytop + r;
+      const int yy = up ? ytop + nrows - 1 - r : ytop + r;
       V* cs = ringc + (r % RING) * 2 * NT + t;
       const uint8_t* rowc = pd.cost + (size_t)yy * W * Dp + d0;
       cp_async<DC>(cs, ok && lo_in ? rowc + (size_t)xlo * Dp : pd.cost, ok && lo_in);
       cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : pd.cost, ok && hi_in);
-      if (UP && owned) {
+      if (Cfg::SEC && second && owned) {
         uint4* xs = ringx + (r % RING) * XW * NO + t;
         const uint4* sd = sd_out + (ok ? (size_t)yy * sd_row : 0);
 #pragma unroll
@@ -604,38 +694,55 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
       }
       cp_async_commit();
     };
+    // a second arrival of a merged launch reads the other order's partial
+    // sums, which exist only after its wait: it prefetches after the wait
+    const bool early = !(MODE == kModeMerged && second);
+    if (early) {
 #pragma unroll
-    for (int r = 0; r < RING - 1; r++) issue_row(r);
-    // ---- wait for the previous band of this strip and its neighbours ----
-    if (t == 0 && bi > 0) {
+      for (int r = 0; r < RING - 1; r++) issue_row(r);
+    }
+    // ---- wait for the previous band of this strip and its neighbours, and
+    // (second arrival of a merged launch) for the other scan order's pass
+    // over this band of this strip ----
+    if (t == 0) {
       long long spins = 0;
-      const int* fl = flags;
-      for (int n = j - 1; n <= j + 1; n++) {
-        if (n < 0 || n >= J) continue;
-        while (ld_acquire(fl + n) < bi) {
+      auto wait_flag = [&](const int* f, int target) {
+        while (ld_acquire(f) < target) {
           if (++spins > a.spin_limit || *((volatile int*)a.err) != 0) {
             atomicExch(a.err, 1);
             s_abort = 1;
-            break;
+            return;
           }
           if (spins > 64) __nanosleep(32);
         }
-        if (s_abort) break;
+      };
+      if (bi > 0) {
+        for (int n = j - 1; n <= j + 1 && !s_abort; n++)
+          if (n >= 0 && n < J) wait_flag(flags + n, bi);
       }
+      if (MODE == kModeMerged && second && !s_abort)
+        wait_flag((up ? pd.flags_down : pd.flags_up) + j, up ? band + 1 : pd.nb - band);
     }
     __syncthreads();
     if (s_abort) {
       cp_async_wait<0>();
       return;
     }
+    if (!early) {
+#pragma unroll
+      for (int r = 0; r < RING - 1; r++) issue_row(r);
+    }
 
     // lanes whose predecessor column lies outside the image start a path
     const uint32_t fl_keep = ((xlo - 1 >= 0) ? 0x0000ffffu : 0u) | ((xhi - 1 >= 0) ? 0xffff0000u : 0u);
     const uint32_t fr_keep = ((xlo + 1 < W) ? 0x0000ffffu : 0u) | ((xhi + 1 < W) ? 0xffff0000u : 0u);
-    const uint8_t* bsv = pd.bs + ((size_t)(((bi + 1) & 1)) * 3 + 0) * W * Dp;
+    // band-end states [order][parity][3][W][Dp]: each scan order of a merged
+    // launch has its own (a separate up launch reuses the down sweep's)
+    uint8_t* const bs0 = pd.bs + (MODE == kModeMerged && up ? (size_t)6 * W * Dp : 0);
+    const uint8_t* bsv = bs0 + ((size_t)(((bi + 1) & 1)) * 3 + 0) * W * Dp;
     const uint8_t* bsl = bsv + (size_t)W * Dp;
     const uint8_t* bsr = bsl + (size_t)W * Dp;
-    uint8_t* wsv = pd.bs + ((size_t)((bi & 1)) * 3 + 0) * W * Dp;
+    uint8_t* wsv = bs0 + ((size_t)((bi & 1)) * 3 + 0) * W * Dp;
     uint8_t* wsl = wsv + (size_t)W * Dp;
     uint8_t* wsr = wsl + (size_t)W * Dp;
 
@@ -683,8 +790,8 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     // winner-take-all + parabolic subpixel of row kk, done by halo threads
     // from the aggregated costs the owned threads left in shared memory
     auto select_row = [&](int kk) {
-      if (!HALO_SELECT || owned || !pd.dint) return;
-      const int yk = UP ? ytop + nrows - 1 - kk : ytop + kk;
+      if (!HALO_SELECT || owned || !pd.dint || !second) return;
+      const int yk = up ? ytop + nrows - 1 - kk : ytop + kk;
       const int ht = t - NO;
       constexpr int ST = SEL_T > 0 ? SEL_T : 1;
       const int c = ht / ST, sub = ht - c * ST;
@@ -714,6 +821,27 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
       }
 #pragma unroll
       for (int o = 1; o < SEL_T; o <<= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o, SEL_T > 0 ? SEL_T : 1));
+      // uniqueness: the smallest S two or more disparities away from d*
+      uint32_t s2 = 0xffffu;
+      if (a.unique && pd.dsub) {
+        const int dk = (int)(key & 255u);
+#pragma unroll
+        for (int j = 0; j < CPT; j++) {
+          const int qq = sub * CPT + j;
+#pragma unroll
+          for (int w = 0; w < G; w++) {
+            const uint4 v4 = srow[(kk & 1) * G * NO + w * NO + cpr * CHUNKS + qq];
+            const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+              const int d = qq * DC + 4 * w + e;
+              if (d < D && (d + 1 < dk || d > dk + 1)) s2 = min(s2, (vv[e] >> (16 * cl)) & 0xffffu);
+            }
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < SEL_T; o <<= 1) s2 = min(s2, __shfl_xor_sync(0xffffffffu, s2, o, SEL_T > 0 ? SEL_T : 1));
+      }
       if (sub == 0 && x < W) {
         const int ds = (int)(key & 255u);
         const int sv = (int)(key >> 8);
@@ -723,6 +851,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
           const int bp = (int)s_at(ds + 1) - sv;
           v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
         }
+        if (100 * (int)s2 < (100 + a.unique) * sv) v = __int_as_float(0x7fc00000);   // not unique
         pd.dint[(size_t)yk * W + x] = (int16_t)ds;
         if (pd.dsub) pd.dsub[(size_t)yk * W + x] = v;
       }
@@ -741,7 +870,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     };
 
     for (int k = 0; k < nrows; k++) {
-      const int y = UP ? ytop + nrows - 1 - k : ytop + k;
+      const int y = up ? ytop + nrows - 1 - k : ytop + k;
       issue_row(k + RING - 1);
       cp_async_wait<RING - 1>();
       {
@@ -755,6 +884,26 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
       }
       const int par = k & 1;
       const bool more = k + 1 < nrows;
+      // adaptive P2 of the step into row y, per path (the predecessor is
+      // (x, y-1) / (x-1, y-1) / (x+1, y-1) going down, y+1 going up), both
+      // lanes; columns and rows are clamped into the image: a lane whose
+      // predecessor is outside restarts and ignores its penalty
+      uint32_t p2v = p2x2, p2f = p2x2, p2r = p2x2;
+      if (pd.guide) {
+        const int yq = min(max(up ? y + 1 : y - 1, 0), H - 1);
+        const uint8_t* gc = pd.guide + (size_t)y * pd.gpitch;
+        const uint8_t* gq = pd.guide + (size_t)yq * pd.gpitch;
+        const int cl = min(max(xlo, 0), W - 1), ch = min(max(xhi, 0), W - 1);
+        const uint32_t il = __ldg(gc + cl), ih = __ldg(gc + ch);
+        auto pen = [&](int dx) {
+          const uint32_t ql = __ldg(gq + min(max(xlo + dx, 0), W - 1));
+          const uint32_t qh = __ldg(gq + min(max(xhi + dx, 0), W - 1));
+          return (uint32_t)s_lut[absdiff_u8(il, ql)] | ((uint32_t)s_lut[absdiff_u8(ih, qh)] << 16);
+        };
+        if (role == 0) p2v = pen(0);
+        if (role != 2) p2f = pen(-1);
+        if (role != 1) p2r = pen(+1);
+      }
       if (role == 0) {
         // ---- owned pairs: all three paths ----
         uint32_t Nv[DC], Nf[DC], Nr[DC];
@@ -762,9 +911,9 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
         neighbours(Lv, lv, rv);
         neighbours(Lf, lf, rf);
         neighbours(Lr, lr, rr);
-        sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2x2, Nv);
-        sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
-        sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+        sgm_update<DC>(Lv, Cc, lv, rv, mv, p1x2, p2v, Nv);
+        sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2f, Nf);
+        sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2r, Nr);
         mv = group_min2<CHUNKS>(tree_min<DC>(Nv), role_mask);
         mf = group_min2<CHUNKS>(tree_min<DC>(Nf), role_mask);
         mr = group_min2<CHUNKS>(tree_min<DC>(Nr), role_mask);
@@ -787,7 +936,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
           for (int i = 0; i < DC; i++)
             S[i] = (en_v ? Nv[i] : 0u) + (en_fl ? Nf[i] : 0u) + (en_fr ? Nr[i] : 0u);
         }
-        if (!UP) {
+        if (!Cfg::SEC || !second) {
           store_u4<DC>(sd_out + (size_t)y * sd_row, 1, S);
         } else {
           // add the down sweep and the horizontal paths
@@ -844,6 +993,20 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
               first = (first & ~eq) | (d2 & eq);
             }
             const uint32_t dstar2 = group_min2<CHUNKS>(first, role_mask);
+            // uniqueness: per lane, the smallest S two or more disparities
+            // away from that lane's d* (0xffff: none)
+            uint32_t s2x2 = 0xffffffffu;
+            if (a.unique && pd.dsub) {
+              const int dl = (int)(dstar2 & 0xffffu), dh = (int)(dstar2 >> 16);
+#pragma unroll
+              for (int i = 0; i < DC; i++) {
+                const int d = d0 + i;
+                const uint32_t ex = ((d >= dl - 1 && d <= dl + 1) ? 0x0000ffffu : 0u) |
+                                    ((d >= dh - 1 && d <= dh + 1) ? 0xffff0000u : 0u);
+                s2x2 = vmin2(s2x2, S[i] | ex);
+              }
+              s2x2 = group_min2<CHUNKS>(s2x2, role_mask);
+            }
             // S(d*-1) and S(d*+1) through shared memory, [group][thread];
             // chunk 0 finishes the low lane's column, chunk 1 the high one
             store_u4<DC>(srow + t, NO, S);
@@ -866,6 +1029,8 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
                   const int bp = (int)s_at(ds + 1) - sv;
                   v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
                 }
+                if (100 * (int)((s2x2 >> sh) & 0xffffu) < (100 + a.unique) * (int)((gmin >> sh) & 0xffffu))
+                  v = __int_as_float(0x7fc00000);   // not unique
                 pd.dint[(size_t)y * W + x] = (int16_t)ds;
                 if (pd.dsub) pd.dsub[(size_t)y * W + x] = v;
               }
@@ -897,7 +1062,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
           neighbours(Lf, lf, rf);
           const bool act = hh + HH >= k;
           if (act) {
-            sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2x2, Nf);
+            sgm_update<DC>(Lf, Cc, lf, rf, mf, p1x2, p2f, Nf);
           } else {
 #pragma unroll
             for (int i = 0; i < DC; i++) Nf[i] = Lf[i];
@@ -914,7 +1079,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
           neighbours(Lr, lr, rr);
           const bool act = hh <= HALO - 1 - k;
           if (act) {
-            sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2x2, Nr);
+            sgm_update<DC>(Lr, Cc, lr, rr, mr, p1x2, p2r, Nr);
           } else {
 #pragma unroll
             for (int i = 0; i < DC; i++) Nr[i] = Lr[i];
@@ -1071,7 +1236,7 @@ cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
 // ---- kernel shape choice (built-in rule, or a tuned override per D class) ----
 namespace {
 struct ShapeOverride {
-  int lo, hi, dc, halo;
+  int lo, hi, dc, halo, order;
 };
 ShapeOverride g_over[16];
 int g_nover = 0;
@@ -1090,6 +1255,7 @@ static Shape builtin_shape(int D) {
   s.dc = D > 128 ? 16 : 8;
   s.chunks = chunks_for(s.dc, D);
   s.halo = s.dc == 8 ? 16 : 8;
+  s.order = 0;
   return s;
 }
 
@@ -1107,6 +1273,7 @@ Shape shape_for(int D, bool tuned) {
       Shape s;
       s.dc = g_over[i].dc;
       s.halo = g_over[i].halo;
+      s.order = g_over[i].order;
       s.chunks = chunks_for(s.dc, D);
       return s;
     }
@@ -1114,7 +1281,7 @@ Shape shape_for(int D, bool tuned) {
   return builtin_shape(D);
 }
 
-int set_shape_override(int d_lo, int d_hi, int dc, int halo) {
+int set_shape_override(int d_lo, int d_hi, int dc, int halo, int order) {
   if (d_lo < 1 || d_hi > SF_MAX_DISPARITY || d_lo > d_hi) return 1;
   if (dc == 0) {   // drop overrides of this class
     int w = 0;
@@ -1123,17 +1290,18 @@ int set_shape_override(int d_lo, int d_hi, int dc, int halo) {
     g_nover = w;
     return 0;
   }
+  if (order != 0 && order != 1) return 1;
   for (int D = d_lo; D <= d_hi; D++)
     if (!shape_supported(dc, chunks_for(dc, D), halo)) return 1;
   if (g_nover == 16) return 1;
-  g_over[g_nover++] = {d_lo, d_hi, dc, halo};
+  g_over[g_nover++] = {d_lo, d_hi, dc, halo, order};
   return 0;
 }
 
-template <int DC, int CHUNKS, int HALO, bool UP>
+template <int DC, int CHUNKS, int HALO, int MODE>
 static cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
-  using Cfg = SweepCfg<DC, CHUNKS, HALO, UP>;
-  auto kern = sweep_kernel<DC, CHUNKS, HALO, UP>;
+  using Cfg = SweepCfg<DC, CHUNKS, HALO, MODE>;
+  auto kern = sweep_kernel<DC, CHUNKS, HALO, MODE>;
   const size_t smem = Cfg::smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1150,20 +1318,24 @@ static cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <bool UP>
+template <int MODE>
 static cudaError_t sweep_select(const SweepArgs& a, cudaStream_t s) {
   const Shape sh = shape_for(a.Dmax, a.builtin_shape == 0);
 #define SF_CASE(DC_, CH_, HA_) \
-  if (sh.dc == DC_ && sh.chunks == CH_ && sh.halo == HA_) return sweep_dispatch<DC_, CH_, HA_, UP>(a, s);
+  if (sh.dc == DC_ && sh.chunks == CH_ && sh.halo == HA_) return sweep_dispatch<DC_, CH_, HA_, MODE>(a, s);
   SF_SWEEP_SHAPES(SF_CASE)
 #undef SF_CASE
   return cudaErrorInvalidConfiguration;
 }
 
-cudaError_t launch_sweep(const SweepArgs& a, bool up, cudaStream_t s) {
+cudaError_t launch_sweep(const SweepArgs& a, int mode, cudaStream_t s) {
   StageTrace trace(SF_STAGE_SGM_SWEEP, s);
   count_launches(1);
-  return up ? sweep_select<true>(a, s) : sweep_select<false>(a, s);
+  switch (mode) {
+    case kModeDown: return sweep_select<kModeDown>(a, s);
+    case kModeUp: return sweep_select<kModeUp>(a, s);
+    default: return sweep_select<kModeMerged>(a, s);
+  }
 }
 
 }  // namespace fused

@@ -17,9 +17,10 @@ def lib():
 
 def test_apply_installs_every_class(lib):
     from paper_1801_04720_gb300 import autotune
-    res = {"classes": [{"lo": 33, "hi": 64, "dc": 8, "halo": 8},
-                       {"lo": 65, "hi": 128, "dc": 16, "halo": 16}]}
-    assert autotune.apply(res) == 2
+    res = {"classes": [{"lo": 33, "hi": 64, "dc": 8, "halo": 8, "order": 1},
+                       {"lo": 65, "hi": 128, "dc": 16, "halo": 16, "order": 0},
+                       {"lo": 129, "hi": 256, "dc": 16, "halo": 8}]}      # no order: 0
+    assert autotune.apply(res) == 3
     for c in res["classes"]:
         lib.sf_set_sweep_shape(c["lo"], c["hi"], 0, 0)
 
@@ -31,13 +32,25 @@ def test_unsupported_shapes_are_rejected(lib, lo, hi, dc, halo):
         lib.sf_set_sweep_shape(lo, hi, dc, halo)
 
 
+@pytest.mark.parametrize("order", [-1, 2, 7])
+def test_unknown_scheduling_orders_are_rejected(lib, order):
+    with pytest.raises(lib.SFError):
+        lib.sf_set_sweep_schedule(65, 128, 16, 8, order)
+
+
+def test_parse_key_round_trip():
+    from paper_1801_04720_gb300 import autotune
+    for dc, halo, order in autotune.CANDIDATES:
+        assert autotune.parse_key(f"{dc}x{halo}o{order}") == (dc, halo, order)
+
+
 def test_every_candidate_is_a_built_shape(lib):
     from paper_1801_04720_gb300 import autotune
     for lo, hi in autotune.DEFAULT_CLASSES:
         ok = 0
-        for dc, halo in autotune.CANDIDATES:
+        for dc, halo, order in autotune.CANDIDATES:
             try:
-                lib.sf_set_sweep_shape(lo, hi, dc, halo)
+                lib.sf_set_sweep_schedule(lo, hi, dc, halo, order)
                 ok += 1
             except lib.SFError:
                 pass
@@ -48,11 +61,16 @@ def test_every_candidate_is_a_built_shape(lib):
 def test_cache_is_keyed_by_gpu_and_size(tmp_path):
     from paper_1801_04720_gb300 import autotune
     path = tmp_path / "tune.json"
-    res = {"gpu": "GPU-A", "W": 1242, "H": 375, "classes": [{"lo": 65, "hi": 128, "dc": 8, "halo": 16}]}
+    res = {"gpu": "GPU-A", "W": 1242, "H": 375,
+           "classes": [{"lo": 65, "hi": 128, "dc": 8, "halo": 16, "order": 1}]}
     path.write_text(json.dumps(res))
     assert autotune.cached(str(path), "GPU-A", 1242, 375) == res
     assert autotune.cached(str(path), "GPU-B", 1242, 375) is None
     assert autotune.cached(str(path), "GPU-A", 640, 480) is None
     assert autotune.cached(str(tmp_path / "missing.json"), "GPU-A", 1242, 375) is None
+    # a cache written before the scheduling order was tuned is stale
+    old = {"gpu": "GPU-A", "W": 1242, "H": 375, "classes": [{"lo": 65, "hi": 128, "dc": 8, "halo": 16}]}
+    path.write_text(json.dumps(old))
+    assert autotune.cached(str(path), "GPU-A", 1242, 375) is None
     path.write_text("{not json")
     assert autotune.cached(str(path), "GPU-A", 1242, 375) is None

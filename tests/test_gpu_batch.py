@@ -116,13 +116,14 @@ def test_batch_rejects_bad_items(sf):
         sf.sf_batch_run(items, sf.params(), ws)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("dc,halo", [(8, 8), (16, 8), (16, 16), (8, 16)])
-def test_tuned_shapes_are_bit_identical(sf, dc, halo):
+def test_tuned_shapes_are_bit_identical(sf, dc, halo, order):
     quads = _quads([(130, 41, 64), (97, 40, 128)], seed0=40)
     base = [_scene(sf, q) for q in quads]
     ref = [sf.sf_scene_flow([s["left_t"], s["right_t"], s["left_t1"], s["right_t1"]], s["flow"],
                             sf.params(D=q.D), s["cam"]) for s, q in zip(base, quads)]
-    sf.sf_set_sweep_shape(33, 128, dc, halo)     # every provided shape covers this class
+    sf.sf_set_sweep_schedule(33, 128, dc, halo, order)   # every provided shape covers this class
     try:
         got = [sf.sf_scene_flow([s["left_t"], s["right_t"], s["left_t1"], s["right_t1"]], s["flow"],
                                 sf.params(D=q.D), s["cam"]) for s, q in zip(base, quads)]
@@ -132,3 +133,32 @@ def test_tuned_shapes_are_bit_identical(sf, dc, halo):
         for k in ("valid", "D0", "D1", "s4"):
             x, y = to_np(a[k]), to_np(b[k])
             assert np.array_equal(np.nan_to_num(x, nan=-9.0), np.nan_to_num(y, nan=-9.0)), k
+
+
+def _oracle_item(args):
+    from oracle import oracle
+    q = args
+    c = q.camera
+    return oracle.scene_flow(q.images(), q.flow, c.f, c.B, c.cx, c.cy, D=q.D)
+
+
+def test_graph_replayed_mixed_batch_every_item_against_oracle(sf):
+    """A batch mixing D = 16, 64 and 192 (three kernel shapes, three sweep
+    launches) and a row too wide for one CTA's distance band, replayed from
+    its CUDA graph three times: every item's D0, D1, validity, S4, motion and
+    point against the oracle's whole path, element by element (integers and
+    masks exact, subpixel within 1e-4 px, scene flow within 1e-5 relative)."""
+    import multiprocessing as mp
+    from gpu_helpers import assert_sceneflow_close
+    quads = _quads([(96, 64, 16), (130, 41, 64), (200, 30, 192), (1242, 12, 192), (67, 53, 64)], seed0=90)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(quads)) as pool:
+        refs = pool.map(_oracle_item, quads)
+    outs = _compare(sf, quads, graph=True, repeats=3)
+    sf.sf_batch_release_graphs()
+    for q, o, r in zip(quads, outs, refs):
+        assert_nan_equal_close(to_np(o["D0"]), r["t0"]["disp"], SUBPIXEL_ATOL, f"D0 D={q.D}")
+        assert_nan_equal_close(to_np(o["D1"]), r["t1"]["disp"], SUBPIXEL_ATOL, f"D1 D={q.D}")
+        got = {k: to_np(o[k]) for k in ("s4", "motion", "point", "valid")}
+        assert_sceneflow_close(got, r["s4"], r["motion"], r["point"], r["valid"])
+        assert r["valid"].sum() > 0

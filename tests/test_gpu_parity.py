@@ -86,6 +86,33 @@ def test_aggregate_random_cost(sf, oracle_mod, W, H, D, P1, P2, mask, staged):
     assert np.array_equal(got.astype(np.int32), exp)
 
 
+# Heights giving one band, two bands, an odd and an even band count at both
+# halo widths (bands of 9 or 17 rows), so the meeting band of the merged
+# launch falls on every kind of boundary.
+ORDER_CASES = [(70, 5, 32), (70, 9, 32), (70, 17, 64), (70, 18, 64), (130, 41, 128), (96, 52, 48),
+               (61, 35, 16), (200, 64, 256)]
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("dc,halo", [(16, 8), (16, 16), (8, 8), (8, 16)])
+@pytest.mark.parametrize("W,H,D", ORDER_CASES)
+def test_aggregate_every_schedule_against_oracle(sf, oracle_mod, W, H, D, dc, halo, order):
+    """The fused band sweeps under each path-scheduling order and shape:
+    the full aggregated cost S against the oracle, bit for bit."""
+    rng = np.random.default_rng(W * 7 + H * 3 + D)
+    C = rng.integers(0, 63, size=(H, W, D), dtype=np.uint8)
+    p = sf.params(D=D)
+    try:
+        sf.sf_set_sweep_schedule(D, D, dc, halo, order)
+    except sf.SFError:
+        pytest.skip("shape not built for this D")
+    try:
+        got = to_np(sf.sf_sgm_aggregate(to_dev(C), p), np.uint16)
+    finally:
+        sf.sf_set_sweep_shape(D, D, 0, 0)
+    assert np.array_equal(got.astype(np.int32), oracle_mod.aggregate(C, 7, 86, 0xFF))
+
+
 def test_aggregate_real_cost(sf, oracle_mod):
     q = synth.fronto_planes()
     C = oracle_mod.cost_volume(oracle_mod.census(q.left_t), oracle_mod.census(q.right_t), 16)
