@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--stream", type=int, default=2,
                     help="frames of the 2048x1024, D=256 stream recipe to time (0 = skip)")
     ap.add_argument("--shape", default=None,
-                    help="sweep shape DCxHALO for the frame's disparity class instead of the "
-                         "autotuner (e.g. 16x16, as in profiling runs)")
+                    help="sweep schedule for the frame's disparity class instead of the "
+                         "autotuner: DCxHALO (two launches, e.g. 16x16) or DCxHALOoORDER "
+                         "(e.g. 16x8o1: both scan orders in one launch), as in profiling runs")
     ap.add_argument("--profile", action="store_true",
                     help="short run for ncu: no clock-sampling load phase, no e2e, no CPU baseline")
     args = ap.parse_args()
@@ -150,18 +151,20 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def bytes_model(stage, N, D, passes=4):
+def bytes_model(stage, N, D, passes=4, order=1):
     """Algorithmic HBM bytes per launch of the dominant stage.
 
     sgm_sweep: the eight paths run in opposite scan orders, so the partial sum
     of the paths of one order must exist for every (p, d) when the opposite
-    sweep reaches p: per SGM pass it is written once (uint16, 2*N*D bytes) by
-    the down sweep and read once by the up sweep.  One sweep launch covers the
-    four passes of a frame -> 4 * 2*N*D bytes.
+    order reaches p: per SGM pass it is written once and read once (uint16,
+    2*N*D bytes each way).  One launch covers the four passes of a frame.
+    With both scan orders in one launch (order 1) that launch does the write
+    and the read -> 4 * 4*N*D bytes; with one launch per order (order 0) each
+    does one of them -> 4 * 2*N*D bytes.
     aggregate (staged kernels): read the uint8 cost and write the uint16 sum
     once per pass -> 3*N*D bytes."""
     if stage == "sgm_sweep":
-        return passes * 2 * N * D
+        return passes * (4 if order == 1 else 2) * N * D
     return 3 * N * D
 
 
@@ -210,12 +213,16 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     tuned = None
     if args.shape:
-        dc, halo = (int(v) for v in args.shape.lower().split("x"))
-        _lib.sf_set_sweep_shape(65, 128, dc, halo)
-        tuned = {"classes": [{"lo": 65, "hi": 128, "dc": dc, "halo": halo, "forced": True}]}
+        # DCxHALO (two launches) or DCxHALOoORDER
+        spec = args.shape.lower()
+        order = int(spec.split("o")[1]) if "o" in spec else 0
+        dc, halo = (int(v) for v in spec.split("o")[0].split("x"))
+        _lib.sf_set_sweep_schedule(65, 128, dc, halo, order)
+        tuned = {"classes": [{"lo": 65, "hi": 128, "dc": dc, "halo": halo, "order": order, "forced": True}]}
     elif not args.no_autotune:
         from paper_1801_04720_gb300 import autotune
-        tuned = autotune.load_or_tune(W=W_IMG, H=H_IMG, classes=[(65, 128)])
+        # every class of disparity counts the batch uses (64, 128, 192)
+        tuned = autotune.load_or_tune(W=W_IMG, H=H_IMG, classes=[(33, 64), (65, 128), (129, 256)])
     q = synth.automotive(seed=args.seed + rank)
     H, W = q.shape
     N = W * H
@@ -279,13 +286,15 @@ def run_ours(args, world, rank, local):
     dominant = max(stage_tot, key=stage_tot.get)
     dom_ms = statistics.mean(stages[dominant])
     hbm_peak, peak_kind = peaks()
-    algo_bytes = bytes_model(dominant, N, D_MAX)
+    cls = [c for c in (tuned or {}).get("classes", []) if c["lo"] <= D_MAX <= c["hi"]]
+    if cls:
+        order = cls[0].get("order", 0)
+        shape_now = f'{cls[0]["dc"]}x{cls[0]["halo"]}o{order}'
+    else:
+        order = 1
+        shape_now = "16x8o1"   # built-in rule for D = 128
+    algo_bytes = bytes_model(dominant, N, D_MAX, order=order)
     achieved = algo_bytes / (dom_ms * 1e-3) / 1e9
-    shape_now = None
-    if tuned and tuned.get("classes"):
-        shape_now = f'{tuned["classes"][0]["dc"]}x{tuned["classes"][0]["halo"]}'
-    elif args.no_autotune:
-        shape_now = "8x16"   # built-in rule for D = 128
     traffic = measured_traffic(dominant, shape_now)
 
     e2e = None
@@ -366,15 +375,19 @@ def run_ours(args, world, rank, local):
     from paper_1801_04720_gb300 import evaluate
     step()
     torch.cuda.synchronize()
-    s4_h, valid_h, flow_h = out["s4"].cpu(), out["valid"].cpu(), flow.cpu()
+    s4_h, valid_h = out["s4"].cpu(), out["valid"].cpu()
     result["accuracy_vs_ground_truth"] = {
         "rule": "outlier: error > 3 px and > 5 % of the true value; rates over the kept pixels",
         "plain": {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
             s4_h, valid_h, q.gt_disp0, q.gt_disp1, q.gt_flow).items()},
-        "plain_dense": {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy_dense(
-            s4_h, flow_h, q.gt_disp0, q.gt_disp1, q.gt_flow).items()},
-        "dense": "d0 and d1 filled by background interpolation (evaluate.fill_background), "
-                 "(u, v) from the input flow"}
+        "dense": "d0 and d1 filled by the densification kernels (sf_densify_sceneflow): the "
+                 "background fill (the benchmark's reading) or the edge-aware fill guided by the left "
+                 "image, (u, v) from the input flow, back-projected at every pixel"}
+    for mode, tag in ((0, "plain_dense"), (1, "plain_dense_edge_aware")):
+        dn = _lib.sf_densify_sceneflow(out["s4"], flow, cam, guide=imgs[0], mode=mode, stream=stream)
+        torch.cuda.synchronize()
+        result["accuracy_vs_ground_truth"][tag] = {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
+            dn["s4"].cpu(), dn["valid"].cpu(), q.gt_disp0, q.gt_disp1, q.gt_flow).items()}
     if args.batch > 0:
         result["batch"] = run_batch(args, dev, _lib, synth, torch)
     if args.learned_eval >= 0:
@@ -401,32 +414,48 @@ def run_batch(args, dev, _lib, synth, torch):
         outs.append(_lib.alloc_scene_flow_outputs(q.shape[1], q.shape[0], dev))
     items = _lib.make_batch(scenes, outs)
     p = _lib.params()
-    ws = torch.empty(_lib.sf_batch_workspace_size(items, p), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    for _ in range(max(2, args.warmup)):
-        _lib.sf_batch_run(items, p, ws, graph=True, stream=stream)
-    torch.cuda.synchronize()
     steps = max(3, min(args.steps, 10))
-    ms = []
-    for k in range(steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _lib.sf_batch_run(items, p, ws, graph=True, stream=stream)
-            e1.record(stream)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    _lib.sf_batch_release_graphs()
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    mean = max_over_ranks(statistics.mean(ms), world, dev)
+
+    def measure(limit):
+        """quadruples/s and workspace bytes with the batch in waves of at most
+        `limit` bytes of buffers (0: one wave)."""
+        _lib.sf_set_batch_wave_limit(limit)
+        ws = torch.empty(_lib.sf_batch_workspace_size(items, p), dtype=torch.uint8, device=dev)
+        for _ in range(max(2, args.warmup)):
+            _lib.sf_batch_run(items, p, ws, graph=True, stream=stream)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _lib.sf_batch_run(items, p, ws, graph=True, stream=stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        _lib.sf_batch_release_graphs()
+        n = ws.numel()
+        del ws
+        torch.cuda.empty_cache()
+        return max_over_ranks(statistics.mean(ms), world, dev), n
+
+    mean, ws_all = measure(0)
+    wave_limit = 8 << 30
+    mean_w, ws_w = measure(wave_limit)
+    _lib.sf_set_batch_wave_limit(0)
     pixels = sum(q.shape[0] * q.shape[1] for q in quads)
     return {"metric": "scene-flow quadruples/s, uneven batch",
             "value": round(replica_rate(mean, world, len(quads)), 2),
             "unit": "quadruples/s", "items": len(quads), "ms_per_step": round(mean, 3),
             "megapixels_per_step": round(pixels / 1e6, 3),
-            "workspace_gb": round(ws.numel() / 1e9, 2), "graph": True,
+            "workspace_gb": round(ws_all / 1e9, 2), "graph": True,
+            "waves": {"limit_gb": round(wave_limit / 1e9, 2), "workspace_gb": round(ws_w / 1e9, 2),
+                      "value": round(replica_rate(mean_w, world, len(quads)), 2), "unit": "quadruples/s",
+                      "ms_per_step": round(mean_w, 3)},
             "sizes": sorted({f"{q.shape[1]}x{q.shape[0]}/D{q.D}" for q in quads})}
 
 
@@ -535,109 +564,324 @@ def run_learned(args, dev, _lib, torch, q, imgs, flow, p, cam, flush, plain_fps)
     return res
 
 
-def _stream_frame(k):
+STREAM_K = 32            # consecutive frames of the large-stream sequence
+STREAM_SEED = 5
+
+
+def _stream_frames(frames):
+    """Worker: frames of the large-stream sequence (the scene depends on the
+    seed alone, so any subset renders on its own)."""
     from paper_1801_04720_gb300 import synth
-    return synth.automotive(seed=k, W=2048, H=1024, D=256, n_segments=40)
+    sq = synth.sequence(STREAM_K, seed=STREAM_SEED, W=2048, H=1024, D=256, n_segments=40, frames=frames)
+    last = STREAM_K - 1
+    return [(k, sq.lefts[k], sq.rights[k], sq.flows[k] if k < last else None, sq.gt_disp[k],
+             sq.gt_flow[k] if k < last else None, sq.gt_next_disp[k] if k < last else None)
+            for k in frames], sq.camera
+
+
+def _oracle_sgm_pass(task):
+    """Worker: one SGM pass of the oracle (census, cost, eight paths, selection)."""
+    from oracle import oracle
+    ref, oth, is_right, D = task
+    return oracle.sgm_pass(oracle.census(ref), oracle.census(oth), D, 7, 86, is_right, 62,
+                           subpixel=not is_right)
+
+
+def _mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+def sequence_bytes_model(N, D):
+    """Algorithmic HBM bytes per frame of a sequence in which every stereo
+    frame's SGM runs once: its two passes' partial sums written and read
+    (2 x 4 N D), its two images in (2 N), census strings written and read
+    (2 x 8 N x 2), the winners of both passes written and read (8 N), its
+    disparity map written once and read by two combinations (12 N), one flow
+    in (8 N) and one step's s4 and validity out (17 N)."""
+    return 8 * N * D + 2 * N + 32 * N + 8 * N + 12 * N + 8 * N + 17 * N
 
 
 def run_stream(args, dev, _lib, torch, flush):
-    """The large-stream configuration: 2048x1024 quadruples, D = 256 (40
-    moving segments), plain path per frame and the learned path two frames
-    per launch, the plain check judging the learned one.  The frames are
-    rendered on the host in spawned workers; each timed step reuses them."""
+    """The large-stream configuration: 32 consecutive 2048x1024 stereo frames
+    (D = 256) of one driving scene with 40 moving segments, through the
+    sequence call (every frame's SGM once, a scene-flow step per consecutive
+    pair) with the plain left-right check and with learned confidence (four
+    left passes per launch), the plain check judging the learned one, and the
+    oracle on frames 0 and 1 (host workers, beside the GPU timing)."""
     import multiprocessing as mp
-    from paper_1801_04720_gb300 import train_confnet
-    n = max(2, args.stream - args.stream % 2)
-    with mp.get_context("spawn").Pool(min(n, 8)) as pool:
-        frames = pool.map(_stream_frame, range(n))
-    H, W = frames[0].shape
-    D = frames[0].D
+    from oracle import oracle
+    from paper_1801_04720_gb300 import evaluate, train_confnet
+    oracle.build()
+    K = STREAM_K
+    D = 256
+    cores = max(1, os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    t_render = time.perf_counter()
+    with ctx.Pool(min(cores, 16)) as pool:
+        parts = pool.map(_stream_frames, [list(range(i, K, min(cores, 16))) for i in range(min(cores, 16))])
+    t_render = time.perf_counter() - t_render
+    cam_h = parts[0][1]
+    fr = {}
+    for lst, _ in parts:
+        for k, l_, r_, f_, gd, gf, gn in lst:
+            fr[k] = (l_, r_, f_, gd, gf, gn)
+    H, W = fr[0][0].shape
+    N = W * H
+    # the oracle on frames 0 and 1 (four SGM passes) in spawned workers while
+    # the GPU is timed; each pass holds about 5 GB of host memory
+    n_or = int(min(4, max(0, _mem_available_gb() // 6)))
+    or_pool = ctx.Pool(n_or) if n_or else None
+    or_async = None
+    if or_pool is not None:
+        tasks = []
+        for k in (0, 1):
+            l_, r_ = fr[k][0], fr[k][1]
+            tasks += [(l_, r_, False, D), (r_, l_, True, D)]
+        or_async = or_pool.map_async(_oracle_sgm_pass, tasks)
     p = _lib.params(D=D)
-    cam = _lib.camera(frames[0].camera.f, frames[0].camera.B, frames[0].camera.cx, frames[0].camera.cy)
-    dimgs = [[torch.from_numpy(im).to(dev) for im in q.images()] for q in frames]
-    dflow = [torch.from_numpy(q.flow).to(dev) for q in frames]
-    ws = _lib.workspace(W, H, p, dev)
-    out = _lib.alloc_scene_flow_outputs(W, H, dev)
+    cam = _lib.camera(cam_h.f, cam_h.B, cam_h.cx, cam_h.cy)
+    L = [torch.from_numpy(fr[k][0]).to(dev) for k in range(K)]
+    R = [torch.from_numpy(fr[k][1]).to(dev) for k in range(K)]
+    F = [torch.from_numpy(fr[k][2]).to(dev) for k in range(K - 1)]
     stream = torch.cuda.current_stream()
-    steps = max(3, min(args.steps, 8))
+    theta, meta = train_confnet.load()
+    packed = _lib.confnet_pack(torch.from_numpy(theta).to(dev))
+    thr = float(meta["threshold"])
+    ws_p = torch.empty(_lib.load().sf_sequence_workspace_size(W, H, __import__("ctypes").byref(p), K, 0),
+                       dtype=torch.uint8, device=dev)
+    ws_l = torch.empty(_lib.load().sf_sequence_workspace_size(W, H, __import__("ctypes").byref(p), K, 1),
+                       dtype=torch.uint8, device=dev)
+    steps = max(3, min(args.steps, 5))
 
-    def timed(fn, k_of):
-        for k in range(2):
-            fn(k_of(k))
+    def timed(fn):
+        out = fn()
         torch.cuda.synchronize()
         ms = []
         for k in range(steps):
             flush.fill_(k & 0xFF)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fn(k_of(k))
+            out = fn()
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
-        return statistics.mean(ms)
+        return statistics.mean(ms), out
 
-    ms_plain = timed(lambda k: _lib.sf_scene_flow(dimgs[k], dflow[k], p, cam, ws=ws, out=out, stream=stream),
-                     lambda k: k % n)
-    theta, meta = train_confnet.load()
-    packed = _lib.confnet_pack(torch.from_numpy(theta).to(dev))
-    thr = float(meta["threshold"])
-    ws2 = _lib.learned_workspace(W, H, p, 4, dev)
-    outs2 = [_lib.alloc_scene_flow_outputs(W, H, dev) for _ in range(2)]
-    ms_learned = timed(lambda k: _lib.sf_scene_flow_learned_frames(
-        [(dimgs[2 * k], dflow[2 * k]), (dimgs[2 * k + 1], dflow[2 * k + 1])], p, cam, packed, thr,
-        ws=ws2, outs=outs2, stream=stream), lambda k: k % (n // 2))
+    out_p = _lib.alloc_sequence_outputs(K, W, H, dev)
+    out_l = _lib.alloc_sequence_outputs(K, W, H, dev)
+    ms_plain, _ = timed(lambda: _lib.sf_sequence_sceneflow(L, R, F, p, cam, ws=ws_p, out=out_p, stream=stream))
+    ms_learn, _ = timed(lambda: _lib.sf_sequence_sceneflow(L, R, F, p, cam, packed=packed, threshold=thr,
+                                                           ws=ws_l, out=out_l, stream=stream))
+    # the plain check judges the learned rule on every frame
     dec, dp, dl, gts = [], [], [], []
     ws1 = _lib.learned_workspace(W, H, p, 1, dev)
-    for k in range(n):
-        plain = _lib.sf_sgm_full(dimgs[k][0], dimgs[k][1], p, ws=ws)
-        lo = _lib.sf_sgm_learned(dimgs[k][0], dimgs[k][1], p, packed=packed, threshold=thr, ws=ws1)
+    wsf = _lib.workspace(W, H, p, dev)
+    for k in range(K):
+        plain = _lib.sf_sgm_full(L[k], R[k], p, ws=wsf)
+        lo = _lib.sf_sgm_learned(L[k], R[k], p, packed=packed, threshold=thr, ws=ws1, features=False)
         dec.append((lo["prob"], lo["dint"], plain["valid"]))
-        dp.append(plain["disp"])
-        dl.append(lo["disp"])
-        gts.append(torch.from_numpy(frames[k].gt_disp0).to(dev))
+        dp.append(out_p["disp"][k])
+        dl.append(out_l["disp"][k])
+        gts.append(torch.from_numpy(fr[k][3]).to(dev))
     rates = train_confnet.rates(dec, thr)
     vs_gt = {"plain_check": train_confnet.accuracy(dp, gts), "learned": train_confnet.accuracy(dl, gts)}
-    # KITTI-style scene-flow accuracy of frame 0 on both paths
-    from paper_1801_04720_gb300 import evaluate
-    _lib.sf_scene_flow(dimgs[0], dflow[0], p, cam, ws=ws, out=out, stream=stream)
-    _lib.sf_scene_flow_learned_frames([(dimgs[0], dflow[0]), (dimgs[1], dflow[1])], p, cam, packed, thr,
-                                      ws=ws2, outs=outs2, stream=stream)
-    torch.cuda.synchronize()
-    f0 = frames[0]
-    sf_acc = {name: {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
-        o["s4"].cpu(), o["valid"].cpu(), f0.gt_disp0, f0.gt_disp1, f0.gt_flow).items()}
-        for name, o in (("plain", out), ("learned", outs2[0]))}
-    sf_acc["plain_dense"] = {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy_dense(
-        out["s4"].cpu(), dflow[0].cpu(), f0.gt_disp0, f0.gt_disp1, f0.gt_flow).items()}
-    N = W * H
-    return {"workload": f"automotive stream {W}x{H} D={D}, 40 moving segments, {n} frames rendered",
-            "plain": {"value": round(1000.0 / ms_plain, 2), "unit": "frames/s", "ms_per_step": round(ms_plain, 3),
-                      "Gcost_entries_per_s": round(4 * N * D / (ms_plain * 1e-3) / 1e9, 1),
-                      "hbm": {"model_bytes_per_frame": frame_bytes_model(N, D),
-                              "achieved_gbs": round(frame_bytes_model(N, D) / (ms_plain * 1e-3) / 1e9, 1),
+    # scene-flow accuracy of step 0 (frames 0 -> 1), sparse and densified by the kernels
+    acc = {}
+    for name, o in (("plain", out_p), ("learned", out_l)):
+        s4, va = o["s4"][0], o["valid"][0]
+        acc[name] = {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
+            s4.cpu(), va.cpu(), fr[0][3], fr[0][5], fr[0][4]).items()}
+        for mode, tag in ((0, "dense_background"), (1, "dense_edge_aware")):
+            dn = _lib.sf_densify_sceneflow(s4, F[0], cam, guide=L[0], mode=mode)
+            acc[f"{name}_{tag}"] = {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
+                dn["s4"].cpu(), dn["valid"].cpu(), fr[0][3], fr[0][5], fr[0][4]).items()}
+    # the oracle on frames 0 and 1
+    parity = {"frames": [0, 1], "unavailable": "not enough host memory for the oracle workers"}
+    if or_async is not None:
+        t_or = time.perf_counter()
+        res = or_async.get()
+        or_pool.close()
+        or_pool.join()
+        disp_o = []
+        for f in (0, 1):
+            (dL, dLs), (dR, _) = res[2 * f], res[2 * f + 1]
+            disp_o.append(oracle.lr_check(dL, dR, dLs, 1)[1])
+        s4o, _, _, vo = oracle.combine(disp_o[0], disp_o[1], fr[0][2], cam_h.f, cam_h.B, cam_h.cx, cam_h.cy)
+        parity = {"frames": [0, 1], "oracle_workers": n_or, "oracle_wait_s": round(time.perf_counter() - t_or, 1)}
+        for f in (0, 1):
+            g = out_p["disp"][f].cpu().numpy()
+            o = disp_o[f]
+            parity[f"frame{f}_validity_mismatches"] = int((np.isnan(g) != np.isnan(o)).sum())
+            m = ~np.isnan(o) & ~np.isnan(g)
+            parity[f"frame{f}_max_subpixel_err_px"] = float(np.abs(g[m] - o[m]).max()) if m.any() else 0.0
+        gv = out_p["valid"][0].cpu().numpy()
+        gs = out_p["s4"][0].cpu().numpy()
+        parity["step0_validity_mismatches"] = int((gv != vo).sum())
+        m = (vo == 1) & (gv == 1)
+        rel = np.abs(gs[m].astype(np.float64) - s4o[m]) / np.maximum(np.abs(s4o[m]), 1e-30)
+        parity["step0_s4_max_rel_err"] = float(rel.max()) if m.any() else 0.0
+    steps_s = (K - 1) * 1000.0 / ms_plain
+    bpf = sequence_bytes_model(N, D)
+    return {"workload": f"automotive sequence {W}x{H} D={D}, 40 moving segments, {K} consecutive frames "
+                        f"(a scene-flow step per consecutive pair)",
+            "render_s": round(t_render, 1),
+            "plain": {"value": round(steps_s, 2), "unit": "scene-flow frames/s", "ms_per_sequence": round(ms_plain, 3),
+                      "stereo_frames_per_s": round(K * 1000.0 / ms_plain, 2),
+                      "hbm": {"model_bytes_per_frame": bpf,
+                              "achieved_gbs": round(bpf * K / (ms_plain * 1e-3) / 1e9, 1),
                               "peak_gbs": peaks()[0],
-                              "frac": round(frame_bytes_model(N, D) / (ms_plain * 1e-3) / 1e9 / peaks()[0], 4),
-                              "model": "frame_bytes_model: 16 N D + 149 N"}},
-            "learned_two_frames_per_launch": {"value": round(2000.0 / ms_learned, 2), "unit": "frames/s",
-                                              "ms_per_step": round(ms_learned, 3)},
+                              "frac": round(bpf * K / (ms_plain * 1e-3) / 1e9 / peaks()[0], 4),
+                              "model": "sequence_bytes_model: 8 N D + 87 N per stereo frame"}},
+            "learned": {"value": round((K - 1) * 1000.0 / ms_learn, 2), "unit": "scene-flow frames/s",
+                        "ms_per_sequence": round(ms_learn, 3), "vs_plain": round(ms_plain / ms_learn, 3),
+                        "passes_per_launch": 4},
             "learned_vs_plain_check": {k: round(v, 5) for k, v in rates.items()},
             "vs_ground_truth": {k: {kk: round(vv, 5) for kk, vv in v.items()} for k, v in vs_gt.items()},
-            "scene_flow_accuracy_frame0": sf_acc,
-            "parity": "frame 0 of this recipe against the oracle in tests/test_gpu_fullsize.py "
-                      "(integers bit-exact); the oracle is not timed here"}
+            "scene_flow_accuracy_step0": acc,
+            "oracle_parity": parity}
 
 
 def cpu_baseline(q):
-    """The oracle as it stands on one full frame (single thread)."""
+    """The oracle as it stands on one full frame (single thread), and the
+    same frame with the oracle's functions spread over every host core."""
     from oracle import oracle
     oracle.build()
     t0 = time.perf_counter()
     oracle.scene_flow(q.images(), q.flow, q.camera.f, q.camera.B, q.camera.cx, q.camera.cy,
                       D=D_MAX)
     dt = time.perf_counter() - t0
-    return {"value": round(1.0 / dt, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": "one full 1242x375 D=128 frame (4 SGM passes + combination), 1 thread",
-            "seconds": round(dt, 2)}
+    out = {"value": round(1.0 / dt, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+           "sample": "one full 1242x375 D=128 frame (4 SGM passes + combination), 1 thread",
+           "seconds": round(dt, 2), "cpu_model": cpu_model()}
+    try:
+        out["all_cores"] = cpu_baseline_all_cores(q)
+    except (OSError, RuntimeError, ValueError) as e:       # e.g. no shared memory on the host
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
+
+
+def cpu_model():
+    """The host CPU's model name (x86 'model name', else lscpu's 'Model name')."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+# ---- all-cores oracle: the oracle's own functions over independent units ----
+# A frame is four SGM passes; each pass is a cost volume and eight path
+# aggregations that do not depend on one another.  Phase 1 computes the four
+# cost volumes (one task each), phase 2 the 32 (pass, direction) paths, each
+# adding its L_r into its pass's sum in shared memory under that pass's lock;
+# the selection, checks and combination then run in the parent.
+_SHM = {}
+
+
+def _shm_array(name, shape, dtype):
+    from multiprocessing import shared_memory
+    if name not in _SHM:
+        _SHM[name] = shared_memory.SharedMemory(name=name)
+    return np.ndarray(shape, dtype=dtype, buffer=_SHM[name].buf)
+
+
+def _ac_init(locks):
+    global _AC_LOCKS
+    _AC_LOCKS = locks
+
+
+def _ac_cost(task):
+    from oracle import oracle
+    k, ref, oth, is_right, D, names, shape = task
+    C = oracle.cost_volume(oracle.census(ref), oracle.census(oth), D, is_right, 62)
+    _shm_array(names["cost"][k], shape, np.uint8)[...] = C
+    return k
+
+
+def _ac_path(task):
+    from oracle import oracle
+    k, r, names, shape = task
+    C = _shm_array(names["cost"][k], shape, np.uint8)
+    L = oracle.path_cost(C, 7, 86, r)
+    with _AC_LOCKS[k]:
+        _shm_array(names["sum"][k], shape, np.int32)[...] += L
+    return k
+
+
+def cpu_baseline_all_cores(q, cores=None, D=None, keep=None):
+    """The oracle on one full frame with its independent units spread over
+    every host core (spawned workers): frames/s and the cores used.  `keep`
+    (a dict) receives the frame's combination outputs."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    from oracle import oracle
+    oracle.build()
+    cores = cores or os.cpu_count() or 1
+    H, W = q.shape
+    D = D or D_MAX
+    shape = (H, W, D)
+    imgs = q.images()
+    passes = [(imgs[0], imgs[1], False), (imgs[1], imgs[0], True), (imgs[2], imgs[3], False),
+              (imgs[3], imgs[2], True)]
+    blocks, names = [], {"cost": [], "sum": []}
+    try:
+        for k in range(4):
+            c = shared_memory.SharedMemory(create=True, size=H * W * D)
+            s_ = shared_memory.SharedMemory(create=True, size=H * W * D * 4)
+            blocks += [c, s_]
+            names["cost"].append(c.name)
+            names["sum"].append(s_.name)
+        ctx = mp.get_context("spawn")
+        locks = [ctx.Lock() for _ in range(4)]
+        with ctx.Pool(cores, initializer=_ac_init, initargs=(locks,)) as pool:
+            pool.map(abs, range(cores))                   # workers started before the clock
+            t0 = time.perf_counter()
+            for k in range(4):
+                np.ndarray(shape, dtype=np.int32, buffer=blocks[2 * k + 1].buf)[...] = 0
+            pool.map(_ac_cost, [(k, passes[k][0], passes[k][1], passes[k][2], D, names, shape)
+                                for k in range(4)])
+            pool.map(_ac_path, [(k, r, names, shape) for k in range(4) for r in oracle.DIRECTIONS],
+                     chunksize=1)
+            sel = []
+            for k in range(4):
+                S = np.ndarray(shape, dtype=np.int32, buffer=blocks[2 * k + 1].buf)
+                sel.append(oracle.select(S, subpixel=(k % 2 == 0)))
+            disp = []
+            for f in range(2):
+                (dL, dLs), (dR, _) = sel[2 * f], sel[2 * f + 1]
+                disp.append(oracle.lr_check(dL, dR, dLs, 1)[1])
+            res = oracle.combine(disp[0], disp[1], q.flow, q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
+            dt = time.perf_counter() - t0
+            if keep is not None:
+                keep["s4"], keep["motion"], keep["point"], keep["valid"] = res
+    finally:
+        for b in blocks:
+            b.close()
+            b.unlink()
+        for b in _SHM.values():
+            b.close()
+        _SHM.clear()
+    return {"value": round(1.0 / dt, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "one full 1242x375 D=128 frame, the oracle's functions over 4 cost volumes and "
+                      "32 (pass, direction) paths in spawned workers",
+            "seconds": round(dt, 2), "cpu_model": cpu_model()}
 
 
 def run_reference(args, rank):

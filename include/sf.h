@@ -228,6 +228,88 @@ sf_status sf_combine_sceneflow(const float* D0, const float* D1, const float* fl
                                int32_t H, const sf_camera* cam, float* s4_out, float* motion_out,
                                float* point_out, uint8_t* valid_out, void* stream);
 
+/* ---- more than two frames (the paper's future work, Sec. 5) ---------------
+ * A sequence of K stereo frames (2 <= K <= SF_MAX_FRAMES) with the flows
+ * F_0 .. F_{K-2} (F_k from frame k to frame k+1, float [H][W][2]).
+ *
+ * Chain: the reference pixel x_0 of frame 0 is followed through every frame,
+ * x_{k+1} = x_k + F_k(x_k) (F_0 at the pixel itself, F_k for k >= 1 by the
+ * bilinear interpolation of Eq. 5 at x_k; positions as float32 sums and
+ * products in a fixed order).  Frame k's disparity is the Eq. 5 interpolation
+ * of D^k at x_k with every tap of nonzero weight usable (not NaN, > 0), as in
+ * the combination; the chain is valid iff every x_k lies in [0, W-1] x
+ * [0, H-1] and every disparity is usable, so each intermediate frame validates
+ * it.  Output: the 3D point of the reference pixel in every frame,
+ * P_k = ((x_k - cx) B / d_k, (y_k - cy) B / d_k, f B / d_k).  With K = 2 this is
+ * sf_combine_sceneflow (point = P_0, motion = P_1 - P_0). */
+#define SF_MAX_FRAMES 64
+
+/* The chain alone.  disps: K device pointers (host array) to float [H][W]
+ * (NaN = removed); flows: K-1 device pointers (host array) to float
+ * [H][W][2]; points_out: float [K][H][W][3] or NULL (NaN where invalid);
+ * valid_out: uint8 [H][W] or NULL. */
+sf_status sf_chain_sceneflow(const float* const* disps, const float* const* flows, int32_t K, int32_t W,
+                             int32_t H, const sf_camera* cam, float* points_out, uint8_t* valid_out, void* stream);
+
+/* Workspace bytes of sf_sequence_sceneflow for K frames; learned = 1 for the
+ * learned-confidence mode (packed != NULL there). */
+size_t sf_sequence_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p, int32_t K, int32_t learned);
+
+/* The hot path over a sequence: the SGM disparity of every stereo frame ONCE
+ * (K pairs, where K-1 separate quadruples would compute 2 (K-1)), with the
+ * plain left-right check (packed == NULL) or the learned confidence
+ * (packed, threshold as in sf_scene_flow_learned); then the combination of
+ * Sec. 3.3 for each consecutive pair (k, k+1), and the chain above.
+ * left, right: K device pointers (host arrays) to uint8 [H][pitch]; flows:
+ * K-1 device pointers.  Outputs, each a host array of device pointers or
+ * NULL: disp_out (K maps float [H][W], NaN where removed), s4_out and
+ * valid_out (K-1 entries, as in sf_combine_sceneflow), motion_out (K-1
+ * entries, each float [H][W][3] or NULL); points_out float [K][H][W][3] and
+ * chain_valid_out uint8 [H][W] (device, or NULL: no chain).  s4_out and
+ * valid_out are both given or both NULL.  workspace: at least
+ * sf_sequence_workspace_size() bytes. */
+sf_status sf_sequence_sceneflow(const uint8_t* const* left, const uint8_t* const* right, int32_t K, int32_t pitch,
+                                const float* const* flows, int32_t W, int32_t H, const sf_sgm_params* p,
+                                const sf_camera* cam, const void* packed, float threshold, float* const* disp_out,
+                                float* const* s4_out, uint8_t* const* valid_out, float* const* motion_out,
+                                float* points_out, uint8_t* chain_valid_out, void* workspace, size_t ws_bytes,
+                                void* stream);
+
+/* ---- densification (the paper's future work, Sec. 5) ----------------------
+ * The method's scene flow is sparse (Sec. 3.3); Table 1's dense rows come from
+ * the benchmark's own fill of a sparse submission (Sec. 4.1).  A map whose
+ * missing values are NaN is filled along each row, then, for the rows with
+ * nothing kept, along each column of the row-filled map.  Within a line a
+ * missing pixel between kept values a (before) and b (after) takes
+ *   SF_FILL_BACKGROUND: min(a, b), the farther surface of a disparity map;
+ *   SF_FILL_EDGE_AWARE: the one whose guide intensity is closer to the
+ *                       pixel's own intensity (min(a, b) on a tie);
+ * with one kept side it takes that value; a line with nothing kept stays NaN
+ * (every pixel of a map with nothing kept stays NaN). */
+#define SF_FILL_BACKGROUND 0
+#define SF_FILL_EDGE_AWARE 1
+
+/* Fills the NaN entries of a float map.  in, out: float [H][W], distinct
+ * buffers (in == out returns SF_ERR_INVALID_ARG); guide: uint8 [H][pitch]
+ * (the reference image), required for SF_FILL_EDGE_AWARE, ignored (may be
+ * NULL) for SF_FILL_BACKGROUND. */
+sf_status sf_fill_disparity(const float* in, int32_t W, int32_t H, const uint8_t* guide, int32_t pitch,
+                            int32_t mode, float* out, void* stream);
+
+/* Dense scene flow from a sparse result of sf_combine_sceneflow /
+ * sf_scene_flow: d0 and d1 of s4_in (channels 2 and 3, NaN where undefined;
+ * d1 is the warped disparity of t+1 at the reference pixel) are each filled as
+ * in sf_fill_disparity, (u, v) is taken from the flow, and the
+ * back-projection of Sec. 3.3 is evaluated at every pixel whose filled d0 and
+ * d1 are both positive: s4_out = (u, v, d0, d1), point = P0, motion = P1 - P0
+ * with x' = x + F(x) as a float32 sum; elsewhere NaN and valid 0.
+ * s4_in, s4_out: float [H][W][4], distinct, 16-byte aligned; flow: float
+ * [H][W][2]; motion_out, point_out: float [H][W][3] or NULL; valid_out: uint8
+ * [H][W]; guide as in sf_fill_disparity (the left image at t). */
+sf_status sf_densify_sceneflow(const float* s4_in, const float* flow, int32_t W, int32_t H, const sf_camera* cam,
+                               const uint8_t* guide, int32_t pitch, int32_t mode, float* s4_out,
+                               float* motion_out, float* point_out, uint8_t* valid_out, void* stream);
+
 /* Workspace bytes for sf_sgm_full and sf_scene_flow at this size. */
 size_t sf_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p);
 
@@ -355,6 +437,15 @@ sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_param
 /* Destroys the CUDA graphs cached by sf_batch_run (host-side resources). */
 void sf_batch_release_graphs(void);
 
+/* Bounds the device memory a batch holds at a time (no counterpart in the
+ * paper): with bytes > 0, sf_batch_run takes the items in consecutive waves,
+ * each as many items as keep its buffers within `bytes` (at least one item),
+ * one wave after another over one shared region, so the workspace is about
+ * the largest wave's buffers instead of the whole batch's.  0 (the default):
+ * one wave.  Process-wide; sf_batch_workspace_size follows it, and a cached
+ * graph is keyed by it.  Outputs are identical for every limit. */
+sf_status sf_set_batch_wave_limit(size_t bytes);
+
 /* Kernel shape of the band sweeps for a class of disparity counts, as chosen
  * by an autotuner: every D in [d_lo, d_hi] then runs with `dc` disparities
  * per thread (8 or 16) and `halo` halo columns (8 or 16; the band height is
@@ -390,7 +481,8 @@ typedef enum {
   SF_STAGE_SGM_SWEEP = 6,   /* fused cost + aggregation sweep                */
   SF_STAGE_FEATURES = 7,    /* learned path: features of the cost curve      */
   SF_STAGE_CONFNET = 8,     /* learned path: confidence network inference    */
-  SF_NUM_STAGES = 7
+  SF_STAGE_DENSIFY = 9,     /* densification of a sparse result              */
+  SF_NUM_STAGES = 10
 } sf_stage;
 
 /* Arms the tracer: from now on every stage the library enqueues is bracketed

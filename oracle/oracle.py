@@ -21,6 +21,15 @@ paper it follows:
 * ``lr_check``: the left-right consistency check that makes the disparity map
   non-dense (Sec. 3.1).
 * ``combine``: Eq. 3-5 of Sec. 3.3, with the back-projection Z = fB/d.
+* ``chain``: more than two frames (the paper's future work, Sec. 5): the
+  reference pixel followed through every frame by the flows, each
+  intermediate frame's disparity validating the chain, and its 3D point in
+  every frame; two frames give the combination of Sec. 3.3.
+* ``fill`` / ``densify``: filling the gaps of the sparse result, the paper's
+  future work (Sec. 5); Table 1's dense rows come from the benchmark's own
+  background fill of a sparse submission (Sec. 4.1).  Background fill, or an
+  edge-aware choice by guide intensity; then the back-projection of Sec. 3.3
+  at every filled pixel.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (brute force, closed forms, invariants).  The exact subpixel value of a real
@@ -53,8 +62,10 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
-                       check=True)
+        # every floating-point operation rounded on its own (no fused
+        # multiply-add contraction, which some targets apply by default)
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC,
+                        "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -74,12 +85,16 @@ def _load():
             lib.oracle_aggregate.argtypes = [P, i, i, i, i, i, ctypes.c_uint32, P, P]
             lib.oracle_aggregate_guided.argtypes = [P, P, i, i, i, i, i, ctypes.c_uint32, P, P]
             lib.oracle_uniqueness.argtypes = [P, i, i, i, i, P, P]
+            lib.oracle_fill.argtypes = [P, P, i, i, i, P, P]
+            lib.oracle_densify.argtypes = [P, P, P, i, i, i, d, d, d, d, P, P, P, P, P]
+            lib.oracle_chain.argtypes = [P, P, i, i, i, d, d, d, d, P, P]
             lib.oracle_select.argtypes = [P, i, i, i, i, P, P]
             lib.oracle_lr_check.argtypes = [P, P, P, i, i, i, P, P]
             lib.oracle_combine.argtypes = [P, P, P, i, i, d, d, d, d, P, P, P, P]
             for fn in ("oracle_census", "oracle_cost", "oracle_path", "oracle_aggregate",
                        "oracle_select", "oracle_lr_check", "oracle_combine", "oracle_path_guided",
-                       "oracle_aggregate_guided", "oracle_uniqueness"):
+                       "oracle_aggregate_guided", "oracle_uniqueness", "oracle_fill", "oracle_densify",
+                       "oracle_chain"):
                 getattr(lib, fn).restype = None
             _lib = lib
     return _lib
@@ -234,3 +249,57 @@ def scene_flow(quad, flow: np.ndarray, f: float, B: float, cx: float, cy: float,
     r1 = disparity(quad[2], quad[3], **sgm_kw)
     s4, motion, point, valid = combine(r0["disp"], r1["disp"], flow, f, B, cx, cy)
     return {"t0": r0, "t1": r1, "s4": s4, "motion": motion, "point": point, "valid": valid}
+
+
+def fill(a: np.ndarray, guide=None, mode: int = 0) -> np.ndarray:
+    """Fill of a sparse map (NaN = missing): rows first, then the columns for
+    the rows left empty; mode 0 background (smaller bounding value), mode 1
+    edge-aware (bounding value of the closer guide intensity, smaller on a
+    tie).  float64 [H][W]."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    H, W = a.shape
+    g, gp = _guide(guide, H, W)
+    if mode == 1 and g is None:
+        raise ValueError("the edge-aware fill needs a guide image")
+    out = np.empty((H, W), dtype=np.float64)
+    rows = np.empty((H, W), dtype=np.float64)
+    _load().oracle_fill(_ptr(a), gp, int(mode), W, H, _ptr(out), _ptr(rows))
+    return out
+
+
+def densify(s4: np.ndarray, flow: np.ndarray, f: float, B: float, cx: float, cy: float, guide=None,
+            mode: int = 0):
+    """Dense scene flow from a sparse s4 [H][W][4] (NaN where undefined):
+    returns (s4, motion, point, valid) with d0 and d1 filled by ``fill``."""
+    s4 = np.ascontiguousarray(s4, dtype=np.float64)
+    H, W = s4.shape[:2]
+    flow = np.ascontiguousarray(flow, dtype=np.float32)
+    g, gp = _guide(guide, H, W)
+    if mode == 1 and g is None:
+        raise ValueError("the edge-aware fill needs a guide image")
+    s4o = np.empty((H, W, 4))
+    motion = np.empty((H, W, 3))
+    point = np.empty((H, W, 3))
+    valid = np.empty((H, W), dtype=np.uint8)
+    scratch = np.empty(5 * H * W)
+    _load().oracle_densify(_ptr(s4), _ptr(flow), gp, int(mode), W, H, f, B, cx, cy, _ptr(s4o), _ptr(motion),
+                           _ptr(point), _ptr(valid), _ptr(scratch))
+    return s4o, motion, point, valid
+
+
+def chain(disps, flows, f: float, B: float, cx: float, cy: float):
+    """Trajectories through K frames: disps K maps float64 [H][W] (NaN =
+    removed), flows K-1 maps float32 [H][W][2].  Returns (points float64
+    [K][H][W][3], valid uint8 [H][W])."""
+    K = len(disps)
+    assert len(flows) == K - 1 and K >= 2
+    D = [np.ascontiguousarray(d, dtype=np.float64) for d in disps]
+    F = [np.ascontiguousarray(fl, dtype=np.float32) for fl in flows]
+    H, W = D[0].shape
+    dp = (ctypes.c_void_p * K)(*[d.ctypes.data for d in D])
+    fp = (ctypes.c_void_p * max(K - 1, 1))(*([fl.ctypes.data for fl in F] or [0]))
+    points = np.empty((K, H, W, 3))
+    valid = np.empty((H, W), dtype=np.uint8)
+    _load().oracle_chain(ctypes.cast(dp, ctypes.c_void_p), ctypes.cast(fp, ctypes.c_void_p), K, W, H, f, B, cx, cy,
+                         _ptr(points), _ptr(valid))
+    return points, valid

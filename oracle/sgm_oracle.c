@@ -307,3 +307,208 @@ void oracle_combine(const double* D0, const double* D1, const float* flow, int W
     }
   }
 }
+
+/* ---- Densification (the paper's future work, Sec. 5; Table 1's dense "All"
+ * rows are the benchmark's own fill of a sparse submission, Sec. 4.1) ----
+ *
+ * Fill of a sparse map (NaN = missing), first along each row, then, for the
+ * rows with nothing kept, along each column of the row-filled map.  Within a
+ * line, a missing pixel between two kept ones at a and b takes:
+ *   mode 0 (background): the smaller of the two values (the farther surface
+ *     for a disparity);
+ *   mode 1 (edge-aware): the value whose guide intensity is closer to the
+ *     pixel's own (|I(p) - I(a)| against |I(p) - I(b)|), the smaller value on
+ *     a tie;
+ * a missing pixel with a kept value on one side only takes that value; a
+ * line with nothing kept stays missing.  guide: uint8 [H][W] (mode 1). */
+static double fill_choose(int mode, const uint8_t* guide, double va, double vb, size_t p, size_t a,
+                          size_t b) {
+  if (mode == 1) {
+    int ia = abs((int)guide[p] - (int)guide[a]);
+    int ib = abs((int)guide[p] - (int)guide[b]);
+    if (ia < ib) return va;
+    if (ib < ia) return vb;
+  }
+  return va < vb ? va : vb;
+}
+
+/* One line of n samples at in[i0 + k*step] -> out (same indexing); guide
+ * indexed alike. */
+static void fill_line(const double* in, const uint8_t* guide, int mode, int n, size_t i0, size_t step,
+                      double* out) {
+  for (int k = 0; k < n; k++) {
+    size_t i = i0 + (size_t)k * step;
+    if (!isnan(in[i])) {
+      out[i] = in[i];
+      continue;
+    }
+    int a = -1, b = -1;
+    for (int j = k - 1; j >= 0; j--)
+      if (!isnan(in[i0 + (size_t)j * step])) { a = j; break; }
+    for (int j = k + 1; j < n; j++)
+      if (!isnan(in[i0 + (size_t)j * step])) { b = j; break; }
+    if (a >= 0 && b >= 0) {
+      size_t ia = i0 + (size_t)a * step, ib = i0 + (size_t)b * step;
+      out[i] = fill_choose(mode, guide, in[ia], in[ib], i, ia, ib);
+    } else if (a >= 0) {
+      out[i] = in[i0 + (size_t)a * step];
+    } else if (b >= 0) {
+      out[i] = in[i0 + (size_t)b * step];
+    } else {
+      out[i] = NAN;
+    }
+  }
+}
+
+void oracle_fill(const double* in, const uint8_t* guide, int mode, int W, int H, double* out,
+                 double* rows) {
+  for (int y = 0; y < H; y++) fill_line(in, guide, mode, W, (size_t)y * W, 1, rows);
+  for (int x = 0; x < W; x++) fill_line(rows, guide, mode, H, (size_t)x, (size_t)W, out);
+  /* the column pass only serves the rows the row pass left empty */
+  for (size_t i = 0; i < (size_t)W * H; i++)
+    if (!isnan(rows[i])) out[i] = rows[i];
+}
+
+/* Dense scene flow from a sparse result: d0 and d1 of s4 (NaN where the
+ * combination left them undefined) each filled by oracle_fill, (u, v) taken
+ * from the flow, then the back-projection of Sec. 3.3 at every pixel whose
+ * filled disparities are both positive (the others NaN, valid 0):
+ * P0 = ((x-cx)B/d0, (y-cy)B/d0, fB/d0), P1 at x' = fl32(x+u), y' = fl32(y+v)
+ * with d1, motion = P1 - P0. */
+void oracle_densify(const double* s4, const float* flow, const uint8_t* guide, int mode, int W, int H,
+                    double f, double B, double cx, double cy, double* s4_out, double* motion,
+                    double* point, uint8_t* valid, double* scratch) {
+  size_t n = (size_t)W * H;
+  double* d0 = scratch;
+  double* d1 = scratch + n;
+  double* f0 = scratch + 2 * n;
+  double* f1 = scratch + 3 * n;
+  double* rows = scratch + 4 * n;
+  for (size_t i = 0; i < n; i++) {
+    d0[i] = s4[4 * i + 2];
+    d1[i] = s4[4 * i + 3];
+  }
+  oracle_fill(d0, guide, mode, W, H, f0, rows);
+  oracle_fill(d1, guide, mode, W, H, f1, rows);
+  for (int y = 0; y < H; y++) {
+    for (int x = 0; x < W; x++) {
+      size_t i = (size_t)y * W + x;
+      float u = flow[2 * i], v = flow[2 * i + 1];
+      double a = f0[i], b = f1[i];
+      int ok = !isnan(a) && !isnan(b) && a > 0.0 && b > 0.0;
+      valid[i] = (uint8_t)ok;
+      s4_out[4 * i + 0] = ok ? (double)u : NAN;
+      s4_out[4 * i + 1] = ok ? (double)v : NAN;
+      s4_out[4 * i + 2] = ok ? a : NAN;
+      s4_out[4 * i + 3] = ok ? b : NAN;
+      double xp = (double)((float)x + u), yp = (double)((float)y + v);
+      double P0[3] = {(x - cx) * B / a, (y - cy) * B / a, f * B / a};
+      double P1[3] = {(xp - cx) * B / b, (yp - cy) * B / b, f * B / b};
+      for (int k = 0; k < 3; k++) {
+        if (motion) motion[3 * i + k] = ok ? P1[k] - P0[k] : NAN;
+        if (point) point[3 * i + k] = ok ? P0[k] : NAN;
+      }
+    }
+  }
+}
+
+/* ---- Multi-frame extension (the paper's future work, Sec. 5: more than two
+ * frame pairs, with an intermediate validation) ----
+ *
+ * K frames with disparity maps D^0 .. D^{K-1} (NaN = removed by the check) and
+ * flows F_0 .. F_{K-2} (F_k maps frame k to k+1).  The reference pixel
+ * x_0 = (x, y) of frame 0 is followed through every frame:
+ *   x_{k+1} = x_k + F_k(x_k),
+ * with F_0(x_0) the flow at the pixel itself and, for k >= 1, F_k(x_k) the
+ * Eq. 5 bilinear interpolation of F_k at x_k (taps of weight 0 skipped).
+ * Positions are float32 round-to-nearest sums and products in a fixed order
+ * (the weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy, each times its tap,
+ * summed in that order): they decide which pixels are read and whether the
+ * chain stays in the image, so both sides take those decisions in the same
+ * precision.  The disparity of frame k is D^0(x_0) for k = 0 and the Eq. 5
+ * interpolation of D^k at x_k for k >= 1 (float64 sums), with the rule of
+ * the combination: every tap of nonzero weight usable.  The chain is valid iff
+ * every x_k lies in [0, W-1] x [0, H-1] and every disparity is usable: each
+ * intermediate frame validates it.  Output: the 3D point of every frame,
+ * P_k = ((x_k - cx) B / d_k, (y_k - cy) B / d_k, f B / d_k), NaN when invalid.
+ * With K = 2 this is the combination of Sec. 3.3 (P_1 - P_0 its motion).
+ *
+ * D: K pointers to double [H][W]; F: K-1 pointers to float [H][W][2];
+ * points: double [K][H][W][3]; valid: uint8 [H][W]. */
+static float bilerp_f32(const float* m, int W, int stride, int ix, int iy, float fx, float fy) {
+  float w00 = (1.0f - fx) * (1.0f - fy);
+  float r = w00 * m[((size_t)iy * W + ix) * stride];
+  if (fx != 0.0f) {
+    float w10 = fx * (1.0f - fy);
+    r = r + w10 * m[((size_t)iy * W + ix + 1) * stride];
+  }
+  if (fy != 0.0f) {
+    float w01 = (1.0f - fx) * fy;
+    r = r + w01 * m[((size_t)(iy + 1) * W + ix) * stride];
+  }
+  if (fx != 0.0f && fy != 0.0f) {
+    float w11 = fx * fy;
+    r = r + w11 * m[((size_t)(iy + 1) * W + ix + 1) * stride];
+  }
+  return r;
+}
+
+void oracle_chain(const double* const* D, const float* const* F, int K, int W, int H, double f, double B,
+                  double cx, double cy, double* points, uint8_t* valid) {
+  for (int y = 0; y < H; y++) {
+    for (int x = 0; x < W; x++) {
+      size_t i = (size_t)y * W + x;
+      float px = (float)x, py = (float)y;
+      int ok = 1;
+      for (int k = 0; k < K && ok; k++) {
+        double d;
+        if (k == 0) {
+          d = D[0][i];
+          ok = disparity_usable(d);
+        } else {
+          /* x_k from x_{k-1} and F_{k-1} */
+          const float* Fk = F[k - 1];
+          float u, v;
+          if (k == 1) {
+            u = Fk[2 * i];
+            v = Fk[2 * i + 1];
+          } else {
+            float x0 = floorf(px), y0 = floorf(py);
+            float fx = px - x0, fy = py - y0;
+            u = bilerp_f32(Fk, W, 2, (int)x0, (int)y0, fx, fy);
+            v = bilerp_f32(Fk + 1, W, 2, (int)x0, (int)y0, fx, fy);
+          }
+          px = px + u;
+          py = py + v;
+          if (!(px >= 0.0f && px <= (float)(W - 1) && py >= 0.0f && py <= (float)(H - 1))) {
+            ok = 0;
+            break;
+          }
+          float x0 = floorf(px), y0 = floorf(py);
+          double fx = (double)(px - x0), fy = (double)(py - y0);
+          int ix = (int)x0, iy = (int)y0;
+          double w[4] = {(1.0 - fx) * (1.0 - fy), fx * (1.0 - fy), (1.0 - fx) * fy, fx * fy};
+          int tx[4] = {ix, ix + 1, ix, ix + 1};
+          int ty[4] = {iy, iy, iy + 1, iy + 1};
+          d = 0.0;
+          for (int t = 0; t < 4 && ok; t++) {
+            if (w[t] == 0.0) continue;
+            double dt = D[k][(size_t)ty[t] * W + tx[t]];
+            if (!disparity_usable(dt)) ok = 0;
+            else d += w[t] * dt;
+          }
+        }
+        if (ok) {
+          double* P = points + (((size_t)k * H * W) + i) * 3;
+          P[0] = ((double)px - cx) * B / d;
+          P[1] = ((double)py - cy) * B / d;
+          P[2] = f * B / d;
+        }
+      }
+      valid[i] = (uint8_t)ok;
+      if (!ok)
+        for (int k = 0; k < K; k++)
+          for (int c = 0; c < 3; c++) points[(((size_t)k * H * W) + i) * 3 + c] = NAN;
+    }
+  }
+}

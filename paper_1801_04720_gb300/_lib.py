@@ -29,7 +29,8 @@ EXPORTED = [
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
     "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
     "sf_batch_workspace_size", "sf_batch_run", "sf_batch_release_graphs", "sf_set_sweep_shape",
-    "sf_set_sweep_schedule", "sf_sgm_aggregate_guided",
+    "sf_set_sweep_schedule", "sf_sgm_aggregate_guided", "sf_fill_disparity", "sf_densify_sceneflow",
+    "sf_chain_sceneflow", "sf_sequence_workspace_size", "sf_sequence_sceneflow", "sf_set_batch_wave_limit",
     "sf_sgm_aggregate_noalloc", "sf_confnet_param_count", "sf_confnet_packed_bytes",
     "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
     "sf_confnet_train_step", "sf_confnet_adam", "sf_learned_workspace_size", "sf_sgm_learned",
@@ -46,7 +47,10 @@ SF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 SF_BATCH_GRAPH = 1
 
 STAGE_NAMES = ["census", "cost", "aggregate", "select", "lrcheck", "combine", "sgm_sweep",
-               "features", "confnet"]
+               "features", "confnet", "densify"]
+
+SF_FILL_BACKGROUND = 0
+SF_FILL_EDGE_AWARE = 1
 
 
 class SFError(RuntimeError):
@@ -146,6 +150,13 @@ def load(path: str = LIB_PATH):
             "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
             "sf_set_sweep_schedule": (i32, [i32, i32, i32, i32, i32]),
             "sf_sgm_aggregate_guided": (i32, [P, P, i32, i32, i32, PP, P, P, sz, P]),
+            "sf_fill_disparity": (i32, [P, i32, i32, P, i32, i32, P, P]),
+            "sf_chain_sceneflow": (i32, [P, P, i32, i32, i32, PC, P, P, P]),
+            "sf_set_batch_wave_limit": (i32, [sz]),
+            "sf_sequence_workspace_size": (sz, [i32, i32, PP, i32, i32]),
+            "sf_sequence_sceneflow": (i32, [P, P, i32, i32, P, i32, i32, PP, PC, P, ctypes.c_float, P, P, P, P,
+                                            P, P, P, sz, P]),
+            "sf_densify_sceneflow": (i32, [P, P, i32, i32, PC, P, i32, i32, P, P, P, P, P]),
             "sf_check_workspace": (i32, [P, i32, i32, PP, i32, P]),
             "sf_debug_set": (i32, [i32, ctypes.c_int64]),
             "sf_scene_flow_learned_frames": (i32, [P, i32, i32, i32, i32, PP, PC, P, ctypes.c_float, P, sz,
@@ -333,6 +344,106 @@ def sf_combine_sceneflow(D0, D1, flow, cam: Camera, want_motion=True, want_point
            load().sf_combine_sceneflow(_ptr(D0), _ptr(D1), _ptr(flow), W, H, ctypes.byref(cam),
                                        _ptr(out["s4"]), _ptr(out["motion"]), _ptr(out["point"]),
                                        _ptr(out["valid"]), _stream(stream)))
+    return out
+
+
+def sf_fill_disparity(d, guide=None, mode=SF_FILL_BACKGROUND, out=None, stream=None):
+    """Fills the NaN entries of a float [H][W] map (densification)."""
+    _dev(d, torch.float32, "d")
+    H, W = d.shape
+    if out is None:
+        out = torch.empty_like(d)
+    if guide is not None:
+        _dev(guide, torch.uint8, "guide")
+    _check("sf_fill_disparity", load().sf_fill_disparity(_ptr(d), W, H, _ptr(guide),
+                                                         guide.stride(0) if guide is not None else 0,
+                                                         int(mode), _ptr(out), _stream(stream)))
+    return out
+
+
+def sf_densify_sceneflow(s4, flow, cam: Camera, guide=None, mode=SF_FILL_BACKGROUND, out=None, stream=None):
+    """Dense scene flow from a sparse s4 [H][W][4] (NaN where undefined)."""
+    _dev(s4, torch.float32, "s4")
+    H, W = s4.shape[:2]
+    dev = s4.device
+    if out is None:
+        out = {"s4": torch.empty((H, W, 4), dtype=torch.float32, device=dev),
+               "motion": torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+               "point": torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+               "valid": torch.empty((H, W), dtype=torch.uint8, device=dev)}
+    if guide is not None:
+        _dev(guide, torch.uint8, "guide")
+    _check("sf_densify_sceneflow",
+           load().sf_densify_sceneflow(_ptr(s4), _ptr(flow), W, H, ctypes.byref(cam), _ptr(guide),
+                                       guide.stride(0) if guide is not None else 0, int(mode), _ptr(out["s4"]),
+                                       _ptr(out["motion"]), _ptr(out["point"]), _ptr(out["valid"]),
+                                       _stream(stream)))
+    return out
+
+
+SF_MAX_FRAMES = 64
+
+
+def _ptr_array(ts):
+    """Host array of device pointers (None -> NULL entries)."""
+    arr = (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+    return ctypes.cast(arr, ctypes.c_void_p), arr
+
+
+def sf_chain_sceneflow(disps, flows, cam: Camera, points=True, stream=None):
+    """Trajectories of frame 0's pixels through K frames: disps K float
+    [H][W] maps, flows K-1 float [H][W][2].  Returns {"points" [K][H][W][3],
+    "valid" [H][W]}."""
+    K = len(disps)
+    H, W = disps[0].shape
+    dev = disps[0].device
+    out = {"points": torch.empty((K, H, W, 3), dtype=torch.float32, device=dev) if points else None,
+           "valid": torch.empty((H, W), dtype=torch.uint8, device=dev)}
+    dp, _k1 = _ptr_array(disps)
+    fp, _k2 = _ptr_array(flows)
+    _check("sf_chain_sceneflow", load().sf_chain_sceneflow(dp, fp, K, W, H, ctypes.byref(cam), _ptr(out["points"]),
+                                                           _ptr(out["valid"]), _stream(stream)))
+    return out
+
+
+def alloc_sequence_outputs(K, W, H, device="cuda", chain=True, motion=False):
+    f32 = torch.float32
+    return {"disp": [torch.empty((H, W), dtype=f32, device=device) for _ in range(K)],
+            "s4": [torch.empty((H, W, 4), dtype=f32, device=device) for _ in range(K - 1)],
+            "valid": [torch.empty((H, W), dtype=torch.uint8, device=device) for _ in range(K - 1)],
+            "motion": [torch.empty((H, W, 3), dtype=f32, device=device) for _ in range(K - 1)] if motion else None,
+            "points": torch.empty((K, H, W, 3), dtype=f32, device=device) if chain else None,
+            "chain_valid": torch.empty((H, W), dtype=torch.uint8, device=device) if chain else None}
+
+
+def sf_sequence_sceneflow(lefts, rights, flows, p: SgmParams, cam: Camera, packed=None, threshold=0.5,
+                          ws=None, chain=True, motion=False, out=None, stream=None):
+    """The hot path over K stereo frames, each frame's SGM once; returns
+    {"disp": K maps, "s4", "valid", "motion": K-1 each, "points", "chain_valid"}."""
+    K = len(lefts)
+    H, W = lefts[0].shape
+    dev = lefts[0].device
+    if ws is None:
+        n = load().sf_sequence_workspace_size(W, H, ctypes.byref(p), K, int(packed is not None))
+        ws = torch.empty(n, dtype=torch.uint8, device=dev)
+    if out is None:
+        out = alloc_sequence_outputs(K, W, H, dev, chain=chain, motion=motion)
+    motion = out["motion"] is not None
+    keep = []
+    arrs = []
+    for group in (lefts, rights, flows, out["disp"], out["s4"], out["valid"]):
+        a, k = _ptr_array(group)
+        arrs.append(a)
+        keep.append(k)
+    mo = None
+    if motion:
+        mo, k = _ptr_array(out["motion"])
+        keep.append(k)
+    _check("sf_sequence_sceneflow",
+           load().sf_sequence_sceneflow(arrs[0], arrs[1], K, lefts[0].stride(0), arrs[2], W, H, ctypes.byref(p),
+                                        ctypes.byref(cam), _ptr(packed), float(threshold), arrs[3], arrs[4], arrs[5],
+                                        mo, _ptr(out["points"]), _ptr(out["chain_valid"]), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
     return out
 
 
@@ -539,6 +650,10 @@ def sf_batch_run(items, p: SgmParams, ws, graph=False, stream=None):
 
 def sf_batch_release_graphs():
     load().sf_batch_release_graphs()
+
+
+def sf_set_batch_wave_limit(nbytes):
+    _check("sf_set_batch_wave_limit", load().sf_set_batch_wave_limit(int(nbytes)))
 
 
 def sf_set_sweep_shape(d_lo, d_hi, dc, halo):

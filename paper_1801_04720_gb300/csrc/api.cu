@@ -572,9 +572,15 @@ std::vector<uint8_t> batch_tables(const BatchSetup& b, const FusedPlan& plan, ui
 }
 
 // Everything after the table upload: costs, sweeps, checks, combination.
+// ws: the wave's buffers (control block first); tab: its descriptor tables.
+// The error word is cleared by the first wave only, so a bounded wait that
+// gave up in any wave stays recorded.
 sf_status batch_enqueue(const sf_batch_item* items, int n, const sf_sgm_params* p, const BatchSetup& b,
-                        const FusedPlan& plan, uint8_t* ws, cudaStream_t s) {
-  SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
+                        const FusedPlan& plan, uint8_t* ws, uint8_t* tab, bool first_wave, cudaStream_t s) {
+  if (first_wave)
+    SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
+  else
+    SF_TRY_CUDA(cudaMemsetAsync(ws + plan.counters, 0, plan.control_bytes - plan.counters, s));
   for (int i = 0; i < n; i++) {
     const sf_batch_item& it = items[i];
     const uint8_t* L[2] = {it.left_t, it.left_t1};
@@ -583,7 +589,6 @@ sf_status batch_enqueue(const sf_batch_item* items, int n, const sf_sgm_params* 
     sf_status st = run_pair_costs(L, R, 2, it.W, it.H, it.pitch, it.D, p, ws, bufs, s);
     if (st != SF_OK) return st;
   }
-  uint8_t* tab = ws + plan.tables;
   int* counters = reinterpret_cast<int*>(ws + plan.counters);
   for (size_t c = 0; c < b.classes.size(); c++) {
     const BatchClass& bc = b.classes[c];
@@ -612,6 +617,48 @@ sf_status batch_enqueue(const sf_batch_item* items, int n, const sf_sgm_params* 
   return SF_OK;
 }
 
+// ---- batch waves: items in consecutive groups whose buffers fit a limit,
+// one after another over one shared region (process-wide limit, 0 = one
+// wave).  Workspace: every wave's descriptor tables, then the region.
+std::atomic<size_t> g_batch_wave_bytes{0};
+
+struct BatchWave {
+  int start = 0, count = 0;
+  BatchSetup b;
+  FusedPlan plan;
+  size_t tab_off = 0;
+  BatchWave(const sf_batch_item* items, int s0, int n, const sf_sgm_params* p)
+      : start(s0), count(n), b(batch_setup(items + s0, n, p)),
+        plan(b.pairs.data(), (int)b.pairs.size(), b.dshape.data(), 2 * (int)b.classes.size(), 0) {}
+};
+
+struct BatchLayout {
+  std::vector<BatchWave> waves;
+  size_t region = 0, region_off = 0, total = 0;
+  sf_status status = SF_OK;
+  BatchLayout(const sf_batch_item* items, int n, const sf_sgm_params* p) {
+    const BatchSetup all = batch_setup(items, n, p);
+    if ((status = all.status) != SF_OK) return;
+    const size_t limit = g_batch_wave_bytes.load(std::memory_order_relaxed);
+    int i = 0;
+    while (i < n) {
+      int k = 1;   // at least one item per wave
+      while (limit && i + k < n && BatchWave(items, i, k + 1, p).plan.total <= limit) k++;
+      if (!limit) k = n - i;
+      waves.emplace_back(items, i, k, p);
+      i += k;
+    }
+    size_t o = 0;
+    for (BatchWave& w : waves) {
+      w.tab_off = o;
+      o = align_up(o + w.b.table_bytes, 256);
+      region = std::max(region, w.plan.total);
+    }
+    region_off = o;
+    total = o + region;
+  }
+};
+
 struct GraphEntry {
   std::vector<uint8_t> key;
   cudaGraphExec_t exec = nullptr;
@@ -633,6 +680,8 @@ std::vector<uint8_t> batch_key(const sf_batch_item* items, int n, const sf_sgm_p
   put(&ws_bytes, sizeof(ws_bytes));
   put(&stream, sizeof(stream));
   for (const auto& pi : b_shape_keys()) put(&pi, sizeof(pi));
+  const size_t wave = g_batch_wave_bytes.load(std::memory_order_relaxed);
+  put(&wave, sizeof(wave));
   return k;
 }
 
@@ -794,6 +843,37 @@ sf_status sf_combine_sceneflow(const float* D0, const float* D1, const float* fl
   return SF_OK;
 }
 
+sf_status sf_fill_disparity(const float* in, int32_t W, int32_t H, const uint8_t* guide, int32_t pitch,
+                            int32_t mode, float* out, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!in || !out || in == out) return SF_ERR_INVALID_ARG;
+  if (mode != SF_FILL_BACKGROUND && mode != SF_FILL_EDGE_AWARE) return SF_ERR_INVALID_ARG;
+  if (mode == SF_FILL_EDGE_AWARE && (!guide || pitch < W)) return SF_ERR_INVALID_ARG;
+  if (!aligned(in, 4) || !aligned(out, 4)) return SF_ERR_INVALID_ARG;
+  SF_TRY_CUDA(launch_fill_map(in, W, H, mode == SF_FILL_EDGE_AWARE ? guide : nullptr, pitch, mode, out,
+                              (cudaStream_t)stream));
+  return SF_OK;
+}
+
+sf_status sf_densify_sceneflow(const float* s4_in, const float* flow, int32_t W, int32_t H, const sf_camera* cam,
+                               const uint8_t* guide, int32_t pitch, int32_t mode, float* s4_out,
+                               float* motion_out, float* point_out, uint8_t* valid_out, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!s4_in || !flow || !cam || !s4_out || !valid_out || s4_in == s4_out) return SF_ERR_INVALID_ARG;
+  if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
+  if (mode != SF_FILL_BACKGROUND && mode != SF_FILL_EDGE_AWARE) return SF_ERR_INVALID_ARG;
+  if (mode == SF_FILL_EDGE_AWARE && (!guide || pitch < W)) return SF_ERR_INVALID_ARG;
+  if (!aligned(s4_in, 16) || !aligned(s4_out, 16) || !aligned(flow, 8) || !aligned(motion_out, 4) ||
+      !aligned(point_out, 4))
+    return SF_ERR_INVALID_ARG;
+  SF_TRY_CUDA(launch_densify(s4_in, flow, W, H, cam->f, cam->B, cam->cx, cam->cy,
+                             mode == SF_FILL_EDGE_AWARE ? guide : nullptr, pitch, mode, s4_out, motion_out,
+                             point_out, valid_out, (cudaStream_t)stream));
+  return SF_OK;
+}
+
 size_t sf_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p) {
   if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
   return workspace_bytes(W, H, p, 2);
@@ -937,28 +1017,39 @@ sf_status sf_debug_set(int32_t key, int64_t value) {
 }
 
 size_t sf_batch_workspace_size(const sf_batch_item* items, int32_t n, const sf_sgm_params* p) {
-  BatchSetup b = batch_setup(items, n, p);
-  if (b.status != SF_OK) return 0;
-  std::vector<int> ds = b.dshape;
-  return FusedPlan(b.pairs.data(), (int)b.pairs.size(), ds.data(), 2 * (int)b.classes.size(),
-                   b.table_bytes).total;
+  const BatchLayout lay(items, n, p);
+  return lay.status == SF_OK ? lay.total : 0;
+}
+
+sf_status sf_set_batch_wave_limit(size_t bytes) {
+  g_batch_wave_bytes.store(bytes, std::memory_order_relaxed);
+  return SF_OK;
 }
 
 sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_params* p, uint32_t flags,
                        void* workspace, size_t ws_bytes, void* stream) {
-  BatchSetup b = batch_setup(items, n, p);
-  if (b.status != SF_OK) return b.status;
+  const BatchLayout lay(items, n, p);
+  if (lay.status != SF_OK) return lay.status;
   if (flags & ~SF_BATCH_GRAPH) return SF_ERR_INVALID_ARG;
-  FusedPlan plan(b.pairs.data(), (int)b.pairs.size(), b.dshape.data(), 2 * (int)b.classes.size(),
-                 b.table_bytes);
-  if (!workspace || ws_bytes < plan.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
+  if (!workspace || ws_bytes < lay.total || !aligned(workspace, 256)) return SF_ERR_INVALID_ARG;
   uint8_t* ws = (uint8_t*)workspace;
+  uint8_t* region = ws + lay.region_off;
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<uint8_t> blob = batch_tables(b, plan, ws, p, items);
-  // descriptor tables travel before the work (pageable source: the copy has
-  // read it when the call returns)
-  SF_TRY_CUDA(cudaMemcpyAsync(ws + plan.tables, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
-  if (!(flags & SF_BATCH_GRAPH)) return batch_enqueue(items, n, p, b, plan, ws, s);
+  // every wave's descriptor tables travel before the work (pageable source:
+  // the copy has read it when the call returns)
+  for (const BatchWave& w : lay.waves) {
+    std::vector<uint8_t> blob = batch_tables(w.b, w.plan, region, p, items + w.start);
+    SF_TRY_CUDA(cudaMemcpyAsync(ws + w.tab_off, blob.data(), blob.size(), cudaMemcpyHostToDevice, s));
+  }
+  auto enqueue = [&]() -> sf_status {
+    for (size_t i = 0; i < lay.waves.size(); i++) {
+      const BatchWave& w = lay.waves[i];
+      sf_status st = batch_enqueue(items + w.start, w.count, p, w.b, w.plan, region, ws + w.tab_off, i == 0, s);
+      if (st != SF_OK) return st;
+    }
+    return SF_OK;
+  };
+  if (!(flags & SF_BATCH_GRAPH)) return enqueue();
   if (s == nullptr) return SF_ERR_INVALID_ARG;   // the legacy default stream cannot be captured
   std::vector<uint8_t> key = batch_key(items, n, p, workspace, ws_bytes, stream);
   std::lock_guard<std::mutex> guard(g_graph_mu);
@@ -969,7 +1060,7 @@ sf_status sf_batch_run(const sf_batch_item* items, int32_t n, const sf_sgm_param
     }
   }
   SF_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-  sf_status st = batch_enqueue(items, n, p, b, plan, ws, s);
+  sf_status st = enqueue();
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &graph);
   if (st != SF_OK) {
@@ -1437,6 +1528,117 @@ sf_status sf_scene_flow_learned_frames(const sf_learned_frame* frames, int32_t n
     const sf_learned_frame& f = frames[i];
     SF_TRY_CUDA(launch_combine(disp[2 * i], disp[2 * i + 1], f.flow, W, H, cam->f, cam->B, cam->cx, cam->cy,
                                f.s4_out, f.motion_out, f.point_out, f.valid_out, s));
+  }
+  return SF_OK;
+}
+
+// ---- sequences of more than two frames ---------------------------------------
+// Workspace: the stereo work of one group of frames (two pairs with the
+// plain check, four left passes with the learned confidence), reused group
+// after group in stream order, then the K disparity maps.
+}  // extern "C"
+
+namespace {
+
+struct SequencePlan {
+  size_t stereo = 0, disp = 0, total = 0;
+  int group = 1;
+  SequencePlan(int W, int H, const sf_sgm_params* p, int K, bool learned) {
+    const size_t N = (size_t)W * H;
+    group = learned ? fused::kMaxPass : 2;
+    stereo = learned ? LearnedPlan(W, H, p->D, group).total : workspace_bytes(W, H, p, 2);
+    size_t o = align_up(stereo, 256);
+    disp = o;
+    o += (size_t)K * align_up(N * sizeof(float), 256);
+    total = o;
+  }
+  float* disp_map(uint8_t* ws, int k, int W, int H) const {
+    return reinterpret_cast<float*>(ws + disp + (size_t)k * align_up((size_t)W * H * sizeof(float), 256));
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+sf_status sf_chain_sceneflow(const float* const* disps, const float* const* flows, int32_t K, int32_t W,
+                             int32_t H, const sf_camera* cam, float* points_out, uint8_t* valid_out, void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!disps || !flows || !cam || K < 2 || K > SF_MAX_FRAMES) return SF_ERR_INVALID_ARG;
+  if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
+  if (!points_out && !valid_out) return SF_ERR_INVALID_ARG;
+  for (int k = 0; k < K; k++)
+    if (!disps[k] || !aligned(disps[k], 4)) return SF_ERR_INVALID_ARG;
+  for (int k = 0; k + 1 < K; k++)
+    if (!flows[k] || !aligned(flows[k], 8)) return SF_ERR_INVALID_ARG;
+  if (!aligned(points_out, 4)) return SF_ERR_INVALID_ARG;
+  SF_TRY_CUDA(launch_chain(disps, flows, K, W, H, cam->f, cam->B, cam->cx, cam->cy, points_out, valid_out,
+                           (cudaStream_t)stream));
+  return SF_OK;
+}
+
+size_t sf_sequence_workspace_size(int32_t W, int32_t H, const sf_sgm_params* p, int32_t K, int32_t learned) {
+  if (check_size(W, H) != SF_OK || !p || p->D < 1 || p->D > SF_MAX_DISPARITY) return 0;
+  if (K < 2 || K > SF_MAX_FRAMES || (learned != 0 && learned != 1)) return 0;
+  return SequencePlan(W, H, p, K, learned != 0).total;
+}
+
+sf_status sf_sequence_sceneflow(const uint8_t* const* left, const uint8_t* const* right, int32_t K, int32_t pitch,
+                                const float* const* flows, int32_t W, int32_t H, const sf_sgm_params* p,
+                                const sf_camera* cam, const void* packed, float threshold, float* const* disp_out,
+                                float* const* s4_out, uint8_t* const* valid_out, float* const* motion_out,
+                                float* points_out, uint8_t* chain_valid_out, void* workspace, size_t ws_bytes,
+                                void* stream) {
+  sf_status st = check_size(W, H);
+  if (st != SF_OK) return st;
+  if (!left || !right || !flows || !cam || !workspace || pitch < W || K < 2 || K > SF_MAX_FRAMES)
+    return SF_ERR_INVALID_ARG;
+  const bool learned = packed != nullptr;
+  if ((st = learned ? check_learned(W, H, p) : check_params(p, W, H)) != SF_OK) return st;
+  if (!(cam->f > 0.0f) || !(cam->B > 0.0f)) return SF_ERR_INVALID_ARG;
+  if ((s4_out == nullptr) != (valid_out == nullptr)) return SF_ERR_INVALID_ARG;
+  for (int k = 0; k < K; k++) {
+    if (!left[k] || !right[k]) return SF_ERR_INVALID_ARG;
+    if (disp_out && (!disp_out[k] || !aligned(disp_out[k], 4))) return SF_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k + 1 < K; k++) {
+    if (!flows[k] || !aligned(flows[k], 8)) return SF_ERR_INVALID_ARG;
+    if (s4_out && (!s4_out[k] || !valid_out[k] || !aligned(s4_out[k], 16))) return SF_ERR_INVALID_ARG;
+    if (motion_out && !aligned(motion_out[k], 4)) return SF_ERR_INVALID_ARG;
+  }
+  if ((points_out || chain_valid_out) && !aligned(points_out, 4)) return SF_ERR_INVALID_ARG;
+  const SequencePlan plan(W, H, p, K, learned);
+  if (ws_bytes < plan.total || !aligned(workspace, 256) || (learned && !aligned(packed, 16)))
+    return SF_ERR_INVALID_ARG;
+  uint8_t* ws = (uint8_t*)workspace;
+  cudaStream_t s = (cudaStream_t)stream;
+  float* disp[SF_MAX_FRAMES];
+  for (int k = 0; k < K; k++) disp[k] = disp_out ? disp_out[k] : plan.disp_map(ws, k, W, H);
+  // every stereo frame once, a group of frames per set of launches
+  for (int g = 0; g < K; g += plan.group) {
+    const int n = std::min(plan.group, K - g);
+    if (learned) {
+      st = run_learned_pairs(n, left + g, right + g, W, H, pitch, p, packed, threshold, nullptr, nullptr, nullptr,
+                             disp + g, nullptr, ws, s);
+    } else if (fused_eligible(W, H, p)) {
+      st = run_fused_pairs(left + g, right + g, n, W, H, pitch, p, nullptr, nullptr, nullptr, disp + g, ws, s);
+    } else {
+      for (int k = g; k < g + n && st == SF_OK; k++)
+        st = sgm_full_impl(left[k], right[k], W, H, pitch, p, nullptr, nullptr, nullptr, disp[k], ws, s);
+    }
+    if (st != SF_OK) return st;
+  }
+  if (s4_out) {
+    for (int k = 0; k + 1 < K; k++)
+      SF_TRY_CUDA(launch_combine(disp[k], disp[k + 1], flows[k], W, H, cam->f, cam->B, cam->cx, cam->cy, s4_out[k],
+                                 motion_out ? motion_out[k] : nullptr, nullptr, valid_out[k], s));
+  }
+  if (points_out || chain_valid_out) {
+    const float* dconst[SF_MAX_FRAMES];
+    for (int k = 0; k < K; k++) dconst[k] = disp[k];
+    SF_TRY_CUDA(launch_chain(dconst, flows, K, W, H, cam->f, cam->B, cam->cx, cam->cy, points_out, chain_valid_out,
+                             s));
   }
   return SF_OK;
 }

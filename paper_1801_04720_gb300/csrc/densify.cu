@@ -1,0 +1,236 @@
+// Densification of the sparse scene flow: the paper's future work (Sec. 5);
+// its Table 1 also reports the dense result the benchmark makes from a sparse
+// submission by filling the gaps (Sec. 4.1).
+//
+// A sparse map (NaN = missing) is filled along each row, then, for the rows
+// with nothing kept, along each column of the row-filled map.  Within a line
+// a missing pixel between kept values a (before) and b (after) takes
+//   mode 0 (background): min(a, b), the farther surface for a disparity;
+//   mode 1 (edge-aware): the value whose guide intensity is closer to the
+//                        pixel's own, min(a, b) on a tie;
+// with one kept side it takes that value; a line with nothing kept stays
+// missing.
+//
+// Kernels (no scratch: the output buffer carries the intermediate state):
+//   fill_rows_kernel: one warp per row.  A forward pass over 32-pixel chunks
+//     finds, with a ballot and a carry from the previous chunks, the nearest
+//     kept pixel at or before each pixel and parks its index in the output
+//     (as the bits of the float); a backward pass finds the nearest kept
+//     pixel after it the same way and writes the filled value.
+//   fill_cols_kernel: one thread per column, reading the row-filled map in
+//     coalesced rows; a row that stayed missing takes the nearest filled rows
+//     above and below (found once per run of empty rows).
+//   backproject_kernel: (u, v) from the flow, the filled d0 and d1, and the
+//     back-projection of Sec. 3.3 at every pixel.
+#include <math.h>
+
+#include "sf_internal.cuh"
+
+namespace sf {
+
+namespace {
+
+struct FillArgs {
+  const float* in[2];     // map m: element (y, x) at in[m][(y * W + x) * istride]
+  float* out[2];          // likewise with ostride
+  int istride, ostride, nmaps, W, H, mode;
+  const uint8_t* guide;   // [H][gpitch], mode 1
+  int gpitch;
+};
+
+__device__ __forceinline__ float fnan() { return __int_as_float(0x7fc00000); }
+
+// the fill value between kept values va (at guide index ia) and vb (ib) for
+// the pixel at guide index ip
+__device__ __forceinline__ float choose(const FillArgs& a, float va, float vb, size_t ip, size_t ia, size_t ib) {
+  if (a.mode == 1) {
+    const int g = a.guide[ip];
+    const int da = abs(g - (int)a.guide[ia]), db = abs(g - (int)a.guide[ib]);
+    if (da < db) return va;
+    if (db < da) return vb;
+  }
+  return fminf(va, vb);
+}
+
+__global__ void __launch_bounds__(256) fill_rows_kernel(const FillArgs a) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= a.nmaps * a.H) return;
+  const int m = warp / a.H, y = warp - m * a.H;
+  const float* in = a.in[m];
+  float* out = a.out[m];
+  const int W = a.W;
+  const size_t row = (size_t)y * W;
+  auto at_in = [&](int x) { return in[(row + x) * a.istride]; };
+  const unsigned below = (2u << lane) - 1u;   // lanes 0 .. lane
+  const unsigned above = ~((1u << lane) - 1u); // lanes lane .. 31
+  // forward: index of the nearest kept pixel at or before x (-1: none)
+  int carry = -1;
+  for (int c = 0; c < W; c += 32) {
+    const int x = c + lane;
+    const float v = x < W ? at_in(x) : fnan();
+    const bool ok = x < W && !isnan(v);
+    const unsigned b = __ballot_sync(0xffffffffu, ok);
+    const unsigned mb = b & below;
+    const int left = mb ? c + 31 - __clz(mb) : carry;
+    if (x < W) out[(row + x) * a.ostride] = ok ? v : __int_as_float(left);
+    if (b) carry = c + 31 - __clz(b);
+  }
+  __syncwarp();
+  // backward: the nearest kept pixel at or after x, and the filled value
+  carry = -1;
+  const int last = ((W - 1) / 32) * 32;
+  for (int c = last; c >= 0; c -= 32) {
+    const int x = c + lane;
+    const float v = x < W ? at_in(x) : fnan();
+    const bool ok = x < W && !isnan(v);
+    const unsigned b = __ballot_sync(0xffffffffu, ok);
+    const unsigned mb = b & above;
+    const int right = mb ? c + __ffs(mb) - 1 : carry;
+    if (x < W && !ok) {
+      const int left = __float_as_int(out[(row + x) * a.ostride]);
+      float r;
+      if (left >= 0 && right >= 0)
+        r = choose(a, at_in(left), at_in(right), (size_t)y * a.gpitch + x, (size_t)y * a.gpitch + left,
+                   (size_t)y * a.gpitch + right);
+      else if (left >= 0)
+        r = at_in(left);
+      else if (right >= 0)
+        r = at_in(right);
+      else
+        r = fnan();
+      out[(row + x) * a.ostride] = r;
+    }
+    if (b) carry = c + __ffs(b) - 1;
+  }
+}
+
+// A row the row pass left missing is missing at every x, so each column
+// thread sees the same rows as empty.
+__global__ void __launch_bounds__(256) fill_cols_kernel(const FillArgs a) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)a.nmaps * a.W) return;
+  const int m = (int)(tid / a.W), x = (int)(tid - (long long)m * a.W);
+  float* out = a.out[m];
+  const int W = a.W, H = a.H;
+  auto at = [&](int y) -> float& { return out[((size_t)y * W + x) * a.ostride]; };
+  int ya = -1, yb = -1;   // nearest filled rows above and below the current run
+  for (int y = 0; y < H; y++) {
+    if (!isnan(at(y))) {
+      ya = y;
+      continue;
+    }
+    if (yb <= y) {
+      yb = -1;
+      for (int k = y + 1; k < H; k++)
+        if (!isnan(at(k))) {
+          yb = k;
+          break;
+        }
+      if (yb < 0) yb = H;   // none below: the rest of the column
+    }
+    float r;
+    if (ya >= 0 && yb < H)
+      r = choose(a, at(ya), at(yb), (size_t)y * a.gpitch + x, (size_t)ya * a.gpitch + x,
+                 (size_t)yb * a.gpitch + x);
+    else if (ya >= 0)
+      r = at(ya);
+    else if (yb < H)
+      r = at(yb);
+    else
+      r = fnan();
+    at(y) = r;   // ya stays the last row filled by the row pass
+  }
+}
+
+// Dense scene flow: filled d0, d1 already in s4 channels 2 and 3.
+__global__ void __launch_bounds__(256)
+    backproject_kernel(const float2* __restrict__ flow, int W, int H, float f, float B, float cx, float cy,
+                       float4* __restrict__ s4, float* __restrict__ motion, float* __restrict__ point,
+                       uint8_t* __restrict__ valid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= W * H) return;
+  const int y = i / W, x = i - y * W;
+  const float2 uv = flow[i];
+  const float4 cur = s4[i];
+  const float d0 = cur.z, d1 = cur.w;
+  const bool ok = !isnan(d0) && !isnan(d1) && d0 > 0.0f && d1 > 0.0f;
+  valid[i] = ok;
+  const float nan = fnan();
+  if (!ok) {
+    s4[i] = make_float4(nan, nan, nan, nan);
+    if (motion) motion[3 * i] = motion[3 * i + 1] = motion[3 * i + 2] = nan;
+    if (point) point[3 * i] = point[3 * i + 1] = point[3 * i + 2] = nan;
+    return;
+  }
+  const float xp = __fadd_rn((float)x, uv.x);
+  const float yp = __fadd_rn((float)y, uv.y);
+  s4[i] = make_float4(uv.x, uv.y, d0, d1);
+  const float z0 = __fdiv_rn(f * B, d0), z1 = __fdiv_rn(f * B, d1);
+  const float p0x = __fdiv_rn(((float)x - cx) * B, d0), p0y = __fdiv_rn(((float)y - cy) * B, d0);
+  const float p1x = __fdiv_rn((xp - cx) * B, d1), p1y = __fdiv_rn((yp - cy) * B, d1);
+  if (motion) {
+    motion[3 * i] = p1x - p0x;
+    motion[3 * i + 1] = p1y - p0y;
+    motion[3 * i + 2] = z1 - z0;
+  }
+  if (point) {
+    point[3 * i] = p0x;
+    point[3 * i + 1] = p0y;
+    point[3 * i + 2] = z0;
+  }
+}
+
+cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
+  const long long rows = (long long)a.nmaps * a.H;
+  fill_rows_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
+  const long long cols = (long long)a.nmaps * a.W;
+  fill_cols_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(a);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fill_map(const float* in, int W, int H, const uint8_t* guide, int gpitch, int mode, float* out,
+                            cudaStream_t s) {
+  StageTrace trace(SF_STAGE_DENSIFY, s);
+  FillArgs a{};
+  a.in[0] = in;
+  a.out[0] = out;
+  a.istride = a.ostride = 1;
+  a.nmaps = 1;
+  a.W = W;
+  a.H = H;
+  a.mode = mode;
+  a.guide = guide;
+  a.gpitch = gpitch;
+  return launch_fill(a, s);
+}
+
+cudaError_t launch_densify(const float* s4_in, const float* flow, int W, int H, float f, float B, float cx, float cy,
+                           const uint8_t* guide, int gpitch, int mode, float* s4_out, float* motion, float* point,
+                           uint8_t* valid, cudaStream_t s) {
+  StageTrace trace(SF_STAGE_DENSIFY, s);
+  FillArgs a{};
+  a.in[0] = s4_in + 2;     // d0
+  a.in[1] = s4_in + 3;     // d1 (the warped disparity of t+1, at the reference pixel)
+  a.out[0] = s4_out + 2;
+  a.out[1] = s4_out + 3;
+  a.istride = a.ostride = 4;
+  a.nmaps = 2;
+  a.W = W;
+  a.H = H;
+  a.mode = mode;
+  a.guide = guide;
+  a.gpitch = gpitch;
+  cudaError_t e = launch_fill(a, s);
+  if (e != cudaSuccess) return e;
+  const int n = W * H;
+  backproject_kernel<<<(n + 255) / 256, 256, 0, s>>>(reinterpret_cast<const float2*>(flow), W, H, f, B, cx, cy,
+                                                     reinterpret_cast<float4*>(s4_out), motion, point, valid);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace sf

@@ -89,5 +89,14 @@ cudaError_t launch_lr_check(const int16_t* dL, const int16_t* dR, const float* d
 cudaError_t launch_combine(const float* D0, const float* D1, const float* flow, int W, int H,
                            float f, float B, float cx, float cy, float* s4, float* motion,
                            float* point, uint8_t* valid, cudaStream_t s);
+// trajectories through K frames (sequence.cu)
+cudaError_t launch_chain(const float* const* disps, const float* const* flows, int K, int W, int H, float f,
+                         float B, float cx, float cy, float* points, uint8_t* valid, cudaStream_t s);
+// densification (densify.cu); mode 0 background, 1 edge-aware (guide needed)
+cudaError_t launch_fill_map(const float* in, int W, int H, const uint8_t* guide, int gpitch, int mode, float* out,
+                            cudaStream_t s);
+cudaError_t launch_densify(const float* s4_in, const float* flow, int W, int H, float f, float B, float cx, float cy,
+                           const uint8_t* guide, int gpitch, int mode, float* s4_out, float* motion, float* point,
+                           uint8_t* valid, cudaStream_t s);
 
 }  // namespace sf

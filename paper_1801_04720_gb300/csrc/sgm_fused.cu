@@ -557,9 +557,13 @@ constexpr int sweep_max_regs(int nt, int ctas) {
   return budget > 168 ? 168 : (budget / 8) * 8;
 }
 
+// two CTAs per SM for a merged launch where that leaves a thread at least
+// 128 registers, else one
+constexpr int merged_ctas(int nt) { return 65536 / (2 * nt) >= 128 ? 2 : 1; }
+
 template <int DC, int CHUNKS, int HALO, int MODE>
 __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
-    __maxnreg__(MODE == kModeMerged ? sweep_max_regs((16 + HALO) * CHUNKS, 2)
+    __maxnreg__(MODE == kModeMerged ? sweep_max_regs((16 + HALO) * CHUNKS, merged_ctas((16 + HALO) * CHUNKS))
                                     : (DC == 16 ? 168 : sweep_max_regs((16 + HALO) * CHUNKS, 1)))
     sweep_kernel(const __grid_constant__ SweepArgs a) {
   using Cfg = SweepCfg<DC, CHUNKS, HALO, MODE>;
@@ -1250,12 +1254,16 @@ static int chunks_for(int dc, int D) {
   return c;
 }
 
+// Built-in rule: both scan orders in one launch with 16 disparities per
+// thread and bands of 9 rows (two CTAs per SM up to D = 128; measured the
+// fastest at 1242 x 375, D = 128 on GB300: 1.38 ms a frame against 1.58 ms
+// for the best two-launch shape); 8 disparities per thread up to D = 32.
 static Shape builtin_shape(int D) {
   Shape s;
-  s.dc = D > 128 ? 16 : 8;
+  s.dc = D > 32 ? 16 : 8;
   s.chunks = chunks_for(s.dc, D);
-  s.halo = s.dc == 8 ? 16 : 8;
-  s.order = 0;
+  s.halo = 8;
+  s.order = 1;
   return s;
 }
 

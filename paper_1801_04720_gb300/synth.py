@@ -264,18 +264,11 @@ def _shade(surfaces, k, s, t, noise: GradientNoise):
     return img
 
 
-def automotive(seed=0, W=1242, H=375, D=128, n_segments=20, f=721.5, B=0.54,
-               disp_range=(2.0, 120.0), max_translation=1.5, max_yaw_deg=3.0,
-               pixel_noise=2.0, flow_noise=0.5):
-    """Automotive-shaped quadruple (the 1242x375, D=128 recipe).
-
-    A far wall (disparity ``disp_range[0]``) and a ground plane form the
-    static background; ``n_segments`` slanted textured rectangles with
-    disparities inside ``disp_range`` each move rigidly (translation up to
-    ``max_translation`` m, yaw up to ``max_yaw_deg``).  Images carry
-    N(0, pixel_noise) sensor noise; the input flow is the induced flow plus
-    N(0, flow_noise) px."""
-    rng = np.random.default_rng(seed)
+def _automotive_scene(rng, W, H, f, B, n_segments, disp_range, max_translation, max_yaw_deg, frames=2):
+    """Camera, texture noise, surfaces and per-surface rigid motions of the
+    automotive recipe.  Segments are placed so that every one of `frames`
+    poses (the motion applied 0 .. frames-1 times) stays inside the
+    disparity range."""
     cam = Camera(f=f, B=B, cx=(W - 1) / 2.0, cy=(H - 1) / 2.0)
     fB = f * B
     noise = GradientNoise(rng)
@@ -316,9 +309,11 @@ def automotive(seed=0, W=1242, H=375, D=128, n_segments=20, f=721.5, B=0.54,
         Rm = _yaw(theta)
         # rigid motion about the segment's centre: X' = Rm (X - c) + c + T
         Tm = centre - Rm @ centre + T
-        moved = _moved(surf, Rm, Tm)
+        poses = [surf]
+        for _ in range(frames - 1):
+            poses.append(_moved(poses[-1], Rm, Tm))
         ok = True
-        for sf in (surf, moved):
+        for sf in poses:
             for a in (-1, 1):
                 for b in (-1, 1):
                     corner = sf.centre + a * sf.half[0] * sf.e1 + b * sf.half[1] * sf.e2
@@ -333,6 +328,23 @@ def automotive(seed=0, W=1242, H=375, D=128, n_segments=20, f=721.5, B=0.54,
         surfaces.append(surf)
         motions.append((Rm, Tm))
 
+    return cam, fB, noise, surfaces, motions
+
+
+def automotive(seed=0, W=1242, H=375, D=128, n_segments=20, f=721.5, B=0.54,
+               disp_range=(2.0, 120.0), max_translation=1.5, max_yaw_deg=3.0,
+               pixel_noise=2.0, flow_noise=0.5):
+    """Automotive-shaped quadruple (the 1242x375, D=128 recipe).
+
+    A far wall (disparity ``disp_range[0]``) and a ground plane form the
+    static background; ``n_segments`` slanted textured rectangles with
+    disparities inside ``disp_range`` each move rigidly (translation up to
+    ``max_translation`` m, yaw up to ``max_yaw_deg``).  Images carry
+    N(0, pixel_noise) sensor noise; the input flow is the induced flow plus
+    N(0, flow_noise) px."""
+    rng = np.random.default_rng(seed)
+    cam, fB, noise, surfaces, motions = _automotive_scene(rng, W, H, f, B, n_segments, disp_range,
+                                                          max_translation, max_yaw_deg)
     surfaces_t1 = [_moved(s, R, T) for s, (R, T) in zip(surfaces, motions)]
     views = {}
     for name, surfs, ox in (("left_t", surfaces, 0.0), ("right_t", surfaces, B),
@@ -360,6 +372,66 @@ def automotive(seed=0, W=1242, H=375, D=128, n_segments=20, f=721.5, B=0.54,
     return Quad(views["left_t"], views["right_t"], views["left_t1"], views["right_t1"], flow, cam,
                 D, gt_d0, gt_d1, gt_flow, k_t.astype(np.int16),
                 extra={"n_segments": n_segments, "seed": seed})
+
+
+class Sequence:
+    """K consecutive stereo frames of one scene: lefts[k], rights[k] uint8
+    [H][W]; flows[k] float32 [H][W][2] from frame k to k+1 (induced flow plus
+    noise); ground truth gt_disp[k] (disparity of the visible surface),
+    gt_flow[k] and gt_next_disp[k] (the disparity at frame k+1 of the point
+    visible at frame k); only the frames rendered are filled (others None)."""
+
+    def __init__(self, K, camera, D):
+        self.K, self.camera, self.D = K, camera, D
+        self.lefts = [None] * K
+        self.rights = [None] * K
+        self.flows = [None] * (K - 1)
+        self.gt_disp = [None] * K
+        self.gt_flow = [None] * (K - 1)
+        self.gt_next_disp = [None] * (K - 1)
+
+
+def sequence(K, seed=0, W=2048, H=1024, D=256, n_segments=40, f=721.5, B=0.54, disp_range=(2.0, 120.0),
+             max_translation=0.25, max_yaw_deg=1.0, pixel_noise=2.0, flow_noise=0.5, frames=None):
+    """K consecutive frames of one evolving automotive-recipe scene: every
+    segment repeats its rigid motion (translation up to ``max_translation`` m,
+    yaw up to ``max_yaw_deg`` per frame) from frame to frame, and is placed so
+    that it stays inside the disparity range over all K frames.  The scene
+    depends on the seed alone and each frame's noise on (seed, frame), so a
+    subset ``frames`` can be rendered on its own (e.g. in parallel workers)
+    and the parts put together; the flow F_k needs frame k rendered."""
+    rng = np.random.default_rng(seed)
+    cam, fB, noise, surfaces, motions = _automotive_scene(rng, W, H, f, B, n_segments, disp_range,
+                                                          max_translation, max_yaw_deg, frames=K)
+    seq = Sequence(K, cam, D)
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    for k in (range(K) if frames is None else frames):
+        frng = np.random.default_rng([seed, k])
+        surfs = list(surfaces)
+        for _ in range(k):
+            surfs = [_moved(s_, R, T) for s_, (R, T) in zip(surfs, motions)]
+        for name, ox in (("left", 0.0), ("right", B)):
+            kk, z, s_, t = _cast(surfs, W, H, cam, ox)
+            img = _shade(surfs, kk, s_, t, noise) + frng.normal(0.0, pixel_noise, size=(H, W))
+            img = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+            if name == "left":
+                seq.lefts[k], k_t, z_t = img, kk, z
+            else:
+                seq.rights[k] = img
+        seq.gt_disp[k] = (fB / z_t).astype(np.float32)
+        if k + 1 < K:
+            P = np.stack([(xs - cam.cx) * z_t / f, (ys - cam.cy) * z_t / f, z_t], axis=-1)
+            P1 = np.empty_like(P)
+            for idx, (R, T) in enumerate(motions):
+                m = k_t == idx
+                P1[m] = P[m] @ R.T + T
+            x1 = f * P1[..., 0] / P1[..., 2] + cam.cx
+            y1 = f * P1[..., 1] / P1[..., 2] + cam.cy
+            gt = np.stack([x1 - xs, y1 - ys], axis=-1).astype(np.float32)
+            seq.gt_flow[k] = gt
+            seq.gt_next_disp[k] = (fB / P1[..., 2]).astype(np.float32)
+            seq.flows[k] = (gt + frng.normal(0.0, flow_noise, size=gt.shape)).astype(np.float32)
+    return seq
 
 
 def stream(n_frames, seed=0, W=2048, H=1024, D=256, n_segments=40, **kw):

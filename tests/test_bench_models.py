@@ -11,9 +11,12 @@ import pytest
 def test_sweep_bytes_model():
     import bench
     N, D = 1242 * 375, 128
-    # the partial sum of one scan order, uint16, written and read once per pass
-    assert bench.bytes_model("sgm_sweep", N, D) == 4 * 2 * N * D
-    assert bench.bytes_model("sgm_sweep", N, D) == 476_928_000
+    # the partial sum of one scan order, uint16, written and read once per
+    # pass: a launch per scan order does one of the two, a merged launch both
+    assert bench.bytes_model("sgm_sweep", N, D, order=0) == 4 * 2 * N * D
+    assert bench.bytes_model("sgm_sweep", N, D, order=0) == 476_928_000
+    assert bench.bytes_model("sgm_sweep", N, D, order=1) == 4 * 4 * N * D
+    assert bench.bytes_model("sgm_sweep", N, D) == 953_856_000
     assert bench.bytes_model("aggregate", N, D) == 3 * N * D
 
 
@@ -65,3 +68,21 @@ def test_measured_traffic_void_after_source_change(fake_root):
     fake_root.write_bytes(b"kernel v2")
     assert bench.measured_traffic("sgm_sweep", "16x16") is None
     assert bench.measured_traffic("aggregate") is None
+
+
+def test_all_cores_oracle_equals_the_oracle():
+    """The all-cores baseline runs the oracle's own functions on independent
+    units; its frame must be the single-thread oracle's frame."""
+    import numpy as np
+    import bench
+    from oracle import oracle
+    from paper_1801_04720_gb300 import synth
+    q = synth.fronto_planes(seed=4)
+    keep = {}
+    r = bench.cpu_baseline_all_cores(q, cores=2, D=q.D, keep=keep)
+    assert r["cores"] == 2 and r["value"] > 0 and r["cpu_model"]
+    c = q.camera
+    ref = oracle.scene_flow(q.images(), q.flow, c.f, c.B, c.cx, c.cy, D=q.D)
+    assert np.array_equal(keep["valid"], ref["valid"])
+    assert np.array_equal(keep["s4"], ref["s4"], equal_nan=True)
+    assert np.array_equal(keep["motion"], ref["motion"], equal_nan=True)

@@ -162,3 +162,37 @@ def test_graph_replayed_mixed_batch_every_item_against_oracle(sf):
         got = {k: to_np(o[k]) for k in ("s4", "motion", "point", "valid")}
         assert_sceneflow_close(got, r["s4"], r["motion"], r["point"], r["valid"])
         assert r["valid"].sum() > 0
+
+
+def test_batch_in_waves_equals_one_wave(sf):
+    """A wave limit bounds the batch workspace; the outputs stay bit-identical
+    (with and without graph replay)."""
+    import torch
+    quads = _quads([(96, 64, 16), (130, 41, 64), (160, 30, 192), (67, 53, 64), (200, 60, 32)], seed0=70)
+    p = sf.params()
+    scenes = [_scene(sf, q) for q in quads]
+    ref = _compare(sf, quads, graph=False)
+    full = sf.sf_batch_workspace_size(sf.make_batch(scenes, [sf.alloc_scene_flow_outputs(
+        q.shape[1], q.shape[0], "cuda") for q in quads]), p)
+    try:
+        sf.sf_set_batch_wave_limit(full // 3)
+        outs = [sf.alloc_scene_flow_outputs(q.shape[1], q.shape[0], "cuda") for q in quads]
+        items = sf.make_batch(scenes, outs)
+        capped = sf.sf_batch_workspace_size(items, p)
+        assert capped < full
+        ws = torch.empty(capped, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.Stream()
+        for graph in (False, True, True):
+            for o in outs:
+                for v in o.values():
+                    if v is not None:
+                        v.fill_(0)
+            sf.sf_batch_run(items, p, ws, graph=graph, stream=stream)
+            torch.cuda.synchronize()
+            for a, b in zip(outs, ref):
+                for k in ("s4", "motion", "point", "valid", "D0", "D1"):
+                    x, y = to_np(a[k]), to_np(b[k])
+                    assert np.array_equal(np.nan_to_num(x, nan=-9.0), np.nan_to_num(y, nan=-9.0)), k
+    finally:
+        sf.sf_set_batch_wave_limit(0)
+        sf.sf_batch_release_graphs()

@@ -89,7 +89,7 @@ def test_aggregate_random_cost(sf, oracle_mod, W, H, D, P1, P2, mask, staged):
 # Heights giving one band, two bands, an odd and an even band count at both
 # halo widths (bands of 9 or 17 rows), so the meeting band of the merged
 # launch falls on every kind of boundary.
-ORDER_CASES = [(70, 5, 32), (70, 9, 32), (70, 17, 64), (70, 18, 64), (130, 41, 128), (96, 52, 48),
+ORDER_CASES = [(70, 7, 32), (70, 9, 32), (70, 17, 64), (70, 18, 64), (130, 41, 128), (96, 52, 48),
                (61, 35, 16), (200, 64, 256)]
 
 

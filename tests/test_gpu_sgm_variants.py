@@ -1,0 +1,177 @@
+"""GPU parity of the SGM variants against the oracle: the intensity-adaptive
+P2 of the SGM cited in Sec. 3.1 (P2 / |I(p) - I(p-r)|, at least P1) and the
+uniqueness filter of the left winners.
+
+Aggregated costs and integer winners and masks are bit-exact, subpixel
+disparities within 1e-4 px, scene flow within 1e-5 relative, on both kernel
+families (fused band sweeps in every scheduling order and shape, staged
+per-path kernels), in the batch, and in the learned path (adaptive P2)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import (SUBPIXEL_ATOL, assert_nan_equal_close, assert_sceneflow_close, to_dev,
+                         to_np)
+from paper_1801_04720_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_04720_gb300 import _lib, build
+    build.build()
+    _lib.load()
+    return _lib
+
+
+def _guide(W, H, seed):
+    rng = np.random.default_rng(seed)
+    g = rng.integers(0, 256, size=(H, W), dtype=np.uint8)
+    g[H // 3:H // 2, W // 4:W // 2] = 77            # flat patch: steps of zero keep P2
+    g[:, -3:] = g[:, -4:-3] + np.arange(1, 4, dtype=np.uint8)   # small steps: large penalties
+    return g
+
+
+GUIDED = [(64, 48, 16), (67, 53, 33), (130, 41, 128), (96, 52, 48), (40, 30, 1), (50, 20, 256),
+          (70, 9, 32), (61, 18, 64)]
+
+
+@pytest.mark.parametrize("staged", [False, True])
+@pytest.mark.parametrize("W,H,D", GUIDED)
+def test_guided_aggregate_against_oracle(sf, oracle_mod, W, H, D, staged):
+    rng = np.random.default_rng(W + 3 * H + 5 * D)
+    C = rng.integers(0, 63, size=(H, W, D), dtype=np.uint8)
+    g = _guide(W, H, D)
+    p = sf.params(D=D, adaptive_p2=True)
+    got = to_np(sf.sf_sgm_aggregate_guided(to_dev(C), to_dev(g), p, ws=None if staged else "auto"),
+                np.uint16)
+    exp = oracle_mod.aggregate(C, 7, 86, 0xFF, img=g)
+    assert np.array_equal(got.astype(np.int32), exp)
+    if D >= 3:      # with fewer disparities no change reaches two levels: P2 never applies
+        assert not np.array_equal(exp, oracle_mod.aggregate(C, 7, 86, 0xFF))
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("dc,halo", [(16, 8), (16, 16), (8, 8), (8, 16)])
+def test_guided_aggregate_every_schedule(sf, oracle_mod, dc, halo, order):
+    W, H, D = 97, 37, 64
+    rng = np.random.default_rng(dc + halo + order)
+    C = rng.integers(0, 63, size=(H, W, D), dtype=np.uint8)
+    g = _guide(W, H, 9)
+    p = sf.params(D=D, adaptive_p2=True)
+    try:
+        sf.sf_set_sweep_schedule(D, D, dc, halo, order)
+    except sf.SFError:
+        pytest.skip("shape not built for this D")
+    try:
+        got = to_np(sf.sf_sgm_aggregate_guided(to_dev(C), to_dev(g), p), np.uint16)
+    finally:
+        sf.sf_set_sweep_shape(D, D, 0, 0)
+    assert np.array_equal(got.astype(np.int32), oracle_mod.aggregate(C, 7, 86, 0xFF, img=g))
+
+
+def test_guided_aggregate_with_constant_p2_ignores_the_guide(sf, oracle_mod):
+    rng = np.random.default_rng(3)
+    C = rng.integers(0, 63, size=(30, 50, 32), dtype=np.uint8)
+    got = to_np(sf.sf_sgm_aggregate_guided(to_dev(C), to_dev(_guide(50, 30, 1)), sf.params(D=32)), np.uint16)
+    assert np.array_equal(got.astype(np.int32), oracle_mod.aggregate(C, 7, 86, 0xFF))
+
+
+VARIANTS = [(True, 0), (False, 15), (True, 10)]
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("adaptive,unique", VARIANTS)
+@pytest.mark.parametrize("W,H,D,seed", [(96, 64, 16, 0), (130, 41, 32, 1), (97, 40, 64, 2)])
+def test_sgm_full_variants_against_oracle(sf, oracle_mod, W, H, D, seed, adaptive, unique, fused):
+    q = synth.fronto_planes(W=W, H=H, D=D, disparities=(2, D // 3, D - 5), seed=seed)
+    p = sf.params(D=D, adaptive_p2=adaptive, uniqueness=unique)
+    sf.sf_set_fused(fused)
+    try:
+        out = sf.sf_sgm_full(to_dev(q.left_t), to_dev(q.right_t), p)
+    finally:
+        sf.sf_set_fused(True)
+    r = oracle_mod.disparity(q.left_t, q.right_t, D=D, adaptive_p2=adaptive, uniqueness=unique)
+    assert np.array_equal(to_np(out["dL"]), r["dL"])
+    assert np.array_equal(to_np(out["dR"]), r["dR"])
+    assert np.array_equal(to_np(out["valid"]), r["valid"])
+    assert_nan_equal_close(to_np(out["disp"]), r["disp"], SUBPIXEL_ATOL, "disp")
+    if unique:
+        plain = oracle_mod.disparity(q.left_t, q.right_t, D=D, adaptive_p2=adaptive)
+        assert r["valid"].sum() < plain["valid"].sum()      # the filter removed something
+
+
+def test_automotive_scene_flow_variants_against_oracle(sf, oracle_mod):
+    q = synth.automotive(seed=5, W=192, H=64, D=48, n_segments=6)
+    cam = sf.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
+    p = sf.params(D=q.D, adaptive_p2=True, uniqueness=12)
+    out = sf.sf_scene_flow([to_dev(im) for im in q.images()], to_dev(q.flow), p, cam)
+    c = q.camera
+    r = oracle_mod.scene_flow(q.images(), q.flow, c.f, c.B, c.cx, c.cy, D=q.D, adaptive_p2=True,
+                              uniqueness=12)
+    assert_nan_equal_close(to_np(out["D0"]), r["t0"]["disp"], SUBPIXEL_ATOL, "D0")
+    assert_nan_equal_close(to_np(out["D1"]), r["t1"]["disp"], SUBPIXEL_ATOL, "D1")
+    got = {k: to_np(out[k]) for k in ("s4", "motion", "point", "valid")}
+    assert_sceneflow_close(got, r["s4"], r["motion"], r["point"], r["valid"])
+    assert r["valid"].sum() > 0
+
+
+def test_batch_variants_equal_per_instance_and_oracle(sf, oracle_mod):
+    import torch
+    quads = [synth.fronto_planes(W=W, H=H, D=D, disparities=(2, D // 3, D - 5), seed=40 + k)
+             for k, (W, H, D) in enumerate([(96, 64, 16), (130, 41, 64), (160, 30, 192)])]
+    p = sf.params(adaptive_p2=True, uniqueness=10)
+    scenes = [{"left_t": to_dev(q.left_t), "right_t": to_dev(q.right_t), "left_t1": to_dev(q.left_t1),
+               "right_t1": to_dev(q.right_t1), "flow": to_dev(q.flow), "D": q.D,
+               "cam": sf.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)} for q in quads]
+    outs = [sf.alloc_scene_flow_outputs(q.shape[1], q.shape[0], "cuda") for q in quads]
+    items = sf.make_batch(scenes, outs)
+    ws = torch.empty(sf.sf_batch_workspace_size(items, p), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    for _ in range(2):
+        sf.sf_batch_run(items, p, ws, graph=True, stream=stream)
+        torch.cuda.synchronize()
+    sf.sf_batch_release_graphs()
+    for q, sc, o in zip(quads, scenes, outs):
+        pq = sf.params(D=q.D, adaptive_p2=True, uniqueness=10)
+        ref = sf.sf_scene_flow([sc["left_t"], sc["right_t"], sc["left_t1"], sc["right_t1"]], sc["flow"], pq,
+                               sc["cam"])
+        for k in ("s4", "valid", "D0", "D1"):
+            a, b = to_np(o[k]), to_np(ref[k])
+            assert np.array_equal(np.nan_to_num(a, nan=-9.0), np.nan_to_num(b, nan=-9.0)), (q.D, k)
+    q, o = quads[0], outs[0]
+    r0 = oracle_mod.disparity(q.left_t, q.right_t, D=q.D, adaptive_p2=True, uniqueness=10)
+    assert_nan_equal_close(to_np(o["D0"]), r0["disp"], SUBPIXEL_ATOL, "D0")
+
+
+def test_learned_features_with_adaptive_p2(sf, oracle_mod):
+    from oracle import confnet_oracle as co
+    q = synth.fronto_planes(W=130, H=37, D=32, disparities=(2, 10, 27), seed=5)
+    p = sf.params(D=32, adaptive_p2=True)
+    out = sf.sf_sgm_learned(to_dev(q.left_t), to_dev(q.right_t), p, packed=None, features=True)
+    cL, cR = oracle_mod.census(q.left_t), oracle_mod.census(q.right_t)
+    C = oracle_mod.cost_volume(cL, cR, 32)
+    L = [oracle_mod.path_cost(C, 7, 86, r, img=q.left_t) for r in oracle_mod.DIRECTIONS]
+    feat, ds = co.features(sum(L), L, C)
+    assert np.array_equal(to_np(out["dint"]), ds)
+    got = (to_np(out["features"]).view(np.uint16).astype(np.uint32) << 16).view(np.float32)
+    assert np.array_equal(got.astype(np.float64), feat)
+
+
+def test_variant_parameters_are_checked(sf):
+    import torch
+    q = synth.fronto_planes(seed=0)
+    l, r = to_dev(q.left_t), to_dev(q.right_t)
+    for bad in (sf.params(D=16, adaptive_p2=2), sf.params(D=16, uniqueness=100),
+                sf.params(D=16, uniqueness=-1)):
+        with pytest.raises(sf.SFError):
+            sf.sf_sgm_full(l, r, bad)
+    C = torch.zeros((48, 64, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(sf.SFError):      # the adaptive P2 needs the guide image
+        sf.sf_sgm_aggregate(C, sf.params(D=16, adaptive_p2=True))
+    with pytest.raises(sf.SFError):      # the learned rule stands in for every check
+        sf.sf_sgm_learned(l, r, sf.params(D=16, uniqueness=5), packed=None)
+    torch.cuda.synchronize()
