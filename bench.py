@@ -158,13 +158,13 @@ def bytes_model(stage, N, D, passes=4, order=1):
     of the paths of one order must exist for every (p, d) when the opposite
     order reaches p: per SGM pass it is written once and read once (uint16,
     2*N*D bytes each way).  One launch covers the four passes of a frame.
-    With both scan orders in one launch (order 1) that launch does the write
-    and the read -> 4 * 4*N*D bytes; with one launch per order (order 0) each
-    does one of them -> 4 * 2*N*D bytes.
+    With both scan orders in one launch (orders 1 and 2) that launch does the
+    write and the read -> 4 * 4*N*D bytes; with one launch per order (order 0)
+    each does one of them -> 4 * 2*N*D bytes.
     aggregate (staged kernels): read the uint8 cost and write the uint16 sum
     once per pass -> 3*N*D bytes."""
     if stage == "sgm_sweep":
-        return passes * (4 if order == 1 else 2) * N * D
+        return passes * (4 if order >= 1 else 2) * N * D
     return 3 * N * D
 
 

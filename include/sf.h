@@ -463,7 +463,11 @@ sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t hal
  * then both vertical scan orders in ONE launch, started from opposite ends of
  * the image: each band of rows is finished (sums, winner, subpixel) by
  * whichever order reaches it second, the other having left its partial sum,
- * so twice as many band tasks are available at a time.  Integers are
+ * so twice as many band tasks are available at a time.  order = 2: order 1
+ * with the horizontal paths in the same launch: their row blocks head its
+ * task queue and the band tasks that finish rows wait for those rows' blocks,
+ * so the horizontal walks overlap the first half of the sweeps (batches of
+ * uneven items run them in their own launch, as in order 1).  Integers are
  * identical in every order and shape.  Other orders, or shapes the build
  * does not provide, return SF_ERR_UNSUPPORTED. */
 sf_status sf_set_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order);
@@ -509,9 +513,12 @@ uint64_t sf_kernel_launches(void);
  *   nothing sets; the waits run out, set the workspace error word
  *   (sf_check_workspace then returns SF_ERR_TIMEOUT) and the kernels return
  *   normally.  0 (the default) skips nothing.
+ * SF_DEBUG_HLINE_DC: disparities per thread of the horizontal-path kernel for
+ *   D > 64, 16 or 32 (0 restores the default, 16); results are identical.
  * Process-wide; not for production use. */
 #define SF_DEBUG_SPIN_LIMIT 1
 #define SF_DEBUG_SKIP_TASKS 2
+#define SF_DEBUG_HLINE_DC 3
 sf_status sf_debug_set(int32_t key, int64_t value);
 
 /* Process-wide choice between the fused stereo kernels (1, default) and the

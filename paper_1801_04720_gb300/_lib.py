@@ -41,6 +41,7 @@ EXPORTED = [
 
 SF_DEBUG_SPIN_LIMIT = 1
 SF_DEBUG_SKIP_TASKS = 2
+SF_DEBUG_HLINE_DC = 3
 
 SF_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 

@@ -3,7 +3,7 @@
 For each class of disparity counts it times every candidate (disparities per
 thread dc, halo width, and the scheduling order of the paths: 0 = down sweep
 then up sweep in two launches, 1 = both scan orders in one launch meeting in
-the middle) on a synthetic quadruple of the requested size through
+the middle, 2 = that launch with the horizontal paths in its queue too) on a synthetic quadruple of the requested size through
 sf_scene_flow, keeps the fastest, and stores the choice in a JSON cache keyed
 by GPU name and size.  ``apply`` installs a cached choice with
 sf_set_sweep_schedule.  Every candidate computes identical integers; only the
@@ -21,7 +21,8 @@ from . import _lib, synth
 
 # (dc, halo, order)
 CANDIDATES = [(8, 16, 0), (8, 8, 0), (16, 8, 0), (16, 16, 0),
-              (16, 8, 1), (16, 16, 1), (8, 8, 1), (8, 16, 1)]
+              (16, 8, 1), (16, 16, 1), (8, 8, 1), (8, 16, 1),
+              (16, 8, 2), (16, 16, 2), (8, 8, 2), (8, 16, 2)]
 DEFAULT_CLASSES = [(1, 32), (33, 64), (65, 128), (129, 256)]
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 

@@ -94,6 +94,11 @@ sf_status check_params(const sf_sgm_params* p, int32_t W, int32_t H) {
 
 bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+// Completion flags of the horizontal paths' row blocks of one pass (two
+// directions, row blocks of at least 16 rows) for the launch that runs them
+// beside the sweeps.
+inline int flags_h_count(int H) { return 2 * ((H + 15) / 16); }
+
 // Workspace of sf_sgm_full / sf_scene_flow, carved with 256-byte alignment.
 struct Workspace {
   size_t cost, agg, dL, dR, dsub, disp0, disp1, total;
@@ -200,7 +205,7 @@ struct FusedPlan {
       const int J = (ps[i].W + fused::kTW - 1) / fused::kTW;
       for (int k = 0; k < 2; k++) {
         pairs[i].pass[k].flags = c;
-        c += (size_t)2 * J * sizeof(int);
+        c += (size_t)(2 * J + flags_h_count(ps[i].H)) * sizeof(int);
       }
     }
     control_bytes = align_up(c, 256);
@@ -260,6 +265,7 @@ fused::PassDesc pass_desc(uint8_t* ws, const FusedPlan& plan, const PairBuffers&
   d.bs = ws + pb.bs;
   d.flags_down = reinterpret_cast<int*>(ws + pb.flags);
   d.flags_up = d.flags_down + d.J;
+  d.flags_h = d.flags_up + d.J;
   d.dint = reinterpret_cast<int16_t*>(ws + pb.dint);
   d.dsub = nullptr;
   d.S = nullptr;
@@ -318,7 +324,11 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
                      const int* tab_dev, const TaskTables* tt, int* counters, int* err,
                      cudaStream_t s, bool tuned = true) {
   const bool inl = d_dev_down == nullptr;
-  const bool merged = fused::shape_for(Dshape, tuned).order == 1;
+  const fused::Shape shape = fused::shape_for(Dshape, tuned);
+  const bool merged = shape.order >= 1;
+  // the horizontal paths inside the sweep launch: passes of one size (the
+  // batch's uneven passes keep their own launch)
+  const bool with_h = shape.order == 2 && inl;
   fused::HLineArgs ha{};
   ha.P1 = p->P1; ha.P2 = p->P2; ha.Dmax = Dshape; ha.npass = npass; ha.path_mask = p->path_mask;
   ha.builtin_shape = tuned ? 0 : 1;
@@ -327,6 +337,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
   sa.builtin_shape = tuned ? 0 : 1;
   sa.P1 = p->P1; sa.P2 = p->P2; sa.subpixel = p->subpixel; sa.Dmax = Dshape; sa.npass = npass;
   sa.unique = p->uniqueness;
+  sa.variants = (p->adaptive_p2 || p->uniqueness) ? 1 : 0;
   sa.path_mask = p->path_mask;
   sa.en_h0 = (p->path_mask >> 0) & 1u;
   sa.en_h1 = (p->path_mask >> 1) & 1u;
@@ -350,7 +361,14 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     sa.nbands = tt->nbands;
     sa.ntasks = tt->ntasks;
   }
-  SF_TRY_CUDA(fused::launch_hline(ha, s));
+  if (with_h) {
+    const int rows = 2 * (16 + shape.halo);
+    sa.hl_blocks = (d[0].H + rows - 1) / rows;
+    sa.hl_tasks = npass * 2 * sa.hl_blocks;
+    sa.ntasks += sa.hl_tasks;
+  } else {
+    SF_TRY_CUDA(fused::launch_hline(ha, s));
+  }
   sa.task_counter = counters;
   if (const int skip = g_skip_down_tasks.load(std::memory_order_relaxed)) {
     static int skip_host;
@@ -365,7 +383,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     } else {
       sa.pass_ptr = d_dev_up;
     }
-    SF_TRY_CUDA(fused::launch_sweep(sa, 2, s));
+    SF_TRY_CUDA(fused::launch_sweep(sa, with_h ? 3 : 2, s));
     return SF_OK;
   }
   SF_TRY_CUDA(fused::launch_sweep(sa, 0, s));
@@ -534,7 +552,7 @@ BatchSetup batch_setup(const sf_batch_item* items, int n, const sf_sgm_params* p
       tmp[k].J = (ps.W + fused::kTW - 1) / fused::kTW;
       tmp[k].nb = nb_of(c.pass_ids[k]);
     }
-    c.tt = build_tables(tmp.data(), (int)tmp.size(), c.sh.order == 1);
+    c.tt = build_tables(tmp.data(), (int)tmp.size(), c.sh.order >= 1);   // orders 1 and 2: one merged launch
     c.off_down = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
     c.off_up = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
     c.off_tab = o; o = align_up(o + c.tt.ints.size() * sizeof(int), 256);
@@ -1013,6 +1031,9 @@ sf_status sf_debug_set(int32_t key, int64_t value) {
     g_skip_down_tasks.store((int)value, std::memory_order_relaxed);
     return SF_OK;
   }
+  if (key == SF_DEBUG_HLINE_DC) {
+    return fused::set_hline_dc(value == 0 ? 16 : (int)value) == 0 ? SF_OK : SF_ERR_INVALID_ARG;
+  }
   return SF_ERR_INVALID_ARG;
 }
 
@@ -1178,7 +1199,7 @@ struct NoallocLayout {
     size_t c = 0;
     err = c; c += sizeof(int);
     counters = c; c += 2 * sizeof(int);
-    flags = c; c += (size_t)2 * J * sizeof(int);
+    flags = c; c += (size_t)(2 * J + flags_h_count(H)) * sizeof(int);
     control_bytes = align_up(c, 256);
     size_t o = control_bytes;
     hf = o; o = align_up(o + N * Dp, 256);
@@ -1218,6 +1239,7 @@ extern "C" sf_status sf_sgm_aggregate_noalloc(const uint8_t* cost, int32_t W, in
   d.bs = ws + lay.bs;
   d.flags_down = reinterpret_cast<int*>(ws + lay.flags);
   d.flags_up = d.flags_down + d.J;
+  d.flags_h = d.flags_up + d.J;
   d.dint = nullptr;
   d.dsub = nullptr;
   d.S = agg_out;
@@ -1253,7 +1275,7 @@ struct LearnedPlan {
     counters = c; c += 2 * sizeof(int);
     for (int k = 0; k < npairs; k++) {
       pr[k].flags = c;
-      c += (size_t)2 * J * sizeof(int);
+      c += (size_t)(2 * J + flags_h_count(H)) * sizeof(int);
     }
     control_bytes = align_up(c, 256);
     size_t o = control_bytes;
@@ -1331,6 +1353,7 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
     pd.bs = ws + b.bs;
     pd.flags_down = reinterpret_cast<int*>(ws + b.flags);
     pd.flags_up = pd.flags_down + J;
+    pd.flags_h = pd.flags_up + J;
     pd.dint = nullptr;
     pd.dsub = nullptr;
     pd.S = reinterpret_cast<uint16_t*>(ws + b.S);

@@ -17,9 +17,9 @@
 //     kept pixel at or before each pixel and parks its index in the output
 //     (as the bits of the float); a backward pass finds the nearest kept
 //     pixel after it the same way and writes the filled value.
-//   fill_cols_kernel: one thread per column, reading the row-filled map in
-//     coalesced rows; a row that stayed missing takes the nearest filled rows
-//     above and below (found once per run of empty rows).
+//   fill_cols_kernel: the rows the row pass left missing (the same in every
+//     column) are marked once per block; one thread per column fills them
+//     from the nearest filled rows above and below.
 //   backproject_kernel: (u, v) from the flow, the filled d0 and d1, and the
 //     back-projection of Sec. 3.3 at every pixel.
 #include <math.h>
@@ -105,41 +105,59 @@ __global__ void __launch_bounds__(256) fill_rows_kernel(const FillArgs a) {
   }
 }
 
-// A row the row pass left missing is missing at every x, so each column
-// thread sees the same rows as empty.
+// The row pass leaves a row either filled at every x or missing at every x
+// (nothing kept in it), so the rows the column pass must fill are the same in
+// every column.  A block marks them once (a bit per row in shared memory,
+// read from its own first column, which no other block writes and this one
+// writes only after the marks are made), then each thread fills its own
+// column at those rows only: the nearest rows above and below that the row
+// pass filled.
+constexpr int kMaxRowWords = (32767 + 31) / 32;
+
 __global__ void __launch_bounds__(256) fill_cols_kernel(const FillArgs a) {
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)a.nmaps * a.W) return;
-  const int m = (int)(tid / a.W), x = (int)(tid - (long long)m * a.W);
-  float* out = a.out[m];
+  __shared__ uint32_t empty[kMaxRowWords];
   const int W = a.W, H = a.H;
+  const int cols_per_map = (W + blockDim.x - 1) / blockDim.x;
+  const int m = blockIdx.x / cols_per_map;
+  const int x0 = (blockIdx.x - m * cols_per_map) * blockDim.x;
+  const int x = x0 + threadIdx.x;
+  float* out = a.out[m];
+  const int words = (H + 31) / 32;
+  for (int w = threadIdx.x; w < words; w += blockDim.x) {
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; b++) {
+      const int y = 32 * w + b;
+      if (y < H && isnan(out[((size_t)y * W + x0) * a.ostride])) bits |= 1u << b;
+    }
+    empty[w] = bits;
+  }
+  __syncthreads();
+  if (x >= W) return;
   auto at = [&](int y) -> float& { return out[((size_t)y * W + x) * a.ostride]; };
-  int ya = -1, yb = -1;   // nearest filled rows above and below the current run
-  for (int y = 0; y < H; y++) {
-    if (!isnan(at(y))) {
-      ya = y;
-      continue;
+  auto is_empty = [&](int y) { return (empty[y >> 5] >> (y & 31)) & 1u; };
+  int ya = -1, yb = -1;   // nearest filled rows above and below the current run of empty rows
+  for (int w = 0; w < words; w++) {
+    uint32_t bits = empty[w];
+    while (bits) {
+      const int y = 32 * w + __ffs(bits) - 1;
+      bits &= bits - 1;
+      if (yb <= y) {        // the first empty row of a run: find its neighbours
+        ya = y - 1;
+        while (ya >= 0 && is_empty(ya)) ya--;
+        yb = y + 1;
+        while (yb < H && is_empty(yb)) yb++;
+      }
+      float r;
+      if (ya >= 0 && yb < H)
+        r = choose(a, at(ya), at(yb), (size_t)y * a.gpitch + x, (size_t)ya * a.gpitch + x, (size_t)yb * a.gpitch + x);
+      else if (ya >= 0)
+        r = at(ya);
+      else if (yb < H)
+        r = at(yb);
+      else
+        r = fnan();
+      at(y) = r;
     }
-    if (yb <= y) {
-      yb = -1;
-      for (int k = y + 1; k < H; k++)
-        if (!isnan(at(k))) {
-          yb = k;
-          break;
-        }
-      if (yb < 0) yb = H;   // none below: the rest of the column
-    }
-    float r;
-    if (ya >= 0 && yb < H)
-      r = choose(a, at(ya), at(yb), (size_t)y * a.gpitch + x, (size_t)ya * a.gpitch + x,
-                 (size_t)yb * a.gpitch + x);
-    else if (ya >= 0)
-      r = at(ya);
-    else if (yb < H)
-      r = at(yb);
-    else
-      r = fnan();
-    at(y) = r;   // ya stays the last row filled by the row pass
   }
 }
 
@@ -184,8 +202,8 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_fill(const FillArgs& a, cudaStream_t s) {
   const long long rows = (long long)a.nmaps * a.H;
   fill_rows_kernel<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(a);
-  const long long cols = (long long)a.nmaps * a.W;
-  fill_cols_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(a);
+  const long long blocks = (long long)a.nmaps * ((a.W + 255) / 256);
+  fill_cols_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -14,9 +14,11 @@ constexpr int kMaxPass = 4;
 // Launch shape chosen by D: a thread owns DC disparities of two lines; the
 // disparities of a line pair are spread over `chunks` consecutive threads (a
 // power of two); the band sweeps carry `halo` extra columns on each side of
-// a strip and walk bands of halo + 1 rows.  `order` schedules the two scan
-// orders: 0 = the down sweep's launch, then the up sweep's; 1 = both in one
-// launch, meeting in the middle.
+// a strip and walk bands of halo + 1 rows.  `order` schedules the paths:
+// 0 = the horizontal paths' launch, the down sweep's, then the up sweep's;
+// 1 = the horizontal paths' launch, then both scan orders in one launch,
+// meeting in the middle; 2 = everything in one launch (the horizontal paths'
+// row blocks first in its queue).
 struct Shape {
   int dc, chunks, halo, order;
 };
@@ -38,6 +40,7 @@ struct PassDesc {
   uint8_t* bs;           // band-end states [2 orders][2][3][W][Dp] u8
   int* flags_down;       // [J] bands completed by the down sweep
   int* flags_up;         // [J] bands completed by the up sweep
+  int* flags_h;          // [2][ceil(H / 16)] row blocks of the horizontal paths done (merged launch with them)
   int16_t* dint;         // winner per pixel (up sweep), or nullptr
   float* dsub;           // subpixel winner (up sweep), or nullptr
   uint16_t* S;           // full aggregated cost [H][W][D] (up sweep), or nullptr
@@ -59,6 +62,8 @@ struct HLineArgs {
 struct SweepArgs {
   int P1, P2, subpixel, Dmax, npass, ntasks;
   int unique;                  // uniqueness ratio (percent) of the winners with a subpixel output, 0 = off
+  int hl_tasks, hl_blocks;     // launch mode 3: horizontal-path tasks at the queue head, row blocks per direction
+  int variants;                // 1: adaptive P2 or uniqueness requested (the kernels that compile them in)
   int builtin_shape;           // 1: ignore tuned shape overrides
   uint32_t path_mask;
   int en_h0, en_h1;
@@ -100,8 +105,14 @@ cudaError_t launch_cost_pair(const CostPairs& job, int W, int H, int D, int Dp, 
 // left-reference volumes only
 cudaError_t launch_cost_left(const CostPairs& job, int W, int H, int D, int Dp, int cmax, cudaStream_t s);
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s);
-// mode 0: down sweep, 1: up sweep, 2: both orders in one launch
+// disparities per thread of the horizontal paths for D > 64 (16 or 32; 0 = ok)
+int set_hline_dc(int dc);
+// mode 0: down sweep, 1: up sweep, 2: both orders in one launch, 3: mode 2
+// with the horizontal paths' row blocks at the head of its queue
 cudaError_t launch_sweep(const SweepArgs& a, int mode, cudaStream_t s);
+// the kernels without / with the SGM variants (sgm_sweep.cu, sgm_sweep_var.cu)
+cudaError_t launch_sweep_plain(const SweepArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_sweep_variants(const SweepArgs& a, int mode, cudaStream_t s);
 
 }  // namespace fused
 }  // namespace sf

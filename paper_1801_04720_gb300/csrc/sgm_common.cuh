@@ -43,6 +43,28 @@ template <> struct ByteVec<16> {
   __device__ static T make(const uint32_t* w) { return make_uint4(w[0], w[1], w[2], w[3]); }
   __device__ static T zero() { return make_uint4(0, 0, 0, 0); }
 };
+struct __align__(16) Bytes32 {
+  uint4 lo, hi;
+};
+template <> struct ByteVec<32> {
+  using T = Bytes32;
+  __device__ static void words(const T& v, uint32_t* w) {
+    w[0] = v.lo.x; w[1] = v.lo.y; w[2] = v.lo.z; w[3] = v.lo.w;
+    w[4] = v.hi.x; w[5] = v.hi.y; w[6] = v.hi.z; w[7] = v.hi.w;
+  }
+  __device__ static T make(const uint32_t* w) {
+    return T{make_uint4(w[0], w[1], w[2], w[3]), make_uint4(w[4], w[5], w[6], w[7])};
+  }
+  __device__ static T zero() { return T{make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)}; }
+};
+
+// Streaming (evict-first) store of DC bytes.
+__device__ __forceinline__ void store_cs(uint2* p, const uint2& v) { __stcs(p, v); }
+__device__ __forceinline__ void store_cs(uint4* p, const uint4& v) { __stcs(p, v); }
+__device__ __forceinline__ void store_cs(Bytes32* p, const Bytes32& v) {
+  __stcs(reinterpret_cast<uint4*>(p), v.lo);
+  __stcs(reinterpret_cast<uint4*>(p) + 1, v.hi);
+}
 
 // Two lines' DC uint8 values -> DC u16x2 registers (line A low lane, line B
 // high lane).  Only for values < 128 (matching costs): sign-replicating

@@ -32,7 +32,7 @@ def test_unsupported_shapes_are_rejected(lib, lo, hi, dc, halo):
         lib.sf_set_sweep_shape(lo, hi, dc, halo)
 
 
-@pytest.mark.parametrize("order", [-1, 2, 7])
+@pytest.mark.parametrize("order", [-1, 3, 7])
 def test_unknown_scheduling_orders_are_rejected(lib, order):
     with pytest.raises(lib.SFError):
         lib.sf_set_sweep_schedule(65, 128, 16, 8, order)

@@ -116,7 +116,7 @@ def test_batch_rejects_bad_items(sf):
         sf.sf_batch_run(items, sf.params(), ws)
 
 
-@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("order", [0, 1, 2])
 @pytest.mark.parametrize("dc,halo", [(8, 8), (16, 8), (16, 16), (8, 16)])
 def test_tuned_shapes_are_bit_identical(sf, dc, halo, order):
     quads = _quads([(130, 41, 64), (97, 40, 128)], seed0=40)
@@ -195,4 +195,24 @@ def test_batch_in_waves_equals_one_wave(sf):
                     assert np.array_equal(np.nan_to_num(x, nan=-9.0), np.nan_to_num(y, nan=-9.0)), k
     finally:
         sf.sf_set_batch_wave_limit(0)
+        sf.sf_batch_release_graphs()
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_batch_under_every_scheduling_order(sf, order):
+    """The batch's descriptor tables follow the scheduling order of each class
+    (one launch per scan order, or both in one launch): bit-equal to
+    per-instance runs under every order, graph replay included."""
+    quads = _quads([(96, 64, 16), (130, 41, 64), (160, 30, 192), (97, 40, 100), (200, 60, 128)], seed0=80 + order)
+    try:
+        sf.sf_set_sweep_schedule(1, 256, 16, 8, order)
+    except sf.SFError:
+        sf.sf_set_sweep_schedule(33, 256, 16, 8, order)
+        sf.sf_set_sweep_schedule(1, 32, 8, 8, order)
+    try:
+        _compare(sf, quads, graph=True, repeats=2)
+    finally:
+        sf.sf_set_sweep_shape(1, 256, 0, 0)
+        sf.sf_set_sweep_shape(33, 256, 0, 0)
+        sf.sf_set_sweep_shape(1, 32, 0, 0)
         sf.sf_batch_release_graphs()

@@ -93,7 +93,7 @@ ORDER_CASES = [(70, 7, 32), (70, 9, 32), (70, 17, 64), (70, 18, 64), (130, 41, 1
                (61, 35, 16), (200, 64, 256)]
 
 
-@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("order", [0, 1, 2])
 @pytest.mark.parametrize("dc,halo", [(16, 8), (16, 16), (8, 8), (8, 16)])
 @pytest.mark.parametrize("W,H,D", ORDER_CASES)
 def test_aggregate_every_schedule_against_oracle(sf, oracle_mod, W, H, D, dc, halo, order):
@@ -276,3 +276,18 @@ def test_status_errors_on_gpu(sf):
         sf.sf_cost_volume(img, img, p, out=torch.empty((48, 64, 1), dtype=torch.uint8, device="cuda"))
     torch.cuda.synchronize()   # the context stays usable
     assert sf.sf_census(img).shape == (48, 64)
+
+
+@pytest.mark.parametrize("hdc", [16, 32])
+@pytest.mark.parametrize("W,H,D", [(130, 41, 128), (300, 23, 96), (97, 19, 256), (64, 30, 80)])
+def test_horizontal_chunk_widths_against_oracle(sf, oracle_mod, W, H, D, hdc):
+    """The horizontal paths with 16 or 32 disparities per thread (two or three
+    shuffle levels in each step's minimum): S bit-exact against the oracle."""
+    rng = np.random.default_rng(W + H + D + hdc)
+    C = rng.integers(0, 63, size=(H, W, D), dtype=np.uint8)
+    sf.sf_debug_set(sf.SF_DEBUG_HLINE_DC, hdc)
+    try:
+        got = to_np(sf.sf_sgm_aggregate(to_dev(C), sf.params(D=D)), np.uint16)
+    finally:
+        sf.sf_debug_set(sf.SF_DEBUG_HLINE_DC, 0)
+    assert np.array_equal(got.astype(np.int32), oracle_mod.aggregate(C, 7, 86, 0xFF))

@@ -54,7 +54,7 @@ def test_guided_aggregate_against_oracle(sf, oracle_mod, W, H, D, staged):
         assert not np.array_equal(exp, oracle_mod.aggregate(C, 7, 86, 0xFF))
 
 
-@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("order", [0, 1, 2])
 @pytest.mark.parametrize("dc,halo", [(16, 8), (16, 16), (8, 8), (8, 16)])
 def test_guided_aggregate_every_schedule(sf, oracle_mod, dc, halo, order):
     W, H, D = 97, 37, 64
