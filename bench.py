@@ -221,8 +221,10 @@ def run_ours(args, world, rank, local):
         tuned = {"classes": [{"lo": 65, "hi": 128, "dc": dc, "halo": halo, "order": order, "forced": True}]}
     elif not args.no_autotune:
         from paper_1801_04720_gb300 import autotune
-        # every class of disparity counts the batch uses (64, 128, 192)
-        tuned = autotune.load_or_tune(W=W_IMG, H=H_IMG, classes=[(33, 64), (65, 128), (129, 256)])
+        # every class of disparity counts the batch uses (64, 128, 192); the
+        # learned calls' own table for the frame (128) and the stream (256)
+        tuned = autotune.load_or_tune(W=W_IMG, H=H_IMG, classes=[(33, 64), (65, 128), (129, 256)],
+                                      learned_classes=[(65, 128), (129, 256)])
     q = synth.automotive(seed=args.seed + rank)
     H, W = q.shape
     N = W * H
@@ -370,6 +372,7 @@ def run_ours(args, world, rank, local):
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_tot.items()},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "sweep_shape": tuned["classes"] if tuned else "built-in",
+        "learned_sweep_shape": (tuned.get("learned") or "built-in") if tuned else "built-in",
     }
     # KITTI-style accuracy of this frame's output against the scene's ground truth
     from paper_1801_04720_gb300 import evaluate

@@ -472,6 +472,16 @@ sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t hal
  * does not provide, return SF_ERR_UNSUPPORTED. */
 sf_status sf_set_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order);
 
+/* sf_set_sweep_schedule for the learned launches of one frame's two left
+ * passes (sf_sgm_learned, sf_scene_flow_learned), which keep a table of
+ * their own: they carry half the work of the plain frame's four passes, so
+ * another shape or order can pay there.  Learned launches of more passes
+ * (sf_scene_flow_learned_frames with two or more frames, the learned
+ * sequence) use the plain table.  Same arguments, rules and status codes;
+ * results are identical in every order and shape.  A learned workspace is
+ * sized for the shape in force when it is sized. */
+sf_status sf_set_learned_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order);
+
 /* ---- tracing and counters (host-side bookkeeping; no paper counterpart) --- */
 
 /* Stage ids written by the tracer. */
@@ -514,7 +524,9 @@ uint64_t sf_kernel_launches(void);
  *   (sf_check_workspace then returns SF_ERR_TIMEOUT) and the kernels return
  *   normally.  0 (the default) skips nothing.
  * SF_DEBUG_HLINE_DC: disparities per thread of the horizontal-path kernel for
- *   D > 64, 16 or 32 (0 restores the default, 16); results are identical.
+ *   D > 64: 4 for a whole warp per line pair (4 disparities a lane up to
+ *   D = 128, 8 above), or 16 or 32; 0 restores the default, 4.  Results are
+ *   identical.
  * Process-wide; not for production use. */
 #define SF_DEBUG_SPIN_LIMIT 1
 #define SF_DEBUG_SKIP_TASKS 2

@@ -29,7 +29,7 @@ EXPORTED = [
     "sf_scene_flow_host_workspace_size", "sf_scene_flow_host", "sf_trace_arm",
     "sf_trace_disarm", "sf_kernel_launches", "sf_set_fused", "sf_check_workspace",
     "sf_batch_workspace_size", "sf_batch_run", "sf_batch_release_graphs", "sf_set_sweep_shape",
-    "sf_set_sweep_schedule", "sf_sgm_aggregate_guided", "sf_fill_disparity", "sf_densify_sceneflow",
+    "sf_set_sweep_schedule", "sf_set_learned_sweep_schedule", "sf_sgm_aggregate_guided", "sf_fill_disparity", "sf_densify_sceneflow",
     "sf_chain_sceneflow", "sf_sequence_workspace_size", "sf_sequence_sceneflow", "sf_set_batch_wave_limit",
     "sf_sgm_aggregate_noalloc", "sf_confnet_param_count", "sf_confnet_packed_bytes",
     "sf_confnet_pack", "sf_confnet_infer", "sf_confnet_train_workspace_size",
@@ -150,6 +150,7 @@ def load(path: str = LIB_PATH):
             "sf_batch_release_graphs": (None, []),
             "sf_set_sweep_shape": (i32, [i32, i32, i32, i32]),
             "sf_set_sweep_schedule": (i32, [i32, i32, i32, i32, i32]),
+            "sf_set_learned_sweep_schedule": (i32, [i32, i32, i32, i32, i32]),
             "sf_sgm_aggregate_guided": (i32, [P, P, i32, i32, i32, PP, P, P, sz, P]),
             "sf_fill_disparity": (i32, [P, i32, i32, P, i32, i32, P, P]),
             "sf_chain_sceneflow": (i32, [P, P, i32, i32, i32, PC, P, P, P]),
@@ -663,6 +664,12 @@ def sf_set_sweep_shape(d_lo, d_hi, dc, halo):
 
 def sf_set_sweep_schedule(d_lo, d_hi, dc, halo, order):
     _check("sf_set_sweep_schedule", load().sf_set_sweep_schedule(d_lo, d_hi, dc, halo, order))
+
+
+def sf_set_learned_sweep_schedule(d_lo, d_hi, dc, halo, order):
+    """Schedule of the learned calls; dc = 0 drops the class."""
+    _check("sf_set_learned_sweep_schedule",
+           load().sf_set_learned_sweep_schedule(d_lo, d_hi, dc, halo, order))
 
 
 # ---- learned confidence ------------------------------------------------------

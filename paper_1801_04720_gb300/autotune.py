@@ -3,11 +3,14 @@
 For each class of disparity counts it times every candidate (disparities per
 thread dc, halo width, and the scheduling order of the paths: 0 = down sweep
 then up sweep in two launches, 1 = both scan orders in one launch meeting in
-the middle, 2 = that launch with the horizontal paths in its queue too) on a synthetic quadruple of the requested size through
-sf_scene_flow, keeps the fastest, and stores the choice in a JSON cache keyed
-by GPU name and size.  ``apply`` installs a cached choice with
-sf_set_sweep_schedule.  Every candidate computes identical integers; only the
-speed differs."""
+the middle, 2 = that launch with the horizontal paths in its queue too) on a
+synthetic quadruple of the requested size, keeps the fastest, and stores the
+choice in a JSON cache keyed by GPU name and size.  The plain calls are timed
+through sf_scene_flow; the learned calls, which keep a table of their own
+(their launches carry the left passes alone), through sf_scene_flow_learned.
+``apply`` installs a cached choice with sf_set_sweep_schedule and
+sf_set_learned_sweep_schedule.  Every candidate computes identical results;
+only the speed differs."""
 from __future__ import annotations
 
 import json
@@ -27,36 +30,52 @@ DEFAULT_CLASSES = [(1, 32), (33, 64), (65, 128), (129, 256)]
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
 
-def _time_scene_flow(q, D, steps, warmup):
+def _time_frames(run, steps, warmup):
     """Mean frame time with the L2 flushed between frames (the bench's
     conditions: a median of unflushed frames can favour a shape whose frame
     time is bimodal)."""
-    dev = torch.device("cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    imgs = [torch.from_numpy(np.ascontiguousarray(im)).to(dev) for im in q.images()]
-    flow = torch.from_numpy(q.flow).to(dev)
-    p = _lib.params(D=D)
-    cam = _lib.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
-    ws = _lib.workspace(q.shape[1], q.shape[0], p, dev)
-    out = _lib.alloc_scene_flow_outputs(q.shape[1], q.shape[0], dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(warmup):
-        _lib.sf_scene_flow(imgs, flow, p, cam, ws=ws, out=out)
+        run()
     ms = []
     for k in range(steps):
         flush.fill_(k & 0xFF)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        _lib.sf_scene_flow(imgs, flow, p, cam, ws=ws, out=out)
+        run()
         e1.record()
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     return statistics.mean(ms)
 
 
-def tune(W=1242, H=375, classes=DEFAULT_CLASSES, steps=20, warmup=3, cache=CACHE, seed=0):
-    """Times every candidate shape per class; returns and stores the choice."""
-    _lib.load()
-    result = {"gpu": torch.cuda.get_device_name(), "W": W, "H": H, "classes": []}
+def _frame(q):
+    dev = torch.device("cuda")
+    imgs = [torch.from_numpy(np.ascontiguousarray(im)).to(dev) for im in q.images()]
+    flow = torch.from_numpy(q.flow).to(dev)
+    cam = _lib.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
+    return imgs, flow, cam, _lib.alloc_scene_flow_outputs(q.shape[1], q.shape[0], dev)
+
+
+def _time_scene_flow(q, D, steps, warmup):
+    imgs, flow, cam, out = _frame(q)
+    p = _lib.params(D=D)
+    ws = _lib.workspace(q.shape[1], q.shape[0], p, "cuda")
+    return _time_frames(lambda: _lib.sf_scene_flow(imgs, flow, p, cam, ws=ws, out=out), steps, warmup)
+
+
+def _time_learned(q, D, packed, steps, warmup):
+    """One frame per call through the learned scene-flow call; the workspace
+    is sized under the schedule being timed."""
+    imgs, flow, cam, out = _frame(q)
+    p = _lib.params(D=D)
+    ws = _lib.learned_workspace(q.shape[1], q.shape[0], p, 2, "cuda")
+    return _time_frames(lambda: _lib.sf_scene_flow_learned(imgs, flow, p, cam, packed, 0.5, ws=ws, out=out),
+                        steps, warmup)
+
+
+def _tune_table(classes, W, H, seed, timer, setter):
+    out = []
     for lo, hi in classes:
         D = hi
         q = synth.fronto_planes(W=W, H=H, D=D, disparities=(2, max(3, D // 3), max(4, D - 5)),
@@ -64,20 +83,38 @@ def tune(W=1242, H=375, classes=DEFAULT_CLASSES, steps=20, warmup=3, cache=CACHE
         timings = {}
         for dc, halo, order in CANDIDATES:
             try:
-                _lib.sf_set_sweep_schedule(lo, hi, dc, halo, order)
+                setter(lo, hi, dc, halo, order)
             except _lib.SFError:
                 continue
             try:
-                timings[f"{dc}x{halo}o{order}"] = _time_scene_flow(q, D, steps, warmup)
+                timings[f"{dc}x{halo}o{order}"] = timer(q, D)
             finally:
-                _lib.sf_set_sweep_shape(lo, hi, 0, 0)
+                setter(lo, hi, 0, 0, 0)
         if not timings:
             continue
         best = min(timings, key=timings.get)
         dc, halo, order = parse_key(best)
-        result["classes"].append({"lo": lo, "hi": hi, "dc": dc, "halo": halo, "order": order,
-                                  "ms": round(timings[best], 4),
-                                  "candidates_ms": {k: round(v, 4) for k, v in timings.items()}})
+        out.append({"lo": lo, "hi": hi, "dc": dc, "halo": halo, "order": order,
+                    "ms": round(timings[best], 4),
+                    "candidates_ms": {k: round(v, 4) for k, v in timings.items()}})
+    return out
+
+
+def tune(W=1242, H=375, classes=DEFAULT_CLASSES, steps=20, warmup=3, cache=CACHE, seed=0,
+         learned_classes=()):
+    """Times every candidate per class (plain calls, and the learned calls
+    for `learned_classes`); returns and stores the choice."""
+    _lib.load()
+    result = {"gpu": torch.cuda.get_device_name(), "W": W, "H": H}
+    result["classes"] = _tune_table(classes, W, H, seed, lambda q, D: _time_scene_flow(q, D, steps, warmup),
+                                    _lib.sf_set_sweep_schedule)
+    result["learned"] = []
+    if learned_classes:
+        # the timing does not depend on the weights: a seeded initialisation
+        packed = _lib.confnet_pack(_lib.confnet_init(7))
+        result["learned"] = _tune_table(learned_classes, W, H, seed,
+                                        lambda q, D: _time_learned(q, D, packed, steps, warmup),
+                                        _lib.sf_set_learned_sweep_schedule)
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         with open(cache, "w") as f:
@@ -98,6 +135,9 @@ def apply(result):
     for c in result.get("classes", []):
         _lib.sf_set_sweep_schedule(c["lo"], c["hi"], c["dc"], c["halo"], c.get("order", 0))
         n += 1
+    for c in result.get("learned", []):
+        _lib.sf_set_learned_sweep_schedule(c["lo"], c["hi"], c["dc"], c["halo"], c["order"])
+        n += 1
     return n
 
 
@@ -114,15 +154,16 @@ def cached(cache, gpu, W, H):
     return None
 
 
-def load_or_tune(W=1242, H=375, cache=CACHE, classes=DEFAULT_CLASSES, **kw):
+def load_or_tune(W=1242, H=375, cache=CACHE, classes=DEFAULT_CLASSES, learned_classes=(), **kw):
     """Uses the cached choice for this GPU and size, tuning when there is none
     (or when the cache lacks one of the requested classes)."""
     res = cached(cache, torch.cuda.get_device_name(), W, H)
     if res is not None:
         have = {(c["lo"], c["hi"]) for c in res["classes"]}
-        if not all(tuple(c) in have for c in classes):
+        have_l = {(c["lo"], c["hi"]) for c in res.get("learned", [])}
+        if not all(tuple(c) in have for c in classes) or not all(tuple(c) in have_l for c in learned_classes):
             res = None
     if res is None:
-        res = tune(W=W, H=H, cache=cache, classes=classes, **kw)
+        res = tune(W=W, H=H, cache=cache, classes=classes, learned_classes=learned_classes, **kw)
     apply(res)
     return res

@@ -283,8 +283,9 @@ struct TaskTables {
   std::vector<int> ints;
   int nbands = 0, ntasks = 0, nblocks = 0, off_band_start = 0, off_band_npass = 0, off_prefixJ = 0,
       off_hblocks = 0;
+  int hline_rows = 16;   // rows per block of the horizontal-path kernel
 };
-TaskTables build_tables(const fused::PassDesc* d, int npass, bool merged) {
+TaskTables build_tables(const fused::PassDesc* d, int npass, bool merged, int Dshape) {
   TaskTables t;
   int nb_max = 0;
   for (int k = 0; k < npass; k++) nb_max = std::max(nb_max, d[k].nb);
@@ -307,7 +308,8 @@ TaskTables build_tables(const fused::PassDesc* d, int npass, bool merged) {
   t.ints[t.off_band_start + nb_max] = task;
   t.ntasks = task;
   int* hb = &t.ints[t.off_hblocks];
-  for (int k = 0; k < npass; k++) hb[k + 1] = hb[k] + 2 * ((d[k].H + 15) / 16);
+  t.hline_rows = fused::hline_block_rows(Dshape);
+  for (int k = 0; k < npass; k++) hb[k + 1] = hb[k] + 2 * ((d[k].H + t.hline_rows - 1) / t.hline_rows);
   t.nblocks = hb[npass];
   return t;
 }
@@ -322,19 +324,19 @@ TaskTables build_tables(const fused::PassDesc* d, int npass, bool merged) {
 sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass, int Dshape,
                      const fused::PassDesc* d_dev_down, const fused::PassDesc* d_dev_up,
                      const int* tab_dev, const TaskTables* tt, int* counters, int* err,
-                     cudaStream_t s, bool tuned = true) {
+                     cudaStream_t s, int table = fused::kShapePlain) {
   const bool inl = d_dev_down == nullptr;
-  const fused::Shape shape = fused::shape_for(Dshape, tuned);
+  const fused::Shape shape = fused::shape_for(Dshape, table);
   const bool merged = shape.order >= 1;
   // the horizontal paths inside the sweep launch: passes of one size (the
   // batch's uneven passes keep their own launch)
   const bool with_h = shape.order == 2 && inl;
   fused::HLineArgs ha{};
   ha.P1 = p->P1; ha.P2 = p->P2; ha.Dmax = Dshape; ha.npass = npass; ha.path_mask = p->path_mask;
-  ha.builtin_shape = tuned ? 0 : 1;
+  ha.shape_table = table;
   ha.err = err;
   fused::SweepArgs sa{};
-  sa.builtin_shape = tuned ? 0 : 1;
+  sa.shape_table = table;
   sa.P1 = p->P1; sa.P2 = p->P2; sa.subpixel = p->subpixel; sa.Dmax = Dshape; sa.npass = npass;
   sa.unique = p->uniqueness;
   sa.variants = (p->adaptive_p2 || p->uniqueness) ? 1 : 0;
@@ -345,7 +347,8 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
   sa.spin_limit = g_spin_limit.load(std::memory_order_relaxed);
   if (inl) {
     for (int k = 0; k < npass; k++) ha.inl[k] = sa.inl[k] = d[k];
-    ha.uniform_blocks = 2 * ((d[0].H + 15) / 16);
+    ha.block_rows = fused::hline_block_rows(Dshape);
+    ha.uniform_blocks = 2 * ((d[0].H + ha.block_rows - 1) / ha.block_rows);
     ha.nblocks = npass * ha.uniform_blocks;
     sa.uniform_items = npass * d[0].J;
     sa.ntasks = (merged ? 2 : 1) * d[0].nb * sa.uniform_items;
@@ -354,6 +357,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     ha.pass_ptr = d_dev_down;
     ha.block_prefix = tab_dev + tt->off_hblocks;
     ha.nblocks = tt->nblocks;
+    ha.block_rows = tt->hline_rows;
     sa.pass_ptr = d_dev_down;
     sa.band_start = tab_dev + tt->off_band_start;
     sa.band_npass = tab_dev + tt->off_band_npass;
@@ -406,26 +410,34 @@ sf_status run_pair_costs(const uint8_t* const* left, const uint8_t* const* right
   if (npairs < 1 || npairs > fused::kMaxPass) return SF_ERR_INVALID_ARG;
   fused::CostPairs job{};
   job.npairs = npairs;
+  const uint8_t* imgs[2 * fused::kMaxPass];
+  uint64_t* cens[2 * fused::kMaxPass];
   for (int k = 0; k < npairs; k++) {
     uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b[k]->census_l);
     uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b[k]->census_r);
-    SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, cl, s));
-    SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, cr, s));
+    imgs[2 * k] = left[k];
+    imgs[2 * k + 1] = right[k];
+    cens[2 * k] = cl;
+    cens[2 * k + 1] = cr;
     job.cL[k] = cl;
     job.cR[k] = cr;
     job.CL[k] = ws + b[k]->pass[0].cost;
     job.CR[k] = ws + b[k]->pass[1].cost;
   }
+  // every image's census in one launch
+  SF_TRY_CUDA(launch_census_images(imgs, cens, 2 * npairs, W, H, pitch, p->census_w, p->census_h, s));
   SF_TRY_CUDA(fused::launch_cost_pair(job, W, H, D, fused::padded_d(D), p->census_w * p->census_h - 1, s));
   return SF_OK;
 }
 
 // Fused SGM for `npairs` stereo pairs of one size: census, one distance
 // computation per pair, both reference passes, the left-right check.
+// With d_out given, the left-right checks are left to the caller, who gets
+// the passes' descriptors (winners, subpixel maps) there.
 sf_status run_fused_pairs(const uint8_t* const* left, const uint8_t* const* right, int npairs,
                           int W, int H, int pitch, const sf_sgm_params* p, int16_t* const* dL_out,
                           int16_t* const* dR_out, uint8_t* const* valid_out, float* const* disp_out,
-                          uint8_t* ws, cudaStream_t s) {
+                          uint8_t* ws, cudaStream_t s, fused::PassDesc* d_out = nullptr) {
   FusedPlan plan = single_plan(W, H, p->D, npairs);
   const size_t N = (size_t)W * H;
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
@@ -452,6 +464,10 @@ sf_status run_fused_pairs(const uint8_t* const* left, const uint8_t* const* righ
   sf_status st = run_sweeps(p, d, 2 * npairs, p->D, nullptr, nullptr, nullptr, nullptr,
                             reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s);
   if (st != SF_OK) return st;
+  if (d_out) {
+    for (int k = 0; k < 2 * npairs; k++) d_out[k] = d[k];
+    return SF_OK;
+  }
   for (int k = 0; k < npairs; k++) {
     uint8_t* valid = (valid_out && valid_out[k]) ? valid_out[k] : ws + plan.pairs[k].valid;
     SF_TRY_CUDA(launch_lr_check(d[2 * k].dint, d[2 * k + 1].dint, d[2 * k].dsub, W, H, p->lr_tol, valid,
@@ -552,7 +568,7 @@ BatchSetup batch_setup(const sf_batch_item* items, int n, const sf_sgm_params* p
       tmp[k].J = (ps.W + fused::kTW - 1) / fused::kTW;
       tmp[k].nb = nb_of(c.pass_ids[k]);
     }
-    c.tt = build_tables(tmp.data(), (int)tmp.size(), c.sh.order >= 1);   // orders 1 and 2: one merged launch
+    c.tt = build_tables(tmp.data(), (int)tmp.size(), c.sh.order >= 1, c.Dshape);   // orders 1 and 2: one merged launch
     c.off_down = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
     c.off_up = o; o = align_up(o + tmp.size() * sizeof(fused::PassDesc), 256);
     c.off_tab = o; o = align_up(o + c.tt.ints.size() * sizeof(int), 256);
@@ -617,20 +633,26 @@ sf_status batch_enqueue(const sf_batch_item* items, int n, const sf_sgm_params* 
                               reinterpret_cast<int*>(ws + plan.err), s);
     if (st != SF_OK) return st;
   }
+  // per item: both checks and the combination in one launch
   for (int i = 0; i < n; i++) {
     const sf_batch_item& it = items[i];
-    float* disp[2];
-    for (int f = 0; f < 2; f++) {
-      const PairBuffers& pb = plan.pairs[2 * i + f];
-      float* user = f == 0 ? it.D0_out : it.D1_out;
-      disp[f] = user ? user : reinterpret_cast<float*>(ws + pb.disp);
-      SF_TRY_CUDA(launch_lr_check(reinterpret_cast<int16_t*>(ws + pb.pass[0].dint),
-                                  reinterpret_cast<int16_t*>(ws + pb.pass[1].dint),
-                                  reinterpret_cast<float*>(ws + pb.dsub), it.W, it.H, p->lr_tol,
-                                  ws + pb.valid, disp[f], s));
-    }
-    SF_TRY_CUDA(launch_combine(disp[0], disp[1], it.flow, it.W, it.H, it.cam.f, it.cam.B, it.cam.cx,
-                               it.cam.cy, it.s4_out, it.motion_out, it.point_out, it.valid_out, s));
+    const PairBuffers& p0 = plan.pairs[2 * i];
+    const PairBuffers& p1 = plan.pairs[2 * i + 1];
+    CheckCombineArgs ca{};
+    ca.dL0 = reinterpret_cast<const int16_t*>(ws + p0.pass[0].dint);
+    ca.dR0 = reinterpret_cast<const int16_t*>(ws + p0.pass[1].dint);
+    ca.dsub0 = reinterpret_cast<const float*>(ws + p0.dsub);
+    ca.dL1 = reinterpret_cast<const int16_t*>(ws + p1.pass[0].dint);
+    ca.dR1 = reinterpret_cast<const int16_t*>(ws + p1.pass[1].dint);
+    ca.dsub1 = reinterpret_cast<const float*>(ws + p1.dsub);
+    ca.flow = reinterpret_cast<const float2*>(it.flow);
+    ca.W = it.W; ca.H = it.H; ca.tol = p->lr_tol;
+    ca.f = it.cam.f; ca.B = it.cam.B; ca.cx = it.cam.cx; ca.cy = it.cam.cy;
+    ca.D0 = it.D0_out ? it.D0_out : reinterpret_cast<float*>(ws + p0.disp);
+    ca.D1 = it.D1_out ? it.D1_out : reinterpret_cast<float*>(ws + p1.disp);
+    ca.s4 = reinterpret_cast<float4*>(it.s4_out);
+    ca.motion = it.motion_out; ca.point = it.point_out; ca.valid = it.valid_out;
+    SF_TRY_CUDA(launch_check_combine(ca, s));
   }
   return SF_OK;
 }
@@ -941,8 +963,21 @@ sf_status sf_scene_flow(const uint8_t* left_t, const uint8_t* right_t, const uin
     const uint8_t* L[2] = {left_t, left_t1};
     const uint8_t* R[2] = {right_t, right_t1};
     float* disp[2] = {D0, D1};
-    if ((st = run_fused_pairs(L, R, 2, W, H, pitch, p, nullptr, nullptr, nullptr, disp, ws, s)) != SF_OK)
+    fused::PassDesc d[4];
+    if ((st = run_fused_pairs(L, R, 2, W, H, pitch, p, nullptr, nullptr, nullptr, disp, ws, s, d)) != SF_OK)
       return st;
+    // both checks and the combination in one launch
+    CheckCombineArgs ca{};
+    ca.dL0 = d[0].dint; ca.dR0 = d[1].dint; ca.dsub0 = d[0].dsub;
+    ca.dL1 = d[2].dint; ca.dR1 = d[3].dint; ca.dsub1 = d[2].dsub;
+    ca.flow = reinterpret_cast<const float2*>(flow);
+    ca.W = W; ca.H = H; ca.tol = p->lr_tol;
+    ca.f = cam->f; ca.B = cam->B; ca.cx = cam->cx; ca.cy = cam->cy;
+    ca.D0 = D0; ca.D1 = D1;
+    ca.s4 = reinterpret_cast<float4*>(s4_out);
+    ca.motion = motion_out; ca.point = point_out; ca.valid = valid_out;
+    SF_TRY_CUDA(launch_check_combine(ca, s));
+    return SF_OK;
   } else {
     Workspace lay(W, H, p->D);
     D0 = D0_out ? D0_out : reinterpret_cast<float*>(ws + lay.disp0);
@@ -1032,7 +1067,7 @@ sf_status sf_debug_set(int32_t key, int64_t value) {
     return SF_OK;
   }
   if (key == SF_DEBUG_HLINE_DC) {
-    return fused::set_hline_dc(value == 0 ? 16 : (int)value) == 0 ? SF_OK : SF_ERR_INVALID_ARG;
+    return fused::set_hline_dc(value == 0 ? 4 : (int)value) == 0 ? SF_OK : SF_ERR_INVALID_ARG;
   }
   return SF_ERR_INVALID_ARG;
 }
@@ -1113,11 +1148,17 @@ void sf_batch_release_graphs(void) {
 }
 
 sf_status sf_set_sweep_shape(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo) {
-  return fused::set_shape_override(d_lo, d_hi, dc, halo, 0) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
+  return fused::set_shape_override(fused::kShapePlain, d_lo, d_hi, dc, halo, 0) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
 }
 
 sf_status sf_set_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order) {
-  return fused::set_shape_override(d_lo, d_hi, dc, halo, order) == 0 ? SF_OK : SF_ERR_UNSUPPORTED;
+  return fused::set_shape_override(fused::kShapePlain, d_lo, d_hi, dc, halo, order) == 0 ? SF_OK
+                                                                                           : SF_ERR_UNSUPPORTED;
+}
+
+sf_status sf_set_learned_sweep_schedule(int32_t d_lo, int32_t d_hi, int32_t dc, int32_t halo, int32_t order) {
+  return fused::set_shape_override(fused::kShapeLearned, d_lo, d_hi, dc, halo, order) == 0 ? SF_OK
+                                                                                             : SF_ERR_UNSUPPORTED;
 }
 
 sf_status sf_set_fused(int32_t enable) {
@@ -1263,6 +1304,11 @@ struct LearnedPair {
          dint = 0, dsub = 0, disp = 0, flags = 0;
 };
 
+// Shape table of a learned launch of npairs left passes: the learned table
+// for one frame's two passes, the plain calls' (tuned on four passes) for
+// more.
+inline int learned_table(int npairs) { return npairs <= 2 ? fused::kShapeLearned : fused::kShapePlain; }
+
 struct LearnedPlan {
   size_t err = 0, counters = 0, control_bytes = 0, total = 0;
   LearnedPair pr[fused::kMaxPass];
@@ -1291,7 +1337,10 @@ struct LearnedPlan {
       b.cost = carve(N * Dp);
       b.hf = carve(N * Dp);
       b.hb = carve(N * Dp);
-      b.sdown = carve(fused::sdown_bytes(W, H, D, false));
+      // room for either table's shape (a sequence's last launch may carry
+      // fewer passes than the workspace was sized for)
+      b.sdown = carve(std::max(fused::sdown_bytes(W, H, D, fused::kShapeLearned),
+                               fused::sdown_bytes(W, H, D, fused::kShapePlain)));
       b.bs = carve(fused::bs_bytes(W, D));
       b.S = carve(N * D * sizeof(uint16_t));
       b.feat = carve(N * 16);
@@ -1324,20 +1373,29 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
   const LearnedPlan plan(W, H, p->D, npairs);
   const int D = p->D, Dp = fused::padded_d(D);
   const int J = (W + fused::kTW - 1) / fused::kTW;
+  // one frame's two left passes: the learned calls' own tuned schedule
+  // (their launches carry half the work of the plain frame's four passes)
+  const int table = learned_table(npairs);
   SF_TRY_CUDA(cudaMemsetAsync(ws, 0, plan.control_bytes, s));
   fused::PassDesc d[fused::kMaxPass];
   fused::CostPairs job{};
   job.npairs = npairs;
+  const uint8_t* imgs[2 * fused::kMaxPass];
+  uint64_t* cens[2 * fused::kMaxPass];
   for (int k = 0; k < npairs; k++) {
     const LearnedPair& b = plan.pr[k];
     uint64_t* cl = reinterpret_cast<uint64_t*>(ws + b.census_l);
     uint64_t* cr = reinterpret_cast<uint64_t*>(ws + b.census_r);
-    SF_TRY_CUDA(launch_census(left[k], W, H, pitch, p->census_w, p->census_h, cl, s));
-    SF_TRY_CUDA(launch_census(right[k], W, H, pitch, p->census_w, p->census_h, cr, s));
+    imgs[2 * k] = left[k];
+    imgs[2 * k + 1] = right[k];
+    cens[2 * k] = cl;
+    cens[2 * k + 1] = cr;
     job.cL[k] = cl;
     job.cR[k] = cr;
     job.CL[k] = ws + b.cost;
   }
+  // every image's census in one launch
+  SF_TRY_CUDA(launch_census_images(imgs, cens, 2 * npairs, W, H, pitch, p->census_w, p->census_h, s));
   // the left volumes of every pair in one launch
   SF_TRY_CUDA(fused::launch_cost_left(job, W, H, D, Dp, p->census_w * p->census_h - 1, s));
   for (int k = 0; k < npairs; k++) {
@@ -1345,7 +1403,7 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
     fused::PassDesc& pd = d[k];
     pd = fused::PassDesc{};
     pd.W = W; pd.H = H; pd.D = D; pd.Dp = Dp; pd.J = J;
-    pd.nb = (H + fused::band_rows(D, false) - 1) / fused::band_rows(D, false);
+    pd.nb = (H + fused::band_rows(D, table) - 1) / fused::band_rows(D, table);
     pd.cost = ws + b.cost;
     pd.hfwd = ws + b.hf;
     pd.hbwd = ws + b.hb;
@@ -1360,13 +1418,11 @@ sf_status run_learned_pairs(int npairs, const uint8_t* const* left, const uint8_
     pd.guide = p->adaptive_p2 ? left[k] : nullptr;
     pd.gpitch = pitch;
   }
-  // the learned path's two passes keep the built-in sweep shape (tuned
-  // overrides are measured on the four passes of the plain frame)
   sf_status st = run_sweeps(p, d, npairs, D, nullptr, nullptr, nullptr, nullptr,
                             reinterpret_cast<int*>(ws + plan.counters), reinterpret_cast<int*>(ws + plan.err), s,
-                            false);
+                            table);
   if (st != SF_OK) return st;
-  const fused::Shape shape = fused::shape_for(D, false);
+  const fused::Shape shape = fused::shape_for(D, table);
   static_assert(confnet::kMaxInferPass >= fused::kMaxPass, "one network launch per learned call");
   confnet::InferArgs ia{};
   for (int k = 0; k < npairs; k++) {

@@ -1,5 +1,7 @@
 // Census transform and Hamming matching-cost volume (SGM matching cost,
 // Sec. 3.1 of arXiv 1801.04720).
+#include <algorithm>
+
 #include "sf_internal.cuh"
 
 namespace sf {
@@ -8,13 +10,21 @@ namespace {
 
 constexpr int kCensusTX = 32, kCensusTY = 8;
 
+// Images of one size whose census one launch computes (blockIdx.z).
+constexpr int kCensusMaxImages = 8;
+struct CensusJob {
+  const uint8_t* img[kCensusMaxImages];
+  uint64_t* out[kCensusMaxImages];
+};
+
 // One thread per pixel; the block stages its (TY + 2ry) x (TX + 2rx) window
 // of edge-clamped pixels in shared memory.
 template <int RX, int RY>
 __global__ void __launch_bounds__(kCensusTX* kCensusTY)
-    census_kernel(const uint8_t* __restrict__ img, int W, int H, int pitch, int rx, int ry,
-                  uint64_t* __restrict__ out) {
+    census_kernel(const __grid_constant__ CensusJob job, int W, int H, int pitch, int rx, int ry) {
   extern __shared__ uint8_t tile[];
+  const uint8_t* __restrict__ img = job.img[blockIdx.z];
+  uint64_t* __restrict__ out = job.out[blockIdx.z];
   const int RXv = RX > 0 ? RX : rx, RYv = RY > 0 ? RY : ry;
   const int tw = kCensusTX + 2 * RXv, th = kCensusTY + 2 * RYv;
   const int x0 = blockIdx.x * kCensusTX - RXv, y0 = blockIdx.y * kCensusTY - RYv;
@@ -94,19 +104,34 @@ __global__ void __launch_bounds__(kCostThreads)
 
 }  // namespace
 
-cudaError_t launch_census(const uint8_t* img, int W, int H, int pitch, int cw, int ch, uint64_t* out,
-                          cudaStream_t s) {
+cudaError_t launch_census_images(const uint8_t* const* imgs, uint64_t* const* outs, int n, int W, int H,
+                                 int pitch, int cw, int ch, cudaStream_t s) {
   StageTrace trace(SF_STAGE_CENSUS, s);
-  count_launches(1);
   const int rx = cw / 2, ry = ch / 2;
   dim3 block(kCensusTX, kCensusTY);
-  dim3 grid((W + kCensusTX - 1) / kCensusTX, (H + kCensusTY - 1) / kCensusTY);
   const size_t smem = (size_t)(kCensusTX + 2 * rx) * (kCensusTY + 2 * ry);
-  if (cw == 9 && ch == 7)
-    census_kernel<4, 3><<<grid, block, smem, s>>>(img, W, H, pitch, rx, ry, out);
-  else
-    census_kernel<0, 0><<<grid, block, smem, s>>>(img, W, H, pitch, rx, ry, out);
-  return cudaGetLastError();
+  for (int i0 = 0; i0 < n; i0 += kCensusMaxImages) {
+    const int m = std::min(kCensusMaxImages, n - i0);
+    CensusJob job{};
+    for (int i = 0; i < m; i++) {
+      job.img[i] = imgs[i0 + i];
+      job.out[i] = outs[i0 + i];
+    }
+    dim3 grid((W + kCensusTX - 1) / kCensusTX, (H + kCensusTY - 1) / kCensusTY, m);
+    count_launches(1);
+    if (cw == 9 && ch == 7)
+      census_kernel<4, 3><<<grid, block, smem, s>>>(job, W, H, pitch, rx, ry);
+    else
+      census_kernel<0, 0><<<grid, block, smem, s>>>(job, W, H, pitch, rx, ry);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_census(const uint8_t* img, int W, int H, int pitch, int cw, int ch, uint64_t* out,
+                          cudaStream_t s) {
+  return launch_census_images(&img, &out, 1, W, H, pitch, cw, ch, s);
 }
 
 cudaError_t launch_cost_volume(const uint8_t* ref, const uint8_t* other, int W, int H, int pitch,

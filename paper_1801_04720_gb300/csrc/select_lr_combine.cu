@@ -70,16 +70,14 @@ __global__ void lr_check_kernel(const int16_t* __restrict__ dL, const int16_t* _
 
 __device__ __forceinline__ bool usable(float d) { return !isnan(d) && d > 0.0f; }
 
-__global__ void combine_kernel(const float* __restrict__ D0, const float* __restrict__ D1,
-                               const float2* __restrict__ flow, int W, int H, float f, float B,
-                               float cx, float cy, float4* __restrict__ s4,
-                               float* __restrict__ motion, float* __restrict__ point,
-                               uint8_t* __restrict__ valid) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= W * H) return;
-  const int y = i / W, x = i - y * W;
-  const float2 uv = flow[i];
-  const float d0 = D0[i];
+// The combination at pixel (x, y) = index i: Eq. 4 / 5 with the disparity
+// of t+1 read through d1_at(tx, ty) (a stored map, or the left-right check
+// evaluated on the fly), back-projection and motion.
+template <class Tap>
+__device__ __forceinline__ void combine_pixel(int i, int x, int y, int W, int H, float d0, float2 uv, Tap d1_at,
+                                              float f, float B, float cx, float cy, float4* __restrict__ s4,
+                                              float* __restrict__ motion, float* __restrict__ point,
+                                              uint8_t* __restrict__ valid) {
   // x' = x + F(x) as a float32 round-to-nearest sum (Eq. 4 / 5 target)
   const float xp = __fadd_rn((float)x, uv.x);
   const float yp = __fadd_rn((float)y, uv.y);
@@ -90,21 +88,21 @@ __global__ void combine_kernel(const float* __restrict__ D0, const float* __rest
     const float fx = xp - x0, fy = yp - y0;  // exact
     const int ix = (int)x0, iy = (int)y0;
     // Eq. 5; a tap whose weight is exactly zero (fx == 0 or fy == 0) is not read
-    const float v00 = D1[iy * W + ix];
+    const float v00 = d1_at(ix, iy);
     ok = usable(v00);
     d1 = __fmul_rn(__fmul_rn(1.0f - fx, 1.0f - fy), v00);
     if (fx != 0.0f) {
-      const float v10 = D1[iy * W + ix + 1];
+      const float v10 = d1_at(ix + 1, iy);
       ok = ok && usable(v10);
       d1 = __fadd_rn(d1, __fmul_rn(__fmul_rn(fx, 1.0f - fy), v10));
     }
     if (fy != 0.0f) {
-      const float v01 = D1[(iy + 1) * W + ix];
+      const float v01 = d1_at(ix, iy + 1);
       ok = ok && usable(v01);
       d1 = __fadd_rn(d1, __fmul_rn(__fmul_rn(1.0f - fx, fy), v01));
     }
     if (fx != 0.0f && fy != 0.0f) {
-      const float v11 = D1[(iy + 1) * W + ix + 1];
+      const float v11 = d1_at(ix + 1, iy + 1);
       ok = ok && usable(v11);
       d1 = __fadd_rn(d1, __fmul_rn(__fmul_rn(fx, fy), v11));
     }
@@ -133,6 +131,47 @@ __global__ void combine_kernel(const float* __restrict__ D0, const float* __rest
   }
 }
 
+__global__ void combine_kernel(const float* __restrict__ D0, const float* __restrict__ D1,
+                               const float2* __restrict__ flow, int W, int H, float f, float B,
+                               float cx, float cy, float4* __restrict__ s4,
+                               float* __restrict__ motion, float* __restrict__ point,
+                               uint8_t* __restrict__ valid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= W * H) return;
+  const int y = i / W, x = i - y * W;
+  combine_pixel(i, x, y, W, H, D0[i], flow[i], [&](int tx, int ty) { return D1[(size_t)ty * W + tx]; }, f, B,
+                cx, cy, s4, motion, point, valid);
+}
+
+// The left-right check of Sec. 3.1 at (x, y) of one pair: the subpixel
+// disparity where the integer winners agree within tol (and the left winner
+// was not removed before the check), NaN elsewhere.
+__device__ __forceinline__ float lr_checked(const int16_t* __restrict__ dL, const int16_t* __restrict__ dR,
+                                            const float* __restrict__ dsub, int W, int x, int y, int tol) {
+  const size_t i = (size_t)y * W + x;
+  const int dl = dL[i];
+  const int xr = x - dl;
+  const float v = dsub[i];
+  if (xr < 0 || isnan(v)) return __int_as_float(0x7fc00000);
+  return abs(dl - (int)dR[(size_t)y * W + xr]) <= tol ? v : __int_as_float(0x7fc00000);
+}
+
+// Both pairs' left-right checks and the combination in one pass: D0 and D1
+// at the pixel are written as maps, and the Eq. 5 taps of D1 evaluate the
+// check of the pair at t+1 themselves (no grid-wide wait for the D1 map).
+__global__ void check_combine_kernel(const CheckCombineArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int W = a.W;
+  if (i >= W * a.H) return;
+  const int y = i / W, x = i - y * W;
+  const float d0 = lr_checked(a.dL0, a.dR0, a.dsub0, W, x, y, a.tol);
+  a.D0[i] = d0;
+  a.D1[i] = lr_checked(a.dL1, a.dR1, a.dsub1, W, x, y, a.tol);
+  combine_pixel(i, x, y, W, a.H, d0, a.flow[i],
+                [&](int tx, int ty) { return lr_checked(a.dL1, a.dR1, a.dsub1, W, tx, ty, a.tol); }, a.f, a.B,
+                a.cx, a.cy, a.s4, a.motion, a.point, a.valid);
+}
+
 }  // namespace
 
 cudaError_t launch_select(const uint16_t* S, int W, int H, int D, int subpixel, int16_t* dint,
@@ -150,6 +189,14 @@ cudaError_t launch_lr_check(const int16_t* dL, const int16_t* dR, const float* d
   count_launches(1);
   const int n = W * H;
   lr_check_kernel<<<(n + 255) / 256, 256, 0, s>>>(dL, dR, dL_sub, W, H, tol, valid, disp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_combine(const CheckCombineArgs& a, cudaStream_t s) {
+  StageTrace trace(SF_STAGE_COMBINE, s);
+  count_launches(1);
+  const int n = a.W * a.H;
+  check_combine_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -22,12 +22,16 @@ constexpr int kMaxPass = 4;
 struct Shape {
   int dc, chunks, halo, order;
 };
-// built-in rule unless a tuned override covers D (and `tuned` allows it)
-Shape shape_for(int D, bool tuned = true);
+// Tables of tuned overrides: the plain calls' and the learned calls' (their
+// launches carry the left passes alone, half the work in flight).
+// kShapeBuiltin asks for the built-in rule whatever is tuned.
+constexpr int kShapeBuiltin = -1, kShapePlain = 0, kShapeLearned = 1;
+// built-in rule unless an override of `table` covers D
+Shape shape_for(int D, int table = kShapePlain);
 bool shape_supported(int dc, int chunks, int halo);
-int set_shape_override(int d_lo, int d_hi, int dc, int halo, int order);   // 0 = ok
+int set_shape_override(int table, int d_lo, int d_hi, int dc, int halo, int order);   // 0 = ok
 inline int padded_d(int D) { return ((D + 15) / 16) * 16; }
-inline int band_rows(int D, bool tuned = true) { return shape_for(D, tuned).halo + 1; }
+inline int band_rows(int D, int table = kShapePlain) { return shape_for(D, table).halo + 1; }
 
 // One stereo pass (one reference image) of the band sweeps and the
 // horizontal paths: its sizes and buffers.
@@ -50,7 +54,8 @@ struct PassDesc {
 
 struct HLineArgs {
   int P1, P2, Dmax, npass, nblocks;   // P2: the constant P2, or the base of the adaptive one
-  int builtin_shape;           // 1: ignore tuned shape overrides
+  int block_rows;              // rows per block: hline_block_rows(Dmax) when the blocks were counted
+  int shape_table;             // kShapePlain, kShapeLearned or kShapeBuiltin
   uint32_t path_mask;
   int uniform_blocks;          // > 0: every pass has this many blocks
   const int* block_prefix;     // otherwise: first block of each pass [npass + 1]
@@ -64,7 +69,7 @@ struct SweepArgs {
   int unique;                  // uniqueness ratio (percent) of the winners with a subpixel output, 0 = off
   int hl_tasks, hl_blocks;     // launch mode 3: horizontal-path tasks at the queue head, row blocks per direction
   int variants;                // 1: adaptive P2 or uniqueness requested (the kernels that compile them in)
-  int builtin_shape;           // 1: ignore tuned shape overrides
+  int shape_table;             // kShapePlain, kShapeLearned or kShapeBuiltin
   uint32_t path_mask;
   int en_h0, en_h1;
   int uniform_items;           // > 0: all passes alike, tasks per band
@@ -80,9 +85,9 @@ struct SweepArgs {
 };
 
 // per-pass buffer sizes (the shape is the launch's, chosen from its largest D)
-inline size_t sdown_bytes(int W, int H, int Dshape, bool tuned = true) {
+inline size_t sdown_bytes(int W, int H, int Dshape, int table = kShapePlain) {
   const int J = (W + kTW - 1) / kTW;
-  const Shape s = shape_for(Dshape, tuned);
+  const Shape s = shape_for(Dshape, table);
   return (size_t)H * J * 16 * s.chunks * s.dc * sizeof(uint32_t);
 }
 inline size_t bs_bytes(int W, int D) { return (size_t)2 * 2 * 3 * W * padded_d(D); }
@@ -107,6 +112,8 @@ cudaError_t launch_cost_left(const CostPairs& job, int W, int H, int D, int Dp, 
 cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s);
 // disparities per thread of the horizontal paths for D > 64 (16 or 32; 0 = ok)
 int set_hline_dc(int dc);
+// rows per block of the horizontal-path kernel for a launch of depth Dmax
+int hline_block_rows(int Dmax);
 // mode 0: down sweep, 1: up sweep, 2: both orders in one launch, 3: mode 2
 // with the horizontal paths' row blocks at the head of its queue
 cudaError_t launch_sweep(const SweepArgs& a, int mode, cudaStream_t s);

@@ -29,19 +29,25 @@ __host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a -
 // bit 0 first.
 template <int RX, int RY>
 __device__ __forceinline__ uint64_t census_window(const uint8_t* tile, int ts, int cx, int cy) {
+  // bits 0..31 and 32.. gathered in two 32-bit words (the bit index is a
+  // compile-time constant, so each bit is one compare and one merge)
   const uint8_t c = tile[cy * ts + cx];
-  uint64_t bits = 0;
+  uint32_t lo = 0, hi = 0;
   int k = 0;
 #pragma unroll
   for (int dy = -RY; dy <= RY; dy++) {
 #pragma unroll
     for (int dx = -RX; dx <= RX; dx++) {
       if (dx == 0 && dy == 0) continue;
-      bits |= (uint64_t)(tile[(cy + dy) * ts + cx + dx] < c) << k;
+      const uint32_t b = tile[(cy + dy) * ts + cx + dx] < c ? 1u : 0u;
+      if (k < 32)
+        lo |= b << (k & 31);
+      else
+        hi |= b << (k & 31);
       k++;
     }
   }
-  return bits;
+  return ((uint64_t)hi << 32) | lo;
 }
 
 __device__ __forceinline__ uint64_t census_window_rt(const uint8_t* tile, int ts, int cx, int cy,
@@ -74,6 +80,9 @@ struct StageTrace {
 // ---- launchers (each returns cudaGetLastError() of its launches) ----------
 cudaError_t launch_census(const uint8_t* img, int W, int H, int pitch, int cw, int ch, uint64_t* out,
                           cudaStream_t s);
+// the census of n images of one size (one launch per eight)
+cudaError_t launch_census_images(const uint8_t* const* imgs, uint64_t* const* outs, int n, int W, int H,
+                                 int pitch, int cw, int ch, cudaStream_t s);
 cudaError_t launch_cost_volume(const uint8_t* ref, const uint8_t* other, int W, int H, int pitch,
                                int cw, int ch, int D, int ref_is_right, uint8_t* cost,
                                cudaStream_t s);
@@ -86,6 +95,25 @@ cudaError_t launch_select(const uint16_t* S, int W, int H, int D, int subpixel, 
                           float* dsub, cudaStream_t s, int unique = 0);
 cudaError_t launch_lr_check(const int16_t* dL, const int16_t* dR, const float* dL_sub, int W, int H,
                             int tol, uint8_t* valid, float* disp, cudaStream_t s);
+// both pairs' left-right checks and the combination in one launch
+struct CheckCombineArgs {
+  const int16_t* dL0;
+  const int16_t* dR0;
+  const float* dsub0;
+  const int16_t* dL1;
+  const int16_t* dR1;
+  const float* dsub1;
+  const float2* flow;
+  int W, H, tol;
+  float f, B, cx, cy;
+  float* D0;       // checked disparity maps (NaN where removed)
+  float* D1;
+  float4* s4;
+  float* motion;   // optional
+  float* point;    // optional
+  uint8_t* valid;
+};
+cudaError_t launch_check_combine(const CheckCombineArgs& a, cudaStream_t s);
 cudaError_t launch_combine(const float* D0, const float* D1, const float* flow, int W, int H,
                            float f, float B, float cx, float cy, float* s4, float* motion,
                            float* point, uint8_t* valid, cudaStream_t s);

@@ -1040,7 +1040,7 @@ cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
 
 template <int MODE, bool VAR>
 cudaError_t sweep_select(const SweepArgs& a, cudaStream_t s) {
-  const Shape sh = shape_for(a.Dmax, a.builtin_shape == 0);
+  const Shape sh = shape_for(a.Dmax, a.shape_table);
 #define SF_CASE(DC_, CH_, HA_) \
   if (sh.dc == DC_ && sh.chunks == CH_ && sh.halo == HA_) return sweep_dispatch<DC_, CH_, HA_, MODE, VAR>(a, s);
   SF_SWEEP_SHAPES(SF_CASE)

@@ -29,8 +29,15 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   return r;
 }
 
-// DC bytes of one line as a vector type (8 -> uint2, 16 -> uint4).
+// DC bytes of one line as a vector type (4 -> uint32_t, 8 -> uint2,
+// 16 -> uint4, 32 -> two uint4).
 template <int DC> struct ByteVec;
+template <> struct ByteVec<4> {
+  using T = uint32_t;
+  __device__ static void words(const T& v, uint32_t* w) { w[0] = v; }
+  __device__ static T make(const uint32_t* w) { return w[0]; }
+  __device__ static T zero() { return 0u; }
+};
 template <> struct ByteVec<8> {
   using T = uint2;
   __device__ static void words(const T& v, uint32_t* w) { w[0] = v.x; w[1] = v.y; }
@@ -59,6 +66,9 @@ template <> struct ByteVec<32> {
 };
 
 // Streaming (evict-first) store of DC bytes.
+__device__ __forceinline__ void store_cs(uint32_t* p, const uint32_t& v) {
+  __stcs(reinterpret_cast<unsigned int*>(p), static_cast<unsigned int>(v));
+}
 __device__ __forceinline__ void store_cs(uint2* p, const uint2& v) { __stcs(p, v); }
 __device__ __forceinline__ void store_cs(uint4* p, const uint4& v) { __stcs(p, v); }
 __device__ __forceinline__ void store_cs(Bytes32* p, const Bytes32& v) {
@@ -133,12 +143,20 @@ __device__ __forceinline__ uint32_t tree_min(const uint32_t* v) {
 }
 
 // Lane-wise min over a group of G consecutive threads (G divides 32).
-// `mask` names the lanes executing the call (whole groups only).
+// `mask` names the lanes executing the call (whole groups only).  A whole
+// warp (G = 32) reduces each 16-bit lane with one warp-wide min reduction
+// (redux.sync) instead of five shuffle levels.
 template <int G>
 __device__ __forceinline__ uint32_t group_min2(uint32_t v, unsigned mask = 0xffffffffu) {
+  if constexpr (G == 32) {
+    const uint32_t lo = __reduce_min_sync(mask, v & 0xffffu);
+    const uint32_t hi = __reduce_min_sync(mask, v >> 16);
+    return lo | (hi << 16);
+  } else {
 #pragma unroll
-  for (int o = 1; o < G; o <<= 1) v = vmin2(v, __shfl_xor_sync(mask, v, o, G));
-  return v;
+    for (int o = 1; o < G; o <<= 1) v = vmin2(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
 }
 
 // One SGM step for DC disparities of two lines (no reduction):

@@ -191,16 +191,21 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // 2. horizontal paths
 // ---------------------------------------------------------------------------
-// A CTA walks 16 consecutive rows (8 line pairs, two rows per register) of
-// one pass in one direction (hline_rows, sf_sweep.cuh).  The merged sweep
-// launch can run the same blocks as tasks of its own queue.
-constexpr int kHlinePairs = 8;                 // line pairs per CTA
-constexpr int kHlineRows = 2 * kHlinePairs;
+// A CTA walks PAIRS line pairs (two rows per register) of one pass in one
+// direction (hline_rows, sf_sweep.cuh): 8 pairs (16 rows, 56 KB tiles) with
+// chunks of 8, 16 or 32 disparities a thread; 2 pairs (4 rows, 16 KB tiles)
+// with a warp per line pair, so that many small blocks spread the rows
+// evenly over the SMs.  The merged sweep launch can run the same walk as
+// tasks of its own queue.
+constexpr int kHlinePairs = 8;
 constexpr int kHlineTileBytes = 56 * 1024;     // one buffer (two CTAs fit an SM)
+constexpr int kHlineWarpPairs = 2;
+constexpr int kHlineWarpTileBytes = 16 * 1024;
 
-template <int DC, int CHUNKS>
-__global__ void __launch_bounds__(kHlinePairs * CHUNKS)
+template <int DC, int CHUNKS, int PAIRS, int TILE>
+__global__ void __launch_bounds__(PAIRS * CHUNKS)
     hline_kernel(const __grid_constant__ HLineArgs a) {
+  constexpr int kRows = 2 * PAIRS;
   extern __shared__ __align__(128) uint8_t hsmem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ int s_fail;
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
     p = lo;
   }
   const PassDesc pd = a.pass_ptr ? a.pass_ptr[p] : a.inl[p];   // by value: fields in registers
-  const int nrb = (pd.H + kHlineRows - 1) / kHlineRows;
+  const int nrb = (pd.H + kRows - 1) / kRows;
   const int rem = blockIdx.x - (a.block_prefix ? a.block_prefix[p] : p * a.uniform_blocks);
   const int dir = rem / nrb;                 // 0: (+1,0), 1: (-1,0)
   const int rb = rem - dir * nrb;
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(kHlinePairs * CHUNKS)
   }
   if (pd.guide) fill_p2_table(s_lut, a.P1, a.P2);
   int ph[2] = {0, 0};
-  hline_rows<DC, CHUNKS, true>(pd, dir, rb * kHlineRows, kHlinePairs, a.P1, a.P2, hsmem, kHlineTileBytes, bars,
+  hline_rows<DC, CHUNKS, true>(pd, dir, rb * kRows, PAIRS, a.P1, a.P2, hsmem, TILE, bars,
                                &s_fail, s_lut, ph, a.err);
 }
 
@@ -288,25 +293,34 @@ cudaError_t launch_cost_pair(const CostPairs& job, int W, int H, int D, int Dp, 
   return cudaGetLastError();
 }
 
-template <int DC, int CHUNKS>
+template <int DC, int CHUNKS, int PAIRS = kHlinePairs, int TILE = kHlineTileBytes>
 static cudaError_t hline_dispatch(const HLineArgs& a, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)kHlineTileBytes;
-  cudaError_t e = cudaFuncSetAttribute(hline_kernel<DC, CHUNKS>,
+  if (a.block_rows != 2 * PAIRS) return cudaErrorInvalidValue;   // blocks counted for another walk
+  const size_t smem = 2 * (size_t)TILE;
+  cudaError_t e = cudaFuncSetAttribute(hline_kernel<DC, CHUNKS, PAIRS, TILE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (a.nblocks <= 0) return cudaSuccess;
-  hline_kernel<DC, CHUNKS><<<a.nblocks, kHlinePairs * CHUNKS, smem, s>>>(a);
+  hline_kernel<DC, CHUNKS, PAIRS, TILE><<<a.nblocks, PAIRS * CHUNKS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-// Disparities per thread of the horizontal paths above D = 64: 16 (eight
-// threads per line pair, three shuffle levels per step's minimum) measured
-// 0.33 ms per 1242 x 375, D = 128 frame against 0.45 ms for 32 (four threads,
-// two levels, but one warp per block: too little issue to cover each step).
-int g_hline_dc = 16;
+// Disparities per thread of the horizontal paths above D = 64.  4 (the
+// default) gives a whole warp to a line pair (4 disparities a lane up to
+// D = 128, 8 up to 256): a step's minimum is one warp-wide reduction per
+// 16-bit lane, and the launch has four times the warps of 16-wide chunks.
+// 16 (eight threads per line pair, three shuffle levels per step's minimum)
+// and 32 (four threads, two levels, one warp per block) leave too few warps
+// to cover each step's latency.  On the 1242 x 375, D = 128 frame: 0.03 ms
+// less per plain frame and 0.12 ms less per learned frame than 16.
+int g_hline_dc = 4;
+
+int hline_block_rows(int Dmax) {
+  return (g_hline_dc == 4 && Dmax > 64) ? 2 * kHlineWarpPairs : 2 * kHlinePairs;
+}
 
 int set_hline_dc(int dc) {
-  if (dc != 16 && dc != 32) return 1;
+  if (dc != 4 && dc != 16 && dc != 32) return 1;
   g_hline_dc = dc;
   return 0;
 }
@@ -315,13 +329,17 @@ cudaError_t launch_hline(const HLineArgs& a, cudaStream_t s) {
   StageTrace trace(SF_STAGE_AGGREGATE, s);
   count_launches(1);
   // the horizontal volumes do not depend on the sweeps' shape.  Each step of
-  // a line waits for the minimum over its chunk group (a shuffle reduction),
-  // and the launch has about one warp per scheduler, so the walk is latency
-  // bound (g_hline_dc: the chunk width).
+  // a line waits for the minimum over its chunk group, so the walk is
+  // latency bound (g_hline_dc: the chunk width).
   // A thread moves DC bytes of every pixel it walks, so DC must divide the
   // padded depth Dp of every pass (a multiple of 16): 32-wide chunks only
   // for passes of one size with Dp % 32 == 0 (a batch launch mixes depths),
   // and only above D = 64 (four 16-wide chunks already cover smaller D).
+  if (a.block_rows == 2 * kHlineWarpPairs) {
+    // a warp per line pair; lanes past a pass's depth carry padding costs
+    if (a.Dmax <= 128) return hline_dispatch<4, 32, kHlineWarpPairs, kHlineWarpTileBytes>(a, s);
+    return hline_dispatch<8, 32, kHlineWarpPairs, kHlineWarpTileBytes>(a, s);
+  }
   bool wide = a.Dmax > 64 && a.pass_ptr == nullptr && a.npass >= 1;
   for (int k = 0; wide && k < a.npass; k++) wide = a.inl[k].Dp % 32 == 0;
   Shape sh;
@@ -355,8 +373,8 @@ namespace {
 struct ShapeOverride {
   int lo, hi, dc, halo, order;
 };
-ShapeOverride g_over[16];
-int g_nover = 0;
+ShapeOverride g_over[2][16];   // [table]
+int g_nover[2] = {0, 0};
 }  // namespace
 
 // chunks of dc disparities covering D, at least two (owned pairs then fill
@@ -388,13 +406,14 @@ bool shape_supported(int dc, int chunks, int halo) {
   return false;
 }
 
-Shape shape_for(int D, bool tuned) {
-  for (int i = tuned ? g_nover - 1 : -1; i >= 0; i--) {
-    if (D >= g_over[i].lo && D <= g_over[i].hi) {
+Shape shape_for(int D, int table) {
+  const ShapeOverride* ov = table >= 0 ? g_over[table] : nullptr;
+  for (int i = table >= 0 ? g_nover[table] - 1 : -1; i >= 0; i--) {
+    if (D >= ov[i].lo && D <= ov[i].hi) {
       Shape s;
-      s.dc = g_over[i].dc;
-      s.halo = g_over[i].halo;
-      s.order = g_over[i].order;
+      s.dc = ov[i].dc;
+      s.halo = ov[i].halo;
+      s.order = ov[i].order;
       s.chunks = chunks_for(s.dc, D);
       return s;
     }
@@ -402,20 +421,23 @@ Shape shape_for(int D, bool tuned) {
   return builtin_shape(D);
 }
 
-int set_shape_override(int d_lo, int d_hi, int dc, int halo, int order) {
+int set_shape_override(int table, int d_lo, int d_hi, int dc, int halo, int order) {
+  if (table < 0 || table > 1) return 1;
   if (d_lo < 1 || d_hi > SF_MAX_DISPARITY || d_lo > d_hi) return 1;
+  ShapeOverride* ov = g_over[table];
+  int& n = g_nover[table];
   if (dc == 0) {   // drop overrides of this class
     int w = 0;
-    for (int i = 0; i < g_nover; i++)
-      if (!(g_over[i].lo == d_lo && g_over[i].hi == d_hi)) g_over[w++] = g_over[i];
-    g_nover = w;
+    for (int i = 0; i < n; i++)
+      if (!(ov[i].lo == d_lo && ov[i].hi == d_hi)) ov[w++] = ov[i];
+    n = w;
     return 0;
   }
   if (order < 0 || order > 2) return 1;
   for (int D = d_lo; D <= d_hi; D++)
     if (!shape_supported(dc, chunks_for(dc, D), halo)) return 1;
-  if (g_nover == 16) return 1;
-  g_over[g_nover++] = {d_lo, d_hi, dc, halo, order};
+  if (n == 16) return 1;
+  ov[n++] = {d_lo, d_hi, dc, halo, order};
   return 0;
 }
 

@@ -13,6 +13,7 @@ def lib():
     yield _lib
     for lo, hi in [(1, 32), (33, 64), (65, 128), (129, 256)]:
         _lib.sf_set_sweep_shape(lo, hi, 0, 0)
+        _lib.sf_set_learned_sweep_schedule(lo, hi, 0, 0, 0)
 
 
 def test_apply_installs_every_class(lib):
@@ -23,6 +24,39 @@ def test_apply_installs_every_class(lib):
     assert autotune.apply(res) == 3
     for c in res["classes"]:
         lib.sf_set_sweep_shape(c["lo"], c["hi"], 0, 0)
+
+
+def test_apply_installs_the_learned_table(lib):
+    from paper_1801_04720_gb300 import autotune
+    res = {"classes": [{"lo": 65, "hi": 128, "dc": 16, "halo": 8, "order": 1}],
+           "learned": [{"lo": 65, "hi": 128, "dc": 16, "halo": 8, "order": 2},
+                       {"lo": 129, "hi": 256, "dc": 16, "halo": 8, "order": 0}]}
+    assert autotune.apply(res) == 3
+    lib.sf_set_sweep_shape(65, 128, 0, 0)
+    for c in res["learned"]:
+        lib.sf_set_learned_sweep_schedule(c["lo"], c["hi"], 0, 0, 0)
+
+
+@pytest.mark.parametrize("args", [(1, 32, 4, 16, 1), (65, 128, 8, 12, 1), (200, 100, 8, 16, 1),
+                                  (129, 257, 16, 8, 1), (65, 128, 16, 8, 3), (65, 128, 16, 8, -1)])
+def test_learned_table_rejects_what_the_plain_table_rejects(lib, args):
+    with pytest.raises(lib.SFError):
+        lib.sf_set_sweep_schedule(*args)
+    with pytest.raises(lib.SFError):
+        lib.sf_set_learned_sweep_schedule(*args)
+
+
+def test_learned_table_holds_sixteen_classes(lib):
+    for d in range(1, 17):
+        lib.sf_set_learned_sweep_schedule(d, d, 8, 8, 1)
+    with pytest.raises(lib.SFError):      # full, while the plain table is not
+        lib.sf_set_learned_sweep_schedule(17, 17, 8, 8, 1)
+    lib.sf_set_sweep_schedule(17, 17, 8, 8, 1)
+    lib.sf_set_sweep_shape(17, 17, 0, 0)
+    for d in range(1, 17):
+        lib.sf_set_learned_sweep_schedule(d, d, 0, 0, 0)
+    lib.sf_set_learned_sweep_schedule(17, 17, 8, 8, 1)
+    lib.sf_set_learned_sweep_schedule(17, 17, 0, 0, 0)
 
 
 @pytest.mark.parametrize("lo,hi,dc,halo", [(1, 32, 4, 16), (65, 128, 8, 12), (200, 100, 8, 16),

@@ -137,3 +137,25 @@ def test_two_frames_per_launch_every_pass_against_oracle(sf, oracle_mod, net):
     torch.cuda.synchronize()
     for q, o in zip(quads, outs):
         check_frame(oracle_mod, theta, thr, q, o)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("dc,halo", [(16, 8), (8, 16)])
+def test_learned_schedules_against_oracle(sf, oracle_mod, net, dc, halo, order):
+    """The learned calls' own schedule table: every order and shape gives the
+    oracle's result (features, network, acceptance, combination)."""
+    import torch
+    theta, packed, thr = net
+    q = synth.automotive(seed=64, W=256, H=80, D=64, n_segments=8)
+    cam = sf.camera(q.camera.f, q.camera.B, q.camera.cx, q.camera.cy)
+    p = sf.params(D=q.D)
+    sf.sf_set_learned_sweep_schedule(33, 64, dc, halo, order)
+    try:
+        # sized under the schedule in force
+        ws = sf.learned_workspace(q.shape[1], q.shape[0], p, 2, "cuda")
+        out = sf.sf_scene_flow_learned([to_dev(im) for im in q.images()], to_dev(q.flow), p, cam, packed, thr,
+                                       ws=ws)
+        torch.cuda.synchronize()
+    finally:
+        sf.sf_set_learned_sweep_schedule(33, 64, 0, 0, 0)
+    check_frame(oracle_mod, theta, thr, q, out)

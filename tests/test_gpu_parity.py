@@ -278,11 +278,13 @@ def test_status_errors_on_gpu(sf):
     assert sf.sf_census(img).shape == (48, 64)
 
 
-@pytest.mark.parametrize("hdc", [16, 32])
-@pytest.mark.parametrize("W,H,D", [(130, 41, 128), (300, 23, 96), (97, 19, 256), (64, 30, 80)])
+@pytest.mark.parametrize("hdc", [4, 16, 32])
+@pytest.mark.parametrize("W,H,D", [(130, 41, 128), (300, 23, 96), (97, 19, 256), (64, 30, 80), (70, 17, 112)])
 def test_horizontal_chunk_widths_against_oracle(sf, oracle_mod, W, H, D, hdc):
     """The horizontal paths with 16 or 32 disparities per thread (two or three
-    shuffle levels in each step's minimum): S bit-exact against the oracle."""
+    shuffle levels in each step's minimum), or a whole warp per line pair (a
+    warp-wide reduction; lanes past the depth carry padding costs): S
+    bit-exact against the oracle."""
     rng = np.random.default_rng(W + H + D + hdc)
     C = rng.integers(0, 63, size=(H, W, D), dtype=np.uint8)
     sf.sf_debug_set(sf.SF_DEBUG_HLINE_DC, hdc)
