@@ -476,11 +476,16 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   // Tasks (band, pass, strip) in band-major order from a global counter: any
   // CTA takes the next one, so a slow SM delays nobody but itself.  A task
   // waits (bounded) for the previous band of its own strip and of both
-  // neighbour strips; those tasks were handed out earlier to running CTAs.
+  // neighbour strips; those tasks were handed out earlier.  A CTA claims its
+  // next task as soon as its current one has passed its waits (the counter's
+  // round trip then overlaps the band); a claimed task that is not running
+  // yet belongs to a CTA whose current task comes earlier in the queue and
+  // only waits on still earlier tasks, so by induction over the queue every
+  // claimed task runs.
   const int ntasks = a.ntasks;
+  if (t == 0) s_task = atomicAdd(a.task_counter, 1);
   for (;;) {
-    if (t == 0) s_task = atomicAdd(a.task_counter, 1);
-    __syncthreads();
+    __syncthreads();   // the claim is visible; every thread has left the previous task
     int task = s_task;
     if (task >= ntasks) break;
     if (HL) {
@@ -497,7 +502,10 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
             return;
         }
         __syncthreads();   // every thread's stores before the release
-        if (t == 0) st_release(hd.flags_h + dir * a.hl_blocks + rb, 1);
+        if (t == 0) {
+          st_release(hd.flags_h + dir * a.hl_blocks + rb, 1);
+          s_task = atomicAdd(a.task_counter, 1);   // every thread read this task's index before the barrier
+        }
         continue;
       }
       task -= a.hl_tasks;
@@ -543,60 +551,80 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     const size_t sd_row = (size_t)J * 16 * CHUNKS * G;
     // ---- prefetch ring: the first rows' inputs are requested before the
     // neighbour wait (they do not depend on it) ----
-    auto issue_row = [&](int r) {
+    // parts: 1 the costs, 2 the other order's partial sums, 4 the
+    // horizontal volumes (the last two for a second arrival's owned pairs)
+    auto issue_row = [&](int r, int parts) {
       const bool ok = r < nrows;
       const int yy = up ? ytop + nrows - 1 - r : ytop + r;
-      V* cs = ringc + (r % RING) * 2 * NT + t;
-      const uint8_t* rowc = pd.cost + (size_t)yy * W * Dp + d0;
-      cp_async<DC>(cs, ok && lo_in ? rowc + (size_t)xlo * Dp : pd.cost, ok && lo_in);
-      cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : pd.cost, ok && hi_in);
+      if (parts & 1) {
+        V* cs = ringc + (r % RING) * 2 * NT + t;
+        const uint8_t* rowc = pd.cost + (size_t)yy * W * Dp + d0;
+        cp_async<DC>(cs, ok && lo_in ? rowc + (size_t)xlo * Dp : pd.cost, ok && lo_in);
+        cp_async<DC>(cs + NT, ok && hi_in ? rowc + (size_t)xhi * Dp : pd.cost, ok && hi_in);
+      }
       if (Cfg::SEC && second && owned) {
         uint4* xs = ringx + (r % RING) * XW * NO + t;
-        const uint4* sd = sd_out + (ok ? (size_t)yy * sd_row : 0);
+        if (parts & 2) {
+          const uint4* sd = sd_out + (ok ? (size_t)yy * sd_row : 0);
 #pragma unroll
-        for (int w = 0; w < G; w++) cp_async<16>(xs + w * NO, sd + w, ok);
-        const size_t ol = ((size_t)yy * W + xlo) * Dp + d0, oh = ((size_t)yy * W + xhi) * Dp + d0;
-        const bool fl = ok && lo_in, fh = ok && hi_in;
-        cp_async<DC>(xs + (G + 0) * NO, fl && a.en_h0 ? pd.hfwd + ol : pd.hfwd, fl && a.en_h0);
-        cp_async<DC>(xs + (G + 1) * NO, fh && a.en_h0 ? pd.hfwd + oh : pd.hfwd, fh && a.en_h0);
-        cp_async<DC>(xs + (G + 2) * NO, fl && a.en_h1 ? pd.hbwd + ol : pd.hbwd, fl && a.en_h1);
-        cp_async<DC>(xs + (G + 3) * NO, fh && a.en_h1 ? pd.hbwd + oh : pd.hbwd, fh && a.en_h1);
+          for (int w = 0; w < G; w++) cp_async<16>(xs + w * NO, sd + w, ok);
+        }
+        if (parts & 4) {
+          const size_t ol = ((size_t)yy * W + xlo) * Dp + d0, oh = ((size_t)yy * W + xhi) * Dp + d0;
+          const bool fl = ok && lo_in, fh = ok && hi_in;
+          cp_async<DC>(xs + (G + 0) * NO, fl && a.en_h0 ? pd.hfwd + ol : pd.hfwd, fl && a.en_h0);
+          cp_async<DC>(xs + (G + 1) * NO, fh && a.en_h0 ? pd.hfwd + oh : pd.hfwd, fh && a.en_h0);
+          cp_async<DC>(xs + (G + 2) * NO, fl && a.en_h1 ? pd.hbwd + ol : pd.hbwd, fl && a.en_h1);
+          cp_async<DC>(xs + (G + 3) * NO, fh && a.en_h1 ? pd.hbwd + oh : pd.hbwd, fh && a.en_h1);
+        }
       }
       cp_async_commit();
     };
-    // a second arrival of a merged launch reads the other order's partial
-    // sums, which exist only after its wait: it prefetches after the wait
+    // A second arrival of a merged launch reads the other order's partial
+    // sums, which exist only after its wait: its first rows' costs (and,
+    // when the horizontal paths ran in an earlier launch, their volumes) are
+    // requested before the wait, the partial sums after it.  The extra
+    // commit group is older than every later row's, so the ring's
+    // wait_group count still covers each row.
     const bool early = !(MERGED && second);
-    if (early) {
+    const int pre = early ? 7 : (HL ? 1 : 1 | 4);
 #pragma unroll
-      for (int r = 0; r < RING - 1; r++) issue_row(r);
-    }
+    for (int r = 0; r < RING - 1; r++) issue_row(r, pre);
     // ---- wait for the previous band of this strip and its neighbours, and
     // (second arrival of a merged launch) for the other scan order's pass
-    // over this band of this strip ----
-    if (t == 0) {
-      long long spins = 0;
-      auto wait_flag = [&](const int* f, int target) {
-        while (ld_acquire(f) < target) {
+    // over this band of this strip: the first warp's lanes poll one flag
+    // each, so the flags' round trips overlap (at most 3 + 1 + 4 flags) ----
+    if (t < 32) {
+      const int* fp = nullptr;
+      int tgt = 0, idx = 0;
+      auto add = [&](const int* f, int target) {
+        if (idx == t) {
+          fp = f;
+          tgt = target;
+        }
+        idx++;
+      };
+      if (bi > 0) {
+        for (int n = j - 1; n <= j + 1; n++)
+          if (n >= 0 && n < J) add(flags + n, bi);
+      }
+      if (MERGED && second) add((up ? pd.flags_down : pd.flags_up) + j, up ? band + 1 : pd.nb - band);
+      if (HL && second) {
+        // the horizontal paths of this band's rows
+        const int hr0 = ytop / (2 * NP), hr1 = (ytop + nrows - 1) / (2 * NP);
+        for (int dir = 0; dir < 2; dir++)
+          for (int rb = hr0; rb <= hr1; rb++) add(pd.flags_h + dir * a.hl_blocks + rb, 1);
+      }
+      if (fp) {
+        long long spins = 0;
+        while (ld_acquire(fp) < tgt) {
           if (++spins > a.spin_limit || *((volatile int*)a.err) != 0) {
             atomicExch(a.err, 1);
             s_abort = 1;
-            return;
+            break;
           }
           if (spins > 64) __nanosleep(32);
         }
-      };
-      if (bi > 0) {
-        for (int n = j - 1; n <= j + 1 && !s_abort; n++)
-          if (n >= 0 && n < J) wait_flag(flags + n, bi);
-      }
-      if (MERGED && second && !s_abort)
-        wait_flag((up ? pd.flags_down : pd.flags_up) + j, up ? band + 1 : pd.nb - band);
-      if (HL && second && !s_abort) {
-        // the horizontal paths of this band's rows
-        const int hr0 = ytop / (2 * NP), hr1 = (ytop + nrows - 1) / (2 * NP);
-        for (int dir = 0; dir < 2 && !s_abort; dir++)
-          for (int rb = hr0; rb <= hr1 && !s_abort; rb++) wait_flag(pd.flags_h + dir * a.hl_blocks + rb, 1);
       }
     }
     __syncthreads();
@@ -604,9 +632,14 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
       cp_async_wait<0>();
       return;
     }
+    // claim the next task now (every thread read this one's index before
+    // the barrier above); the last thread, a halo lane, holds the answer in
+    // a register until the band ends, so no warp waits for the round trip
+    int next_task = 0;
+    if (t == NT - 1) next_task = atomicAdd(a.task_counter, 1);
     if (!early) {
 #pragma unroll
-      for (int r = 0; r < RING - 1; r++) issue_row(r);
+      for (int r = 0; r < RING - 1; r++) issue_row(r, 7 & ~pre);
     }
 
     // lanes whose predecessor column lies outside the image start a path
@@ -747,7 +780,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
 
     for (int k = 0; k < nrows; k++) {
       const int y = up ? ytop + nrows - 1 - k : ytop + k;
-      issue_row(k + RING - 1);
+      issue_row(k + RING - 1, 7);
       cp_async_wait<RING - 1>();
       {
         const V* cs = ringc + (k % RING) * 2 * NT + t;
@@ -1014,6 +1047,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     cp_async_wait<0>();
     __syncthreads();
     if (t == 0) st_release(flags + j, bi + 1);
+    if (t == NT - 1) s_task = next_task;   // read after the barrier at the top of the loop
     select_row(nrows - 1);   // the last row of the band (its costs are in place)
   }
 }
