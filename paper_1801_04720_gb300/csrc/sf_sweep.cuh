@@ -371,9 +371,11 @@ struct SweepCfg {
   static constexpr int TH = HALO + 1;       // band rows
   static constexpr int RING = SEC ? 2 : 3;  // prefetch depth in rows
   static constexpr int XW = DC / 4 + 4;     // uint4 slots per owned thread per row (second arrival)
+  // halo threads per owned column pair for the winner selection
+  static constexpr int select_threads() { return (HALO * CHUNKS) / 16 > 0 ? (HALO * CHUNKS) / 16 : 1; }
   static constexpr bool select_by_halo() {
-    return SEC && CHUNKS >= 2 && (HALO * CHUNKS) / kTW >= 1 &&
-           (CHUNKS % ((HALO * CHUNKS) / kTW > 0 ? (HALO * CHUNKS) / kTW : 1)) == 0;
+    return SEC && CHUNKS >= 2 && (HALO * CHUNKS) / 16 >= 1 && select_threads() <= 32 &&
+           (CHUNKS % select_threads()) == 0;
   }
   static constexpr size_t smem_bytes() {
     return (size_t)2 * 2 * (DC / 4) * NT * 16     // diagonal hand-over
@@ -407,9 +409,9 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   using V = typename ByteVec<DC>::T;
   constexpr int NP = Cfg::NP, NT = Cfg::NT, NO = Cfg::NO, TH = Cfg::TH, RING = Cfg::RING;
   constexpr int XW = Cfg::XW, G = DC / 4;
-  // winner selection by the halo warps (they carry two paths, the owned
-  // warps three plus the sums): SEL_T threads per output column
-  constexpr int SEL_T = (HALO * CHUNKS) / kTW;
+  // winner selection by the halo warps (they carry one path, the owned
+  // warps three plus the sums): SEL_P threads per owned column pair
+  constexpr int SEL_P = Cfg::select_threads();
   constexpr bool HALO_SELECT = Cfg::select_by_halo();
   extern __shared__ __align__(16) uint8_t smem[];
   // diagonal hand-over buffers, [parity][register group][thread] uint4
@@ -696,71 +698,89 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
       }
     }
 
-    // winner-take-all + parabolic subpixel of row kk, done by halo threads
-    // from the aggregated costs the owned threads left in shared memory
+    // winner-take-all + parabolic subpixel of row kk, done by the halo
+    // threads from the aggregated costs the owned threads left in shared
+    // memory: SEL_P threads per owned column pair, packed u16x2 minima over
+    // both columns at once.  Padding disparities hold 0xffff there, above
+    // every aggregated cost (at most 8 x 255).
     auto select_row = [&](int kk) {
       if (!HALO_SELECT || owned || !pd.dint || !second) return;
+      constexpr int PT = SEL_P, CPT = CHUNKS / SEL_P;
       const int yk = up ? ytop + nrows - 1 - kk : ytop + kk;
       const int ht = t - NO;
-      constexpr int ST = SEL_T > 0 ? SEL_T : 1;
-      const int c = ht / ST, sub = ht - c * ST;
-      const int cpr = c & 15, cl = c >> 4;
-      const int x = x0 + c;
-      const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow + (kk & 1) * G * NO);
-      auto s_at = [&](int d) {
-        const int qq = d / DC, ii = d - qq * DC;
-        return (sw[((ii >> 2) * NO + cpr * CHUNKS + qq) * 4 + (ii & 3)] >> (16 * cl)) & 0xffffu;
-      };
-      constexpr int CPT = CHUNKS / (SEL_T > 0 ? SEL_T : 1);
-      uint32_t key = 0xffffffffu;   // S * 256 + d: the minimum is the smallest d with minimal S
+      const int cp = ht / PT, sub = ht - cp * PT;
+      const uint4* rw = srow + (kk & 1) * G * NO + cp * CHUNKS + sub * CPT;
+      // the minimal S of each column, over this thread's chunks, then over
+      // the pair's threads
+      uint32_t g = 0xffffffffu;
 #pragma unroll
-      for (int j = 0; j < CPT; j++) {
-        const int qq = sub * CPT + j;
+      for (int jj = 0; jj < CPT; jj++) {
 #pragma unroll
         for (int w = 0; w < G; w++) {
-          const uint4 v4 = srow[(kk & 1) * G * NO + w * NO + cpr * CHUNKS + qq];
-          const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
-#pragma unroll
-          for (int e = 0; e < 4; e++) {
-            const int d = qq * DC + 4 * w + e;
-            const uint32_t sv = (vv[e] >> (16 * cl)) & 0xffffu;
-            if (d < D) key = min(key, sv * 256u + (uint32_t)d);
-          }
+          const uint4 v4 = rw[w * NO + jj];
+          g = vmin2(g, vmin2(vmin2(v4.x, v4.y), vmin2(v4.z, v4.w)));
         }
       }
 #pragma unroll
-      for (int o = 1; o < SEL_T; o <<= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o, SEL_T > 0 ? SEL_T : 1));
-      // uniqueness: the smallest S two or more disparities away from d*
-      uint32_t s2 = 0xffffu;
-      if (VAR && a.unique && pd.dsub) {
-        const int dk = (int)(key & 255u);
+      for (int o = 1; o < PT; o <<= 1) g = vmin2(g, __shfl_xor_sync(0xffffffffu, g, o, PT));
+      // the first disparity reaching it: key = (S > min) * 256 + d per
+      // column (S - min >= 0 lane-wise, so the subtraction borrows nothing)
+      uint32_t key = 0xffffffffu;
 #pragma unroll
-        for (int j = 0; j < CPT; j++) {
-          const int qq = sub * CPT + j;
+      for (int jj = 0; jj < CPT; jj++) {
+        const uint32_t db = (uint32_t)((sub * CPT + jj) * DC) * 0x10001u;
+#pragma unroll
+        for (int w = 0; w < G; w++) {
+          const uint4 v4 = rw[w * NO + jj];
+          const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+          for (int e = 0; e < 4; e++)
+            key = vmin2(key, vmin2(vv[e] - g, 0x10001u) * 256u + db + (uint32_t)(4 * w + e) * 0x10001u);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < PT; o <<= 1) key = vmin2(key, __shfl_xor_sync(0xffffffffu, key, o, PT));
+      // uniqueness: the smallest S two or more disparities away from d*
+      uint32_t s2 = 0xffffffffu;
+      if (VAR && a.unique && pd.dsub) {
+        const int dl = (int)(key & 0xffu), dh = (int)((key >> 16) & 0xffu);
+#pragma unroll
+        for (int jj = 0; jj < CPT; jj++) {
 #pragma unroll
           for (int w = 0; w < G; w++) {
-            const uint4 v4 = srow[(kk & 1) * G * NO + w * NO + cpr * CHUNKS + qq];
+            const uint4 v4 = rw[w * NO + jj];
             const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-              const int d = qq * DC + 4 * w + e;
-              if (d < D && (d + 1 < dk || d > dk + 1)) s2 = min(s2, (vv[e] >> (16 * cl)) & 0xffffu);
+              const int d = (sub * CPT + jj) * DC + 4 * w + e;
+              const uint32_t ex = ((d >= dl - 1 && d <= dl + 1) ? 0x0000ffffu : 0u) |
+                                  ((d >= dh - 1 && d <= dh + 1) ? 0xffff0000u : 0u);
+              s2 = vmin2(s2, vv[e] | ex);
             }
           }
         }
 #pragma unroll
-        for (int o = 1; o < SEL_T; o <<= 1) s2 = min(s2, __shfl_xor_sync(0xffffffffu, s2, o, SEL_T > 0 ? SEL_T : 1));
+        for (int o = 1; o < PT; o <<= 1) s2 = vmin2(s2, __shfl_xor_sync(0xffffffffu, s2, o, PT));
       }
-      if (sub == 0 && x < W) {
-        const int ds = (int)(key & 255u);
-        const int sv = (int)(key >> 8);
+      // thread 0 of the pair writes the low column, thread 1 the high one
+      const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow + (kk & 1) * G * NO);
+      for (int l = sub; l < 2; l += PT) {
+        const int x = x0 + cp + 16 * l;
+        if (x >= W) continue;
+        const int sh = 16 * l;
+        auto s_at = [&](int d) {
+          const int qq = d / DC, ii = d - qq * DC;
+          return (sw[((ii >> 2) * NO + cp * CHUNKS + qq) * 4 + (ii & 3)] >> sh) & 0xffffu;
+        };
+        const int ds = (int)((key >> sh) & 0xffu);
+        const int sv = (int)((g >> sh) & 0xffffu);
         float v = (float)ds;
         if (a.subpixel && ds > 0 && ds < D - 1) {
           const int am = (int)s_at(ds - 1) - sv;
           const int bp = (int)s_at(ds + 1) - sv;
           v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
         }
-        if (VAR && 100 * (int)s2 < (100 + a.unique) * sv) v = __int_as_float(0x7fc00000);   // not unique
+        if (VAR && 100 * (int)((s2 >> sh) & 0xffffu) < (100 + a.unique) * sv) v = __int_as_float(0x7fc00000);
         pd.dint[(size_t)yk * W + x] = (int16_t)ds;
         if (pd.dsub) pd.dsub[(size_t)yk * W + x] = v;
       }
