@@ -168,6 +168,48 @@ def bytes_model(stage, N, D, passes=4, order=1):
     return 3 * N * D
 
 
+def densify_bytes_model(N):
+    """Algorithmic HBM bytes of one sf_densify_sceneflow call on a frame:
+    per map (d0, d1) the row pass reads the sparse value twice and writes it
+    twice (the parked index, then the value: 16 N); then the dense
+    back-projection reads the flow and s4 (24 N) and writes s4, motion, point
+    and validity (41 N).  The column pass touches only rows with nothing
+    kept (none on these frames)."""
+    return 2 * 16 * N + 24 * N + 41 * N
+
+
+def run_densify(_lib, torch, out, flow, cam, guide, stream, flush, N):
+    """Time of the densification call on the frame's sparse output, both
+    modes (L2 flushed between calls)."""
+    H, W = out["s4"].shape[:2]
+    dev = out["s4"].device
+    dn = {"s4": torch.empty((H, W, 4), dtype=torch.float32, device=dev),
+          "motion": torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+          "point": torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+          "valid": torch.empty((H, W), dtype=torch.uint8, device=dev)}
+    res = {"call": "sf_densify_sceneflow on the frame's sparse s4 (fill_rows, fill_cols, backproject kernels)"}
+    hbm_peak = peaks()[0]
+    for mode, tag in ((0, "background"), (1, "edge_aware")):
+        for _ in range(3):
+            _lib.sf_densify_sceneflow(out["s4"], flow, cam, guide=guide, mode=mode, out=dn, stream=stream)
+        ms = []
+        for k in range(20):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _lib.sf_densify_sceneflow(out["s4"], flow, cam, guide=guide, mode=mode, out=dn, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.mean(ms)
+        b = densify_bytes_model(N) + (N if mode == 1 else 0)
+        res[tag] = {"ms_per_call": round(t, 4), "model_bytes": b,
+                    "achieved_gbs": round(b / (t * 1e-3) / 1e9, 1),
+                    "frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)}
+    res["model"] = "densify_bytes_model: 97 N (+ N guide reads in the edge-aware mode)"
+    return res
+
+
 def frame_bytes_model(N, D):
     """Algorithmic HBM bytes of one plain scene-flow frame (4 SGM passes and
     the combination) for a design that stores nothing but the partial sum of
@@ -391,6 +433,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         result["accuracy_vs_ground_truth"][tag] = {k: round(v, 5) for k, v in evaluate.scene_flow_accuracy(
             dn["s4"].cpu(), dn["valid"].cpu(), q.gt_disp0, q.gt_disp1, q.gt_flow).items()}
+    result["densify"] = run_densify(_lib, torch, out, flow, cam, imgs[0], stream, flush, N)
     if args.batch > 0:
         result["batch"] = run_batch(args, dev, _lib, synth, torch)
     if args.learned_eval >= 0:

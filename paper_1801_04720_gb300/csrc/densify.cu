@@ -16,7 +16,8 @@
 //     finds, with a ballot and a carry from the previous chunks, the nearest
 //     kept pixel at or before each pixel and parks its index in the output
 //     (as the bits of the float); a backward pass finds the nearest kept
-//     pixel after it the same way and writes the filled value.
+//     pixel after it the same way and writes the filled value.  Groups of
+//     chunks issue their loads together.
 //   fill_cols_kernel: the rows the row pass left missing (the same in every
 //     column) are marked once per block; one thread per column fills them
 //     from the nearest filled rows above and below.
@@ -52,6 +53,11 @@ __device__ __forceinline__ float choose(const FillArgs& a, float va, float vb, s
   return fminf(va, vb);
 }
 
+// Chunks of 32 pixels handled per group: their loads are issued together
+// (the carries between chunks are register work), so a row costs a few
+// memory round trips instead of one per chunk.
+constexpr int kFillGroup = 4;
+
 __global__ void __launch_bounds__(256) fill_rows_kernel(const FillArgs a) {
   const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -64,44 +70,68 @@ __global__ void __launch_bounds__(256) fill_rows_kernel(const FillArgs a) {
   auto at_in = [&](int x) { return in[(row + x) * a.istride]; };
   const unsigned below = (2u << lane) - 1u;   // lanes 0 .. lane
   const unsigned above = ~((1u << lane) - 1u); // lanes lane .. 31
-  // forward: index of the nearest kept pixel at or before x (-1: none)
+  const int nch = (W + 31) / 32;
+  // forward: index of the nearest kept pixel at or before x (-1: none),
+  // parked in the output as the bits of the float
   int carry = -1;
-  for (int c = 0; c < W; c += 32) {
-    const int x = c + lane;
-    const float v = x < W ? at_in(x) : fnan();
-    const bool ok = x < W && !isnan(v);
-    const unsigned b = __ballot_sync(0xffffffffu, ok);
-    const unsigned mb = b & below;
-    const int left = mb ? c + 31 - __clz(mb) : carry;
-    if (x < W) out[(row + x) * a.ostride] = ok ? v : __int_as_float(left);
-    if (b) carry = c + 31 - __clz(b);
+  for (int c0 = 0; c0 < nch; c0 += kFillGroup) {
+    float v[kFillGroup];
+#pragma unroll
+    for (int u = 0; u < kFillGroup; u++) {
+      const int x = (c0 + u) * 32 + lane;
+      v[u] = (c0 + u < nch && x < W) ? at_in(x) : fnan();
+    }
+#pragma unroll
+    for (int u = 0; u < kFillGroup; u++) {
+      const int c = (c0 + u) * 32, x = c + lane;
+      const bool ok = x < W && !isnan(v[u]);
+      const unsigned b = __ballot_sync(0xffffffffu, ok);
+      const unsigned mb = b & below;
+      const int left = mb ? c + 31 - __clz(mb) : carry;
+      if (c0 + u < nch && x < W) out[(row + x) * a.ostride] = ok ? v[u] : __int_as_float(left);
+      if (b) carry = c + 31 - __clz(b);
+    }
   }
   __syncwarp();
   // backward: the nearest kept pixel at or after x, and the filled value
   carry = -1;
-  const int last = ((W - 1) / 32) * 32;
-  for (int c = last; c >= 0; c -= 32) {
-    const int x = c + lane;
-    const float v = x < W ? at_in(x) : fnan();
-    const bool ok = x < W && !isnan(v);
-    const unsigned b = __ballot_sync(0xffffffffu, ok);
-    const unsigned mb = b & above;
-    const int right = mb ? c + __ffs(mb) - 1 : carry;
-    if (x < W && !ok) {
-      const int left = __float_as_int(out[(row + x) * a.ostride]);
-      float r;
-      if (left >= 0 && right >= 0)
-        r = choose(a, at_in(left), at_in(right), (size_t)y * a.gpitch + x, (size_t)y * a.gpitch + left,
-                   (size_t)y * a.gpitch + right);
-      else if (left >= 0)
-        r = at_in(left);
-      else if (right >= 0)
-        r = at_in(right);
-      else
-        r = fnan();
-      out[(row + x) * a.ostride] = r;
+  for (int c0 = nch - 1; c0 >= 0; c0 -= kFillGroup) {
+    float v[kFillGroup];
+    int left[kFillGroup], right[kFillGroup];
+#pragma unroll
+    for (int u = 0; u < kFillGroup; u++) {
+      const int x = (c0 - u) * 32 + lane;
+      const bool in_row = c0 - u >= 0 && x < W;
+      v[u] = in_row ? at_in(x) : fnan();
+      left[u] = in_row ? __float_as_int(out[(row + x) * a.ostride]) : -1;   // the parked index where v is NaN
     }
-    if (b) carry = c + __ffs(b) - 1;
+#pragma unroll
+    for (int u = 0; u < kFillGroup; u++) {
+      const int c = (c0 - u) * 32, x = c + lane;
+      const bool ok = c0 - u >= 0 && x < W && !isnan(v[u]);
+      const unsigned b = __ballot_sync(0xffffffffu, ok);
+      const unsigned mb = b & above;
+      right[u] = mb ? c + __ffs(mb) - 1 : carry;
+      if (b) carry = c + __ffs(b) - 1;
+    }
+    // the gaps' values: the gathers of every chunk of the group together
+#pragma unroll
+    for (int u = 0; u < kFillGroup; u++) {
+      const int x = (c0 - u) * 32 + lane;
+      if (c0 - u < 0 || x >= W || !isnan(v[u])) continue;
+      const int l = left[u], r = right[u];
+      float res;
+      if (l >= 0 && r >= 0)
+        res = choose(a, at_in(l), at_in(r), (size_t)y * a.gpitch + x, (size_t)y * a.gpitch + l,
+                     (size_t)y * a.gpitch + r);
+      else if (l >= 0)
+        res = at_in(l);
+      else if (r >= 0)
+        res = at_in(r);
+      else
+        res = fnan();
+      out[(row + x) * a.ostride] = res;
+    }
   }
 }
 

@@ -413,6 +413,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   // warps three plus the sums): SEL_P threads per owned column pair
   constexpr int SEL_P = Cfg::select_threads();
   constexpr bool HALO_SELECT = Cfg::select_by_halo();
+  static_assert(HALO_SELECT || !Cfg::SEC, "launches with second arrivals select by the halo threads");
   extern __shared__ __align__(16) uint8_t smem[];
   // diagonal hand-over buffers, [parity][register group][thread] uint4
   // (consecutive threads hit consecutive 16-byte words: no bank conflicts)
@@ -907,64 +908,9 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
               }
             }
           }
-          if (pd.dint && HALO_SELECT) {
+          if (pd.dint) {
             // the halo warps select the winners of this row after the barrier
             store_u4<DC>(srow + (k & 1) * G * NO + t, NO, S);
-          } else if (pd.dint) {
-            // winner-take-all: the smallest d with the minimal S, per lane
-            const uint32_t gmin = group_min2<CHUNKS>(tree_min<DC>(S), role_mask);
-            uint32_t first = 0xffffffffu;
-#pragma unroll
-            for (int i = DC - 1; i >= 0; i--) {
-              const uint32_t d2 = (uint32_t)(d0 + i) * 0x10001u;
-              const uint32_t x2 = S[i] ^ gmin;
-              const uint32_t eq = ((x2 & 0xffffu) ? 0u : 0x0000ffffu) | ((x2 >> 16) ? 0u : 0xffff0000u);
-              first = (first & ~eq) | (d2 & eq);
-            }
-            const uint32_t dstar2 = group_min2<CHUNKS>(first, role_mask);
-            // uniqueness: per lane, the smallest S two or more disparities
-            // away from that lane's d* (0xffff: none)
-            uint32_t s2x2 = 0xffffffffu;
-            if (VAR && a.unique && pd.dsub) {
-              const int dl = (int)(dstar2 & 0xffffu), dh = (int)(dstar2 >> 16);
-#pragma unroll
-              for (int i = 0; i < DC; i++) {
-                const int d = d0 + i;
-                const uint32_t ex = ((d >= dl - 1 && d <= dl + 1) ? 0x0000ffffu : 0u) |
-                                    ((d >= dh - 1 && d <= dh + 1) ? 0xffff0000u : 0u);
-                s2x2 = vmin2(s2x2, S[i] | ex);
-              }
-              s2x2 = group_min2<CHUNKS>(s2x2, role_mask);
-            }
-            // S(d*-1) and S(d*+1) through shared memory, [group][thread];
-            // chunk 0 finishes the low lane's column, chunk 1 the high one
-            store_u4<DC>(srow + t, NO, S);
-            __syncwarp(role_mask);
-            if (q < 2) {
-              const int l = q;
-              const int x = l ? xhi : xlo;
-              if (x >= 0 && x < W) {
-                const int sh = 16 * l;
-                const int ds = (dstar2 >> sh) & 0xffff;
-                const uint32_t* sw = reinterpret_cast<const uint32_t*>(srow);
-                auto s_at = [&](int d) {   // S at disparity d of this pair
-                  const int qq = d / DC, ii = d - qq * DC;
-                  return (sw[((ii >> 2) * NO + pr * CHUNKS + qq) * 4 + (ii & 3)] >> sh) & 0xffffu;
-                };
-                float v = (float)ds;
-                if (a.subpixel && ds > 0 && ds < D - 1) {
-                  const int sv = (int)s_at(ds);
-                  const int am = (int)s_at(ds - 1) - sv;
-                  const int bp = (int)s_at(ds + 1) - sv;
-                  v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
-                }
-                if (VAR && 100 * (int)((s2x2 >> sh) & 0xffffu) < (100 + a.unique) * (int)((gmin >> sh) & 0xffffu))
-                  v = __int_as_float(0x7fc00000);   // not unique
-                pd.dint[(size_t)y * W + x] = (int16_t)ds;
-                if (pd.dsub) pd.dsub[(size_t)y * W + x] = v;
-              }
-            }
-            __syncwarp(role_mask);
           }
         }
 #pragma unroll

@@ -86,3 +86,10 @@ def test_all_cores_oracle_equals_the_oracle():
     assert np.array_equal(keep["valid"], ref["valid"])
     assert np.array_equal(keep["s4"], ref["s4"], equal_nan=True)
     assert np.array_equal(keep["motion"], ref["motion"], equal_nan=True)
+
+
+def test_densify_bytes_model():
+    import bench
+    N = 1242 * 375
+    # two maps: row pass read twice + written twice (16 N); back-projection 24 N in, 41 N out
+    assert bench.densify_bytes_model(N) == 2 * 16 * N + 24 * N + 41 * N == 97 * N
