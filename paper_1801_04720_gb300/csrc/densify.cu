@@ -56,7 +56,7 @@ __device__ __forceinline__ float choose(const FillArgs& a, float va, float vb, s
 // Chunks of 32 pixels handled per group: their loads are issued together
 // (the carries between chunks are register work), so a row costs a few
 // memory round trips instead of one per chunk.
-constexpr int kFillGroup = 4;
+constexpr int kFillGroup = 8;
 
 __global__ void __launch_bounds__(256) fill_rows_kernel(const FillArgs a) {
   const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -153,13 +153,12 @@ __global__ void __launch_bounds__(256) fill_cols_kernel(const FillArgs a) {
   const int x = x0 + threadIdx.x;
   float* out = a.out[m];
   const int words = (H + 31) / 32;
-  for (int w = threadIdx.x; w < words; w += blockDim.x) {
-    uint32_t bits = 0;
-    for (int b = 0; b < 32; b++) {
-      const int y = 32 * w + b;
-      if (y < H && isnan(out[((size_t)y * W + x0) * a.ostride])) bits |= 1u << b;
-    }
-    empty[w] = bits;
+  // one row per thread, a ballot per warp: bit y of the marks is row y
+  for (int y0 = 0; y0 < 32 * words; y0 += blockDim.x) {
+    const int y = y0 + (int)threadIdx.x;
+    const bool e = y < H && isnan(out[((size_t)y * W + x0) * a.ostride]);
+    const uint32_t bits = __ballot_sync(0xffffffffu, e);
+    if ((threadIdx.x & 31) == 0 && y < 32 * words) empty[y >> 5] = bits;
   }
   __syncthreads();
   if (x >= W) return;
