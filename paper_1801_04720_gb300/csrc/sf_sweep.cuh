@@ -1031,8 +1031,9 @@ cudaError_t sweep_dispatch(const SweepArgs& a, cudaStream_t s) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  // one wave of CTAs; tasks come from a queue, and a task is only waited on
-  // after a running CTA has taken it, so no co-residency guarantee is needed
+  // one wave of CTAs; tasks come from a queue and are claimed only by
+  // running CTAs, each of which finishes its current (earlier) task before
+  // the one it claimed, so no co-residency guarantee is needed
   const int grid = std::max(1, std::min(a.ntasks, per_sm * sms));
   kern<<<grid, Cfg::NT, smem, s>>>(a);
   return cudaGetLastError();
