@@ -108,3 +108,31 @@ def test_cache_is_keyed_by_gpu_and_size(tmp_path):
     assert autotune.cached(str(path), "GPU-A", 1242, 375) is None
     path.write_text("{not json")
     assert autotune.cached(str(path), "GPU-A", 1242, 375) is None
+
+
+def test_tune_table_picks_the_fastest_and_drops_each_trial(monkeypatch):
+    """The per-table search with a fake timer: every built candidate is
+    installed once, dropped after its timing, and the fastest is kept."""
+    from paper_1801_04720_gb300 import autotune, synth
+    monkeypatch.setattr(synth, "fronto_planes", lambda **kw: None)
+    calls = []
+
+    def setter(lo, hi, dc, halo, order):
+        calls.append((lo, hi, dc, halo, order))
+        if (dc, halo) == (8, 8) and order == 2:
+            raise autotune._lib.SFError("sf_set_sweep_schedule", 2)   # not built
+
+    def timer(q, D):
+        dc, halo, order = calls[-1][2:]
+        return 1.0 + 0.1 * order + (0.05 if dc == 8 else 0.0) + (0.01 if halo == 16 else 0.0)
+
+    out = autotune._tune_table([(65, 128)], 1242, 375, 0, timer, setter)
+    assert len(out) == 1
+    best = out[0]
+    assert (best["dc"], best["halo"], best["order"]) == (16, 8, 0)
+    assert "8x8o2" not in best["candidates_ms"]
+    assert len(best["candidates_ms"]) == len(autotune.CANDIDATES) - 1
+    # every trial is followed by dropping the class again
+    trials = [c for c in calls if c[2] != 0]
+    drops = [c for c in calls if c[2] == 0]
+    assert len(drops) == len(trials) - 1 and all(c[:2] == (65, 128) for c in calls)
