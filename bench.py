@@ -210,6 +210,25 @@ def run_densify(_lib, torch, out, flow, cam, guide, stream, flush, N):
     return res
 
 
+def stage_bytes_model(stage, N, D, passes=4):
+    """Algorithmic HBM bytes per frame of each stage of the plain path as the
+    kernels are built (stored cost and horizontal volumes included):
+    census: four images in, four uint64 strings out (36 N);
+    cost: the strings in, both references' uint8 volumes of both pairs out
+      (32 N + 4 N Dp);
+    aggregate (horizontal paths): per pass the cost in and both uint8 path
+      volumes out (3 N Dp);
+    sgm_sweep: the partial sums of one scan order written and read, uint16
+      (4 N D per pass; the stored volumes it also reads are not counted);
+    combine (both checks and the combination): winners and subpixel maps of
+      both pairs and the flow in (24 N), both disparity maps, s4, motion,
+      point and validity out (49 N)."""
+    Dp = (D + 15) // 16 * 16
+    return {"census": 36 * N, "cost": 32 * N + passes * N * Dp,
+            "aggregate": passes * 3 * N * Dp, "sgm_sweep": passes * 4 * N * D,
+            "combine": 73 * N}.get(stage)
+
+
 def frame_bytes_model(N, D):
     """Algorithmic HBM bytes of one plain scene-flow frame (4 SGM passes and
     the combination) for a design that stores nothing but the partial sum of
@@ -412,6 +431,9 @@ def run_ours(args, world, rank, local):
                       "frac": round(frame_bytes_model(N, D_MAX) / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                       "model": "frame_bytes_model: 16 N D + 149 N"},
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_tot.items()},
+        "stages_hbm": {k: {"model_bytes": stage_bytes_model(k, N, D_MAX),
+                           "frac": round(stage_bytes_model(k, N, D_MAX) / (v / args.steps * 1e-3) / 1e9 / hbm_peak, 4)}
+                       for k, v in stage_tot.items() if stage_bytes_model(k, N, D_MAX)},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "sweep_shape": tuned["classes"] if tuned else "built-in",
         "learned_sweep_shape": (tuned.get("learned") or "built-in") if tuned else "built-in",

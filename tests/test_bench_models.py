@@ -93,3 +93,15 @@ def test_densify_bytes_model():
     N = 1242 * 375
     # two maps: row pass read twice + written twice (16 N); back-projection 24 N in, 41 N out
     assert bench.densify_bytes_model(N) == 2 * 16 * N + 24 * N + 41 * N == 97 * N
+
+
+def test_stage_bytes_model():
+    import bench
+    N, D = 1242 * 375, 128
+    m = {k: bench.stage_bytes_model(k, N, D) for k in ("census", "cost", "aggregate", "sgm_sweep", "combine")}
+    assert m["census"] == 4 * N + 4 * 8 * N
+    assert m["cost"] == 4 * 8 * N + 4 * N * D                # two pairs, both references
+    assert m["aggregate"] == 4 * (N * D + 2 * N * D)          # cost in, two path volumes out
+    assert m["sgm_sweep"] == bench.bytes_model("sgm_sweep", N, D, order=1)
+    assert m["combine"] == (2 + 2 + 4) * 2 * N + 8 * N + (4 + 4 + 16 + 12 + 12 + 1) * N
+    assert bench.stage_bytes_model("features", N, D) is None
