@@ -97,7 +97,7 @@ bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 // Completion flags of the horizontal paths' row blocks of one pass (two
 // directions, row blocks of at least 16 rows) for the launch that runs them
 // beside the sweeps.
-inline int flags_h_count(int H) { return 2 * ((H + 15) / 16); }
+inline int flags_h_count(int H) { return 2 * ((H + 3) / 4); }   // row blocks of 4 rows or more
 
 // Workspace of sf_sgm_full / sf_scene_flow, carved with 256-byte alignment.
 struct Workspace {
@@ -366,7 +366,7 @@ sf_status run_sweeps(const sf_sgm_params* p, const fused::PassDesc* d, int npass
     sa.ntasks = tt->ntasks;
   }
   if (with_h) {
-    const int rows = 2 * (16 + shape.halo);
+    const int rows = fused::merged_hline_rows(shape.dc, shape.chunks, shape.halo);
     sa.hl_blocks = (d[0].H + rows - 1) / rows;
     sa.hl_tasks = npass * 2 * sa.hl_blocks;
     sa.ntasks += sa.hl_tasks;

@@ -31,6 +31,14 @@ Shape shape_for(int D, int table = kShapePlain);
 bool shape_supported(int dc, int chunks, int halo);
 int set_shape_override(int table, int d_lo, int d_hi, int dc, int halo, int order);   // 0 = ok
 inline int padded_d(int D) { return ((D + 15) / 16) * 16; }
+// Rows per block of the horizontal paths run inside a merged launch (launch
+// mode 3) by its CTAs of (16 + halo) x chunks threads: above 64 disparities
+// a warp per line pair, when the CTA is whole warps, as in the standalone
+// walk; otherwise the sweep's own thread layout, 16 + halo line pairs.
+__host__ __device__ constexpr int merged_hline_rows(int dc, int chunks, int halo) {
+  return ((16 + halo) * chunks % 32 == 0 && dc * chunks > 64) ? 2 * ((16 + halo) * chunks / 32)
+                                                                : 2 * (16 + halo);
+}
 inline int band_rows(int D, int table = kShapePlain) { return shape_for(D, table).halo + 1; }
 
 // One stereo pass (one reference image) of the band sweeps and the

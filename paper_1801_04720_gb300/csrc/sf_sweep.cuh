@@ -429,6 +429,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
   __shared__ uint16_t s_lut[256];   // adaptive P2 by intensity step
   constexpr bool MERGED = Cfg::MERGED;
   constexpr bool HL = MODE == kModeMergedH;
+  constexpr int HL_ROWS = merged_hline_rows(DC, CHUNKS, HALO);   // rows per horizontal-path task
   __shared__ __align__(8) uint64_t hbars[2];   // horizontal-path tiles (HL)
   __shared__ int s_hfail;
   int hph[2] = {0, 0};
@@ -500,9 +501,18 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
         const PassDesc hd = a.pass_ptr ? a.pass_ptr[hp] : a.inl[hp];
         if ((a.path_mask >> dir) & 1u) {
           constexpr int kTile = (int)((Cfg::smem_bytes() / 2) & ~(size_t)127);
-          if (!hline_rows_call<DC, CHUNKS, VAR>(hd, dir, rb * 2 * NP, NP, a.P1, a.P2, smem, kTile, hbars, &s_hfail,
-                                                s_lut, hph, a.err))
-            return;
+          // a warp per line pair above 64 disparities (4 a lane up to 128,
+          // 8 above), as the standalone walk; else the sweep's own layout
+          constexpr bool kWarp = HL_ROWS != 2 * NP;
+          constexpr int kHDC = DC * CHUNKS > 128 ? 8 : 4;
+          bool hok;
+          if constexpr (kWarp)
+            hok = hline_rows_call<kHDC, 32, VAR>(hd, dir, rb * HL_ROWS, HL_ROWS / 2, a.P1, a.P2, smem, kTile, hbars,
+                                                 &s_hfail, s_lut, hph, a.err);
+          else
+            hok = hline_rows_call<DC, CHUNKS, VAR>(hd, dir, rb * HL_ROWS, NP, a.P1, a.P2, smem, kTile, hbars,
+                                                   &s_hfail, s_lut, hph, a.err);
+          if (!hok) return;
         }
         __syncthreads();   // every thread's stores before the release
         if (t == 0) {
@@ -596,7 +606,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
     // ---- wait for the previous band of this strip and its neighbours, and
     // (second arrival of a merged launch) for the other scan order's pass
     // over this band of this strip: the first warp's lanes poll one flag
-    // each, so the flags' round trips overlap (at most 3 + 1 + 4 flags) ----
+    // each, so the flags' round trips overlap (at most 3 + 1 + 6 flags) ----
     if (t < 32) {
       const int* fp = nullptr;
       int tgt = 0, idx = 0;
@@ -614,7 +624,7 @@ __global__ void __launch_bounds__((16 + HALO) * CHUNKS, 1)
       if (MERGED && second) add((up ? pd.flags_down : pd.flags_up) + j, up ? band + 1 : pd.nb - band);
       if (HL && second) {
         // the horizontal paths of this band's rows
-        const int hr0 = ytop / (2 * NP), hr1 = (ytop + nrows - 1) / (2 * NP);
+        const int hr0 = ytop / HL_ROWS, hr1 = (ytop + nrows - 1) / HL_ROWS;
         for (int dir = 0; dir < 2; dir++)
           for (int rb = hr0; rb <= hr1; rb++) add(pd.flags_h + dir * a.hl_blocks + rb, 1);
       }
