@@ -160,12 +160,14 @@ def bytes_model(stage, N, D, passes=4, order=1):
     2*N*D bytes each way).  One launch covers the four passes of a frame.
     With both scan orders in one launch (orders 1 and 2) that launch does the
     write and the read -> 4 * 4*N*D bytes; with one launch per order (order 0)
-    each does one of them -> 4 * 2*N*D bytes.
-    aggregate (staged kernels): read the uint8 cost and write the uint16 sum
-    once per pass -> 3*N*D bytes."""
+    each does one of them -> 4 * 2*N*D bytes.  With order 2 the launch also
+    runs the horizontal paths: per pass the uint8 cost read once and both
+    uint8 path volumes written -> + 4 * 3*N*Dp bytes.
+    aggregate (the horizontal paths' own launch): the same 3*N*Dp per pass."""
+    Dp = (D + 15) // 16 * 16
     if stage == "sgm_sweep":
-        return passes * (4 if order >= 1 else 2) * N * D
-    return 3 * N * D
+        return passes * (4 if order >= 1 else 2) * N * D + (passes * 3 * N * Dp if order == 2 else 0)
+    return passes * 3 * N * Dp
 
 
 def densify_bytes_model(N):
@@ -210,7 +212,7 @@ def run_densify(_lib, torch, out, flow, cam, guide, stream, flush, N):
     return res
 
 
-def stage_bytes_model(stage, N, D, passes=4):
+def stage_bytes_model(stage, N, D, passes=4, order=1):
     """Algorithmic HBM bytes per frame of each stage of the plain path as the
     kernels are built (stored cost and horizontal volumes included):
     census: four images in, four uint64 strings out (36 N);
@@ -219,13 +221,16 @@ def stage_bytes_model(stage, N, D, passes=4):
     aggregate (horizontal paths): per pass the cost in and both uint8 path
       volumes out (3 N Dp);
     sgm_sweep: the partial sums of one scan order written and read, uint16
-      (4 N D per pass; the stored volumes it also reads are not counted);
+      (4 N D per pass; the stored volumes it also reads are not counted),
+      plus the horizontal paths' 3 N Dp per pass when the launch runs them
+      (order 2);
     combine (both checks and the combination): winners and subpixel maps of
       both pairs and the flow in (24 N), both disparity maps, s4, motion,
       point and validity out (49 N)."""
     Dp = (D + 15) // 16 * 16
     return {"census": 36 * N, "cost": 32 * N + passes * N * Dp,
-            "aggregate": passes * 3 * N * Dp, "sgm_sweep": passes * 4 * N * D,
+            "aggregate": passes * 3 * N * Dp,
+            "sgm_sweep": passes * 4 * N * D + (passes * 3 * N * Dp if order == 2 else 0),
             "combine": 73 * N}.get(stage)
 
 
@@ -431,9 +436,10 @@ def run_ours(args, world, rank, local):
                       "frac": round(frame_bytes_model(N, D_MAX) / (ms * 1e-3) / 1e9 / hbm_peak, 4),
                       "model": "frame_bytes_model: 16 N D + 149 N"},
         "stages_ms_per_step": {k: round(v / args.steps, 5) for k, v in stage_tot.items()},
-        "stages_hbm": {k: {"model_bytes": stage_bytes_model(k, N, D_MAX),
-                           "frac": round(stage_bytes_model(k, N, D_MAX) / (v / args.steps * 1e-3) / 1e9 / hbm_peak, 4)}
-                       for k, v in stage_tot.items() if stage_bytes_model(k, N, D_MAX)},
+        "stages_hbm": {k: {"model_bytes": stage_bytes_model(k, N, D_MAX, order=order),
+                           "frac": round(stage_bytes_model(k, N, D_MAX, order=order) / (v / args.steps * 1e-3)
+                                         / 1e9 / hbm_peak, 4)}
+                       for k, v in stage_tot.items() if stage_bytes_model(k, N, D_MAX, order=order)},
         "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
         "sweep_shape": tuned["classes"] if tuned else "built-in",
         "learned_sweep_shape": (tuned.get("learned") or "built-in") if tuned else "built-in",

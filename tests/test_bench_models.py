@@ -17,7 +17,11 @@ def test_sweep_bytes_model():
     assert bench.bytes_model("sgm_sweep", N, D, order=0) == 476_928_000
     assert bench.bytes_model("sgm_sweep", N, D, order=1) == 4 * 4 * N * D
     assert bench.bytes_model("sgm_sweep", N, D) == 953_856_000
-    assert bench.bytes_model("aggregate", N, D) == 3 * N * D
+    # the horizontal paths' launch: the cost in, both uint8 path volumes out, per pass
+    assert bench.bytes_model("aggregate", N, D) == 4 * 3 * N * D
+    # order 2: the merged launch runs the horizontal paths too
+    assert bench.bytes_model("sgm_sweep", N, D, order=2) == 4 * 4 * N * D + 4 * 3 * N * D
+    assert bench.stage_bytes_model("sgm_sweep", N, D, order=2) == bench.bytes_model("sgm_sweep", N, D, order=2)
 
 
 def test_frame_bytes_model_itemised():
