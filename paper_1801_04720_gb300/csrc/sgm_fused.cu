@@ -89,14 +89,16 @@ __global__ void __launch_bounds__(1024, 1)
     if (row + (int)gridDim.x < nrows) fetch(row + gridDim.x, buf ^ 1);
     const uint64_t* sl = cbuf + buf * cw;
     const uint64_t* srt = sl + W;
+    // right pixel j = x - 4g - k sits at srt[(x-k) & 3][((x-k) >> 2) - g]; a
+    // warp's columns step by nw (a multiple of 4), which leaves (x-k) & 3
+    // unchanged and adds nw / 4 to (x-k) >> 2
+    int base[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) base[k] = ((warp - k) & 3) * Q + ((warp - k) >> 2);
     for (int x = warp; x < W; x += nw) {
       const uint64_t a = sl[x];
       uint32_t* dst = left_only ? reinterpret_cast<uint32_t*>(CL + ((size_t)y * W + x) * Dp)
                                 : reinterpret_cast<uint32_t*>(band + x * Ds);
-      // right pixel j = x - 4g - k sits at srt[(x-k) & 3][((x-k) >> 2) - g]
-      int base[4];
-#pragma unroll
-      for (int k = 0; k < 4; k++) base[k] = ((x - k) & 3) * Q + ((x - k) >> 2);
       // every candidate of this column exists (warp-uniform): no checks
       const bool full = D == Dp && x >= Dp - 1;
       for (int g = lane; g < groups; g += 32) {
@@ -117,6 +119,8 @@ __global__ void __launch_bounds__(1024, 1)
         }
         dst[g] = packed;
       }
+#pragma unroll
+      for (int k = 0; k < 4; k++) base[k] += nw >> 2;
     }
     if (left_only) continue;
     __syncthreads();
