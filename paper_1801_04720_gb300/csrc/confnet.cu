@@ -955,6 +955,50 @@ __device__ __forceinline__ void px_step8(PxState& st, int d0, const uint32_t* sw
   }
 }
 
+// Staged form's statistics: the three group winners as in px_step8; S0, d*,
+// S2 and the neighbours of d* at the granularity of blocks of eight
+// disparities (one 16-byte word of S): the first block holding the strict
+// minimum (bb, s0), and m2 = the minimum over blocks at least two blocks away
+// from bb (the prefix minimum lagged by two blocks when a new best block
+// appears, every block from bb + 2 on afterwards).  Blocks bb - 1 .. bb + 1
+// are read again once d* is known (blk_finish).
+struct BlkState {
+  uint32_t kh, kd, ku, s0, m2, lag, prev;
+  int bb;
+};
+
+__device__ __forceinline__ void blk_step8(BlkState& st, int d0, const uint32_t* sw, uint32_t f0, uint32_t f1,
+                                          uint32_t b0, uint32_t b1, const uint32_t* ww, int hi) {
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    const uint32_t d = (uint32_t)(d0 + e);
+    const uint32_t sv = (e & 1) ? sw[e >> 1] >> 16 : sw[e >> 1] & 0xffffu;
+    const uint32_t fb = e < 4 ? f0 : f1, bb = e < 4 ? b0 : b1;
+    const uint32_t gh = ((fb >> (8 * (e & 3))) & 0xffu) + ((bb >> (8 * (e & 3))) & 0xffu);
+    const uint32_t gd = hi ? ww[e] >> 16 : ww[e] & 0xffffu;
+    st.kh = min(st.kh, (gh << 8) | d);
+    st.kd = min(st.kd, (gd << 8) | d);
+    st.ku = min(st.ku, ((sv - gh - gd) << 8) | d);
+  }
+  // the block's minimum from its packed words, then the block statistics
+  const uint32_t p = __vminu2(__vminu2(sw[0], sw[1]), __vminu2(sw[2], sw[3]));
+  const uint32_t bm = min(p & 0xffffu, p >> 16);
+  const int b = d0 >> 3;
+  if (bm < st.s0) {
+    st.s0 = bm;
+    st.bb = b;
+    st.m2 = st.lag;
+  } else if (b >= st.bb + 2) {
+    st.m2 = min(st.m2, bm);
+  }
+  st.lag = min(st.lag, st.prev);
+  st.prev = bm;
+}
+
+// d*, S(d* - 1), S(d* + 1) and S2 from blocks bb - 1 .. bb + 1 of the
+// pixel's S row, then the common tail.
+__device__ __forceinline__ void blk_finish(const FeatureArgs& a, const BlkState& st, size_t pix, int x);
+
 // Features, winner and subpixel winner of pixel `pix` (column x) from its
 // online statistics.
 __device__ __forceinline__ void px_finish(const FeatureArgs& a, const PxState& st, size_t pix, int x) {
@@ -992,6 +1036,49 @@ __device__ __forceinline__ void px_finish(const FeatureArgs& a, const PxState& s
     v = __fadd_rn((float)ds, __fdiv_rn((float)(am - bp), (float)(2 * (am + bp))));
   }
   a.dsub[pix] = v;
+}
+
+__device__ __forceinline__ void blk_finish(const FeatureArgs& a, const BlkState& st, size_t pix, int x) {
+  const int nb = a.D >> 3, b = st.bb;
+  const uint4* srow = reinterpret_cast<const uint4*>(a.S + pix * a.D);
+  // S of blocks b - 1 .. b + 1 (kBig outside the curve), as 12 words of two
+  uint32_t w[12];
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    const int bj = b - 1 + j;
+    uint4 q = make_uint4(kBig, kBig, kBig, kBig);
+    if (bj >= 0 && bj < nb) q = __ldg(srow + bj);
+    w[4 * j + 0] = q.x;
+    w[4 * j + 1] = q.y;
+    w[4 * j + 2] = q.z;
+    w[4 * j + 3] = q.w;
+  }
+  auto v = [&](int i) { return (i & 1) ? w[i >> 1] >> 16 : w[i >> 1] & 0xffffu; };
+  // first disparity of block b reaching the minimum
+  int e0 = 7;
+#pragma unroll
+  for (int e = 7; e >= 0; e--)
+    if (v(8 + e) == st.s0) e0 = e;
+  PxState ps{st.kh, st.kd, st.ku, st.s0, st.m2, 0u, 0u, 0u, 0u, 8 * b + e0};
+  // d* sits at index i0 = 8 + e0 of v (8..15), so indices 0..6 and 17..23
+  // are always two or more away; the others are selected by constant
+  // indices (no indexed register array)
+  const int i0 = 8 + e0;
+  uint32_t vm = 0u, vp = 0u;
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    vm = e == e0 ? v(7 + e) : vm;
+    vp = e == e0 ? v(9 + e) : vp;
+  }
+#pragma unroll
+  for (int i = 0; i < 7; i++) ps.m2 = min(ps.m2, min(v(i), v(17 + i)));
+#pragma unroll
+  for (int i = 7; i < 17; i++) ps.m2 = (i <= i0 - 2 || i >= i0 + 2) ? min(ps.m2, v(i)) : ps.m2;
+  // (past either end of the curve v reads 0xffff, above every S; the
+  // neighbours there are 0 as in the other forms)
+  ps.vm = ps.ds > 0 ? vm : 0u;
+  ps.vp = ps.ds < a.D - 1 ? vp : 0u;
+  px_finish(a, ps, pix, x);
 }
 
 
@@ -1048,7 +1135,8 @@ __global__ void __launch_bounds__(256, 2)
 // asynchronous copies (double-buffered: the next chunk's copies run while
 // this one is consumed); each thread then reads its own pixel's rows, padded
 // by 16 bytes so that a warp's 16-byte reads spread over all banks, and
-// updates the same online statistics as the per-pixel form.
+// updates the group winners per disparity and S0 / S2 per block of eight
+// (blk_step8), reading the three blocks around the best one again at the end.
 constexpr int kStThreads = 128;
 constexpr int kStS = 80, kStH = 48, kStW = 144;              // padded row bytes
 constexpr int kStStage = kStThreads * (kStS + 2 * kStH) + 4 * 16 * kStW;
@@ -1093,7 +1181,7 @@ __global__ void __launch_bounds__(kStThreads)
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  PxState st{kBig, kBig, kBig, kBig, kBig, kBig, kBig, 0u, 0u, 0};
+  BlkState st{kBig, kBig, kBig, kBig, kBig, kBig, kBig, 0};
   const int hi = (x >> 4) & 1, wrow = ((tid >> 5) << 4) + (x & 15);
   const int nchunks = a.D / 32;
   load_chunk(0, 0);
@@ -1120,13 +1208,13 @@ __global__ void __launch_bounds__(kStThreads)
         const uint4 f = pf[g >> 1], b = pb[g >> 1];
         const uint32_t sw[4] = {sv.x, sv.y, sv.z, sv.w};
         const uint32_t ww[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-        px_step8(st, 32 * k + 8 * g, sw, (g & 1) ? f.z : f.x, (g & 1) ? f.w : f.y, (g & 1) ? b.z : b.x,
-                 (g & 1) ? b.w : b.y, ww, hi);
+        blk_step8(st, 32 * k + 8 * g, sw, (g & 1) ? f.z : f.x, (g & 1) ? f.w : f.y, (g & 1) ? b.z : b.x,
+                  (g & 1) ? b.w : b.y, ww, hi);
       }
     }
     __syncthreads();
   }
-  if (tid < ncols) px_finish(a, st, row0 + tid, x);
+  if (tid < ncols) blk_finish(a, st, row0 + tid, x);
 }
 
 // Channel 7, the visibility margin: pixel x of a row matches right-image

@@ -62,9 +62,10 @@ def random_features(rng, H, W):
 
 
 # vector form of the features pass for D % 4 == 0 (one or two 128-disparity
-# chunks), scalar form otherwise
+# chunks), scalar form otherwise; the staged form (D % 32 == 0) at D = 32,
+# 64, 160 and 256
 SCENES = [(64, 48, 16, 0), (97, 41, 48, 1), (130, 37, 32, 2), (61, 29, 22, 3), (300, 20, 160, 4),
-          (200, 16, 150, 5)]
+          (200, 16, 150, 5), (150, 33, 64, 6), (290, 19, 256, 7)]
 
 
 @pytest.mark.parametrize("W,H,D,seed", SCENES)
