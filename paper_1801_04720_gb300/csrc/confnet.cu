@@ -21,7 +21,8 @@
 //      5th-generation tensor cores: tcgen05.mma with operands in shared
 //      memory and accumulators in tensor memory, one warp issuing and eight
 //      draining the accumulators, all four layers of an output tile fused in
-//      shared memory, the tiles of every pass of a call in one launch.
+//      shared memory (a layer's MMAs start on the rows its predecessor has
+//      finished), the tiles of every pass of a call in one launch.
 //   3. training kernels (fp32 CUDA cores): forward with the same bfloat16
 //      roundings, weighted binary cross-entropy, data and weight gradients,
 //      Adam.
@@ -381,7 +382,8 @@ constexpr int kSmW = kSmY + 4 * kPlane2;            // packed weights
 constexpr int kSmBias = kSmW + kWElems * 2;
 constexpr int kMaxPairs = (region_rows(1) * kP / 128 + 1) / 2;   // M-tile pairs of the largest layer
 constexpr int kSmBar = kSmBias + kBiasFloats * 4;                  // one mbarrier per M-tile pair
-constexpr int kSmTmem = kSmBar + 8 * (kMaxPairs + 1);            // + one for the final drain
+constexpr int kSmEp = kSmBar + 8 * (kMaxPairs + 1);              // + one for the final drain
+constexpr int kSmTmem = kSmEp + 8 * kMaxPairs;                    // epilogue done, per M-tile pair
 constexpr int kSmTotal = kSmTmem + 8;
 constexpr int kEpiWarps = 8;                                       // epilogue warps (two per TMEM lane quarter)
 constexpr int kIssuer = kEpiWarps;                                 // the warp that issues the MMAs
@@ -389,7 +391,7 @@ constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = kEpiThreads + 32;
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kMmaSpin = 1ll << 24;
-static_assert(4 * kPlane3 <= 4 * kPlane1, "layer-3 activations reuse the layer-1 buffer");
+static_assert(kPlane3 <= kPlane1, "layer-3 activations reuse the layer-1 buffer (its plane stride)");
 static_assert((region_rows(1) * kP) % 128 == 0 && (region_rows(4) * kP) % 128 == 0, "whole M tiles");
 static_assert(kSmTotal <= 227 * 1024, "shared memory");
 static_assert(kSmX % 16 == 0 && kSmY % 16 == 0 && kSmW % 16 == 0 && kSmBar % 8 == 0, "alignment");
@@ -502,6 +504,10 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   if (tid == 0) {
     for (int i = 0; i <= kMaxPairs; i++)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + i)) : "memory");
+    for (int i = 0; i < kMaxPairs; i++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(sm + kSmEp + 8 * i)),
+                   "r"(kEpiThreads)
+                   : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   }
   const uint64_t ad2 = mat_desc(smem_u32(bufx), kPlane1, 128u), bd2 = mat_desc(w2_base, kC * 16u, 128u);
   const uint64_t ad3 = mat_desc(smem_u32(bufy), kPlane2, 128u), bd3 = mat_desc(w3_base, kC * 16u, 128u);
-  const uint64_t ad4 = mat_desc(smem_u32(bufx), kPlane3, 128u), bd4 = mat_desc(w4_base, 16u * 16u, 128u);
+  const uint64_t ad4 = mat_desc(smem_u32(bufx), kPlane1, 128u), bd4 = mat_desc(w4_base, 16u * 16u, 128u);
 
   // epilogue of one M tile of a layer: this warp's 32 rows (its TMEM lane
   // quarter) -> bias, ReLU, bf16 -> the next layer's planes; the last layer
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
     const int i = m / kP, jj = m - i * kP;
     if (layer < 3) {
       uint8_t* dst = layer == 1 ? bufy : bufx;
-      const int plane = layer == 0 ? kPlane1 : layer == 1 ? kPlane2 : kPlane3;
+      const int plane = layer == 1 ? kPlane2 : kPlane1;
       const float* bl = bias + kC * layer;
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(kC * mt), v);
@@ -603,11 +609,21 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
   // Per layer the issuer commits the MMAs of each pair of M tiles to that
   // pair's mbarrier; the epilogue warps take the pairs as they complete
   // (warps 0-3 the even tile of a pair, 4-7 the odd one), so the epilogue of
-  // one pair overlaps the MMAs of the next.  The layer ends with a CTA
-  // barrier: the next layer reads the activations just written and reuses
-  // the TMEM columns.
+  // one pair overlaps the MMAs of the next.  Layers overlap too: every
+  // epilogue thread arrives on the pair's "done" mbarrier once its outputs
+  // are in shared memory and its accumulator columns are read, and the
+  // issuer starts pair pi of layer l + 1 once pairs 0 .. pi + 1 of layer l
+  // are done (output rows of M tiles 2 pi, 2 pi + 1 read the input M tiles up
+  // to 2 pi + 3: a 3x3 tap reaches 2 kP + 2 pixels ahead; those tiles' TMEM
+  // columns are the ones reused).  The layer-3 activations take the layer-1
+  // plane stride, so a write into M tile m of the shared buffer can only
+  // meet reads of layer-1 M tiles <= m, all complete by then.  A CTA
+  // barrier separates tiles.
   const bool epi = warp < kEpiWarps;
-  uint32_t phases = 0;                                // parity of each pair's mbarrier
+  const uint32_t epp = smem_u32(sm + kSmEp);
+  uint32_t phases = 0;                                // parity of each pair's MMA mbarrier
+  uint32_t ep_par = 0;                                // parity of each pair's "done" mbarrier (issuer)
+  bool timed_out = false;                             // sticky per thread
   if (epi && blockIdx.x < ntiles) fetch_features(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int ps = tile / per_pass, tl = tile - ps * per_pass;
@@ -619,19 +635,36 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
     __syncthreads();
     fence_after();
 
-    for (int layer = 0; layer < 4 && !failed; layer++) {
+    for (int layer = 0; layer < 4; layer++) {
       const int nm = region_rows(layer + 1) * kP / 128;
       const int npairs = (nm + 1) / 2;
+      const int prev_pairs = layer > 0 ? (region_rows(layer) * kP / 128 + 1) / 2 : 0;
       const int N = layer == 3 ? 16 : kC;
-      bool timed_out = false;
       if (warp == kIssuer) {
         // ---- issue: warp-uniform descriptors, one elected lane per MMA ----
         fence_after();
         const uint32_t idesc = instr_desc(N);
         const uint64_t ab = layer == 1 ? ad2 : layer == 2 ? ad3 : ad4;
         const uint64_t bb = layer == 1 ? bd2 : layer == 2 ? bd3 : bd4;
-        const uint32_t plane16 = (layer == 1 ? kPlane1 : layer == 2 ? kPlane2 : kPlane3) / 16;
-        for (int pi = 0; pi < npairs; pi++) {
+        const uint32_t plane16 = (layer == 2 ? kPlane2 : kPlane1) / 16;
+        int q_next = 0;   // next pair of the previous layer to wait for
+        // wait (bounded) until pairs < q_end of the previous layer are done
+        auto wait_prev = [&](int q_end) {
+          for (; q_next < q_end && !timed_out; q_next++) {
+            long long spins = 0;
+            while (!bar_try_wait(epp + 8u * (uint32_t)q_next, (ep_par >> q_next) & 1u)) {
+              if (++spins > kMmaSpin) {
+                timed_out = true;
+                break;
+              }
+            }
+            ep_par ^= 1u << q_next;
+          }
+          fence_after();
+        };
+        for (int pi = 0; pi < npairs && !timed_out; pi++) {
+          if (layer > 0) wait_prev(min(pi + 2, prev_pairs));
+          if (timed_out) break;
           for (int mt = 2 * pi; mt < 2 * pi + 2 && mt < nm; mt++) {
             if (layer == 0) {
 #pragma unroll
@@ -652,7 +685,9 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
           if (elect_one()) mma_commit(barp + 8u * (uint32_t)pi);
           __syncwarp();
         }
-      } else {
+        // every phase of the previous layer is waited for, in order
+        if (layer > 0) wait_prev(prev_pairs);
+      } else if (!timed_out) {
         // ---- epilogue, pair by pair (bounded waits) ----
         for (int pi = 0; pi < npairs; pi++) {
           long long spins = 0;
@@ -667,15 +702,21 @@ __global__ void __launch_bounds__(kThreads, 1) infer_kernel(InferArgs a) {
           fence_after();
           const int mt = 2 * pi + half;
           if (mt < nm) epilogue(layer, mt, X0, Y0, out);
+          if (layer < 3) {
+            // outputs visible to the tensor cores, accumulator columns read
+            fence_async_smem();
+            fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(epp + 8u * (uint32_t)pi) : "memory");
+          }
         }
         // every MMA of layer 1 has completed: the next tile's features may come in
         if (layer == 0 && !timed_out && tile + (int)gridDim.x < ntiles) fetch_features(tile + gridDim.x);
       }
-      fence_async_smem();
-      fence_before();
-      failed = __syncthreads_or(timed_out) != 0;
-      if (failed && tid == 0 && a.err) atomicExch(a.err, 1);
     }
+    fence_async_smem();
+    fence_before();
+    failed = __syncthreads_or(timed_out) != 0;
+    if (failed && tid == 0 && a.err) atomicExch(a.err, 1);
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy left in flight
   if (warp == kIssuer) {
