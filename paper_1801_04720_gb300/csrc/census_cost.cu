@@ -44,6 +44,74 @@ __global__ void __launch_bounds__(kCensusTX* kCensusTY)
   out[(size_t)y * W + x] = bits;
 }
 
+// The 9 x 7 window (the method's), four horizontally adjacent pixels a
+// thread: for one offset the four pixels' neighbours are four consecutive
+// bytes of the tile row, one byte permute of two aligned tile words; they
+// are compared with the four centres at once (unsigned byte compare by
+// SWAR: the low seven bits through an add that cannot carry between bytes,
+// the top bit by a logic function), and each verdict, the top bit of its
+// byte, moves to bit k % 8 of that byte in group word k / 8.  Byte j of the
+// eight group words is then pixel j's 62-bit string, bit k for the k-th
+// offset in the same row-major order as census_window.
+constexpr int kC97TX = 128, kC97TY = 8;   // a warp per row: 32 threads x 4 columns
+constexpr int kC97TW = kC97TX + 8;        // tile row: 4 clamped columns on each side
+constexpr int kC97TH = kC97TY + 6;
+constexpr int kC97Words = kC97TW / 4;
+
+__device__ __forceinline__ uint32_t bytes_at(uint32_t lo, uint32_t hi, int s) {
+  // bytes s .. s + 3 of the 8-byte sequence lo:hi (s in 0..4)
+  return s == 0 ? lo : s == 4 ? hi : __byte_perm(lo, hi, (uint32_t)(s | (s + 1) << 4 | (s + 2) << 8 | (s + 3) << 12));
+}
+
+__global__ void __launch_bounds__(256)
+    census97_kernel(const __grid_constant__ CensusJob job, int W, int H, int pitch) {
+  __shared__ __align__(16) uint8_t tile[kC97TH * kC97TW];
+  const uint8_t* __restrict__ img = job.img[blockIdx.z];
+  uint64_t* __restrict__ out = job.out[blockIdx.z];
+  const int bx = blockIdx.x * kC97TX, by = blockIdx.y * kC97TY;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kC97TH * kC97TW; i += 256) {
+    const int ty = i / kC97TW, tx = i - ty * kC97TW;
+    const int gx = clampi(bx - 4 + tx, 0, W - 1), gy = clampi(by - 3 + ty, 0, H - 1);
+    tile[i] = img[(size_t)gy * pitch + gx];
+  }
+  __syncthreads();
+  const int lane = tid & 31, row = tid >> 5;
+  const int y = by + row, x0 = bx + 4 * lane;
+  if (y >= H || x0 >= W) return;
+  // pixel x0 sits at tile column 4 + 4 lane: word lane + 1 of its tile row
+  const uint32_t* tw = reinterpret_cast<const uint32_t*>(tile) + lane + 1;
+  const uint32_t c = tw[(row + 3) * kC97Words];
+  const uint32_t K = 0x80808080u - (c & 0x7f7f7f7fu);
+  uint32_t g[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) g[i] = 0u;
+  int k = 0;
+#pragma unroll
+  for (int dy = -3; dy <= 3; dy++) {
+    const uint32_t* rw = tw + (row + 3 + dy) * kC97Words;
+    const uint32_t A = rw[-1], B = rw[0], C = rw[1];
+#pragma unroll
+    for (int dx = -4; dx <= 4; dx++) {
+      if (dx == 0 && dy == 0) continue;
+      const uint32_t n = dx < 0 ? bytes_at(A, B, 4 + dx) : bytes_at(B, C, dx);
+      const uint32_t t = (n & 0x7f7f7f7fu) + K;        // top bit: low seven bits of n >= those of c
+      const uint32_t lt = (~n & c) | (~(n ^ c) & ~t);  // top bit: n < c
+      g[k >> 3] |= (lt >> (7 - (k & 7))) & (0x01010101u << (k & 7));
+      k++;
+    }
+  }
+  uint64_t* o = out + (size_t)y * W + x0;
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    if (x0 + j >= W) break;
+    const uint32_t sel = (uint32_t)(j | (j + 4) << 4);
+    const uint32_t lo = __byte_perm(__byte_perm(g[0], g[1], sel), __byte_perm(g[2], g[3], sel), 0x5410);
+    const uint32_t hi = __byte_perm(__byte_perm(g[4], g[5], sel), __byte_perm(g[6], g[7], sel), 0x5410);
+    o[j] = ((uint64_t)hi << 32) | lo;
+  }
+}
+
 // Cost volume of one image row segment [xs, xs + kCostTX): the block computes
 // the census strings it needs from the raw images, then writes
 // cost[y][x][d] with consecutive threads on consecutive d (coalesced).
@@ -117,12 +185,14 @@ cudaError_t launch_census_images(const uint8_t* const* imgs, uint64_t* const* ou
       job.img[i] = imgs[i0 + i];
       job.out[i] = outs[i0 + i];
     }
-    dim3 grid((W + kCensusTX - 1) / kCensusTX, (H + kCensusTY - 1) / kCensusTY, m);
     count_launches(1);
-    if (cw == 9 && ch == 7)
-      census_kernel<4, 3><<<grid, block, smem, s>>>(job, W, H, pitch, rx, ry);
-    else
+    if (cw == 9 && ch == 7) {
+      dim3 grid97((W + kC97TX - 1) / kC97TX, (H + kC97TY - 1) / kC97TY, m);
+      census97_kernel<<<grid97, 256, 0, s>>>(job, W, H, pitch);
+    } else {
+      dim3 grid((W + kCensusTX - 1) / kCensusTX, (H + kCensusTY - 1) / kCensusTY, m);
       census_kernel<0, 0><<<grid, block, smem, s>>>(job, W, H, pitch, rx, ry);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -38,6 +38,17 @@ def test_census(sf, oracle_mod, W, H, cw, ch):
     assert np.array_equal(got, oracle_mod.census(img, cw, ch))
 
 
+@pytest.mark.parametrize("W,H", [(9, 7), (13, 7), (129, 7), (131, 10)])
+def test_census_small_and_ragged(sf, oracle_mod, W, H):
+    # the 9 x 7 kernel takes four columns a thread and 128 x 8 pixels a
+    # block: the smallest image the window allows, a thread with one or
+    # three of its columns inside, one column past a block
+    img = rand_img(W, H, 3 * W + H)
+    img[:, ::3] = 128
+    got = to_np(sf.sf_census(to_dev(img), 9, 7), np.uint64)
+    assert np.array_equal(got, oracle_mod.census(img, 9, 7))
+
+
 def test_census_pitched_image(sf, oracle_mod):
     # rows of 96 bytes holding an 80-pixel image: the pitch argument is honoured
     import ctypes
